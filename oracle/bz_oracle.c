@@ -352,7 +352,8 @@ static double f_equilibrium(const bzo_config* c, int s, double E)
 /* ------------------------------------------------------------------ */
 /* Thermal masses, Eqs. (mg), (mq).  Each species integral uses its    */
 /* own dispersion E^a = sqrt(p^2 + m_a^2) with the previous masses      */
-/* (E = |p| when m2_prev is NULL, the first step).  The bin sums are    */
+/* (E = |p| when m2_prev is NULL, the first step, and always in mass    */
+/* mode 1, the massless dispersion).  The bin sums are                  */
 /* taken exactly in 2^-30 fixed point; out[x][0] = m_g^2, out[x][1+i] = */
 /* m_{q_i}^2.  Returns 0, or 1 if a fixed-point sum would overflow.     */
 /* ------------------------------------------------------------------ */
@@ -370,7 +371,7 @@ int bzo_masses(const bzo_config* c, const int64_t* state, const double* m2_prev,
     for (int64_t x = 0; x < nxc; ++x) {
         int64_t sum_g = 0, sum_q[3] = {0, 0, 0};
         double m2p[4] = {0, 0, 0, 0};
-        if (m2_prev)
+        if (m2_prev && c->mass_mode != 1)
             for (int i = 0; i < 4; ++i) m2p[i] = m2_prev[x * 4 + i];
         for (int64_t j = 0; j < npc; ++j) {
             int jx = (int)(j / ((int64_t)c->np[1] * c->np[2]));
@@ -644,8 +645,11 @@ int bzo_collision(const bzo_config* c, const bzo_run* r, const int64_t* state, c
 /* Drift, Eq. (left handside), flux form, first-order upwind, periodic */
 /* in x.  Face flux F_{i+1/2} = c_d n_i if p_d > 0 else c_d n_{i+1},    */
 /* with the Courant number c_d = (p_d / E_p(x_up)) dt/dx taken at the   */
-/* upwind cell.  On the int64 state each face flux is rounded to an    */
-/* integer once and applied with opposite signs to the two cells.      */
+/* upwind cell.  On the int64 state the Courant number is evaluated in  */
+/* IEEE single precision (correctly rounded sqrt and divide) and held   */
+/* in 2^-30 fixed point; each face flux round((n c) 2^-30) is an exact  */
+/* integer product, computed once and applied with opposite signs to    */
+/* the two cells, so the sum of the state is invariant.                 */
 /* ------------------------------------------------------------------ */
 static double courant(const bzo_config* c, const double* m2, int64_t x, int s, double pd, double pp,
                       double dtdx)
@@ -654,6 +658,22 @@ static double courant(const bzo_config* c, const double* m2, int64_t x, int s, d
     if (c->mass_mode != 1) m = m2[x * 4 + mass_slot(s)];
     double E = sqrt(pp + m);
     return (pd / E) * dtdx;
+}
+
+static int64_t courant_fx(const bzo_config* c, const double* m2, int64_t x, int s, float pdf,
+                          float ppf, float dtdxf)
+{
+    float m = 0.0f;
+    if (c->mass_mode != 1) m = (float)m2[x * 4 + mass_slot(s)];
+    float E = sqrtf(ppf + m);
+    float cf = (pdf / E) * dtdxf;
+    return llrintf(cf * 1073741824.0f);
+}
+
+static int64_t flux_fx(int64_t n, int64_t C)
+{
+    __int128 prod = (__int128)n * (__int128)C + ((__int128)1 << 29);
+    return (int64_t)(prod >> 30);
 }
 
 static int64_t xlin(const bzo_config* c, int ix, int iy, int iz)
@@ -665,7 +685,7 @@ int bzo_drift(const bzo_config* c, const int64_t* in, const double* m2, double d
 {
     int ns = nslots(c);
     int64_t nxc = n_xcells(c), npc = n_pcells(c);
-    double dtdx = dt / c->dx;
+    float dtdxf = (float)(dt / c->dx);
     double dp[3] = {2.0 * c->L / c->np[0], 2.0 * c->L / c->np[1], 2.0 * c->L / c->np[2]};
     int species[NSPEC];
     for (int s = 0; s < NSPEC; ++s)
@@ -681,9 +701,9 @@ int bzo_drift(const bzo_config* c, const int64_t* in, const double* m2, double d
             for (int64_t j = 0; j < npc; ++j) {
                 int jv[3] = {(int)(j / ((int64_t)c->np[1] * c->np[2])),
                              (int)((j / c->np[2]) % c->np[1]), (int)(j % c->np[2])};
-                double pv[3];
-                for (int d = 0; d < 3; ++d) pv[d] = -c->L + ((double)jv[d] + 0.5) * dp[d];
-                double pp = (pv[0] * pv[0] + pv[1] * pv[1]) + pv[2] * pv[2];
+                float pf[3];
+                for (int d = 0; d < 3; ++d) pf[d] = (float)(-c->L + ((double)jv[d] + 0.5) * dp[d]);
+                float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
                 int64_t nc = in[((int64_t)sl * nxc + x) * npc + j];
                 int64_t acc = 0;
                 for (int d = 0; d < 3; ++d) {
@@ -693,16 +713,14 @@ int bzo_drift(const bzo_config* c, const int64_t* in, const double* m2, double d
                     hi[d] = (xi[d] + 1) % c->nx[d];
                     int64_t xl = xlin(c, lo[0], lo[1], lo[2]), xh = xlin(c, hi[0], hi[1], hi[2]);
                     int64_t fplus, fminus;
-                    if (pv[d] > 0.0) {
-                        double cc = courant(c, m2, x, s, pv[d], pp, dtdx);
-                        double cl = courant(c, m2, xl, s, pv[d], pp, dtdx);
-                        fplus = llrint(cc * (double)nc);
-                        fminus = llrint(cl * (double)in[((int64_t)sl * nxc + xl) * npc + j]);
+                    if (pf[d] > 0.0f) {
+                        fplus = flux_fx(nc, courant_fx(c, m2, x, s, pf[d], ppf, dtdxf));
+                        fminus = flux_fx(in[((int64_t)sl * nxc + xl) * npc + j],
+                                         courant_fx(c, m2, xl, s, pf[d], ppf, dtdxf));
                     } else {
-                        double ch = courant(c, m2, xh, s, pv[d], pp, dtdx);
-                        double cc = courant(c, m2, x, s, pv[d], pp, dtdx);
-                        fplus = llrint(ch * (double)in[((int64_t)sl * nxc + xh) * npc + j]);
-                        fminus = llrint(cc * (double)nc);
+                        fplus = flux_fx(in[((int64_t)sl * nxc + xh) * npc + j],
+                                        courant_fx(c, m2, xh, s, pf[d], ppf, dtdxf));
+                        fminus = flux_fx(nc, courant_fx(c, m2, x, s, pf[d], ppf, dtdxf));
                     }
                     acc += fplus - fminus;
                 }
