@@ -646,7 +646,8 @@ int bzo_collision(const bzo_config* c, const bzo_run* r, const int64_t* state, c
 /* in x.  Face flux F_{i+1/2} = c_d n_i if p_d > 0 else c_d n_{i+1},    */
 /* with the Courant number c_d = (p_d / E_p(x_up)) dt/dx taken at the   */
 /* upwind cell.  On the int64 state the Courant number is evaluated in  */
-/* IEEE single precision (correctly rounded sqrt and divide) and held   */
+/* IEEE single precision as (p_d (1/sqrt(p^2 + m^2))) dt/dx (correctly  */
+/* rounded sqrt and divide) and held                                    */
 /* in 2^-30 fixed point; each face flux round((n c) 2^-30) is an exact  */
 /* integer product, computed once and applied with opposite signs to    */
 /* the two cells, so the sum of the state is invariant.                 */
@@ -665,8 +666,8 @@ static int64_t courant_fx(const bzo_config* c, const double* m2, int64_t x, int 
 {
     float m = 0.0f;
     if (c->mass_mode != 1) m = (float)m2[x * 4 + mass_slot(s)];
-    float E = sqrtf(ppf + m);
-    float cf = (pdf / E) * dtdxf;
+    float inv = 1.0f / sqrtf(ppf + m);
+    float cf = (pdf * inv) * dtdxf;
     return llrintf(cf * 1073741824.0f);
 }
 
@@ -783,10 +784,17 @@ int bzo_drift_f64(const bzo_config* c, const double* in, const double* m2, doubl
 /* ------------------------------------------------------------------ */
 /* Moments, Eqs. (particle numbers), (energy momentum tensor): per      */
 /* x-cell and active species, out[x][slot][0..4] = (n, eps, T01, T02,   */
-/* T03) as densities in GeV^3 / GeV^4, with E = sqrt(p^2 + m^2) at the   */
-/* bin centres (|p| in mass mode 1).  Also nsum[slot] = exact int64     */
-/* sum of the state (total number in units 2^-40 Dp^3/(2 pi)^3).         */
+/* T03) as densities in GeV^3 / GeV^4.  The sums are exact integer sums */
+/* (order independent): the number is sum n; the energy uses E at the   */
+/* bin centre in IEEE single precision, sqrt(p^2 + m^2) (|p| in mass     */
+/* mode 1), held in 2^-24 fixed point; the momentum uses p_d =          */
+/* (2 j_d + 1 - n_d) dp_d / 2.  nsum[slot] = exact sum of the state.    */
 /* ------------------------------------------------------------------ */
+static double i128_to_double(__int128 v)
+{
+    return (double)(int64_t)(v >> 64) * 18446744073709551616.0 + (double)(uint64_t)v;
+}
+
 int bzo_moments(const bzo_config* c, const int64_t* state, const double* m2, double* out,
                 int64_t* nsum)
 {
@@ -802,31 +810,25 @@ int bzo_moments(const bzo_config* c, const int64_t* state, const double* m2, dou
     for (int64_t x = 0; x < nxc; ++x) {
         for (int sl = 0; sl < ns; ++sl) {
             int s = species[sl];
-            double m = c->mass_mode == 1 ? 0.0 : m2[x * 4 + mass_slot(s)];
-            int64_t ntot = 0;
-            double e = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+            float m = c->mass_mode == 1 ? 0.0f : (float)m2[x * 4 + mass_slot(s)];
+            __int128 ntot = 0, e = 0, t[3] = {0, 0, 0};
             for (int64_t j = 0; j < npc; ++j) {
                 int jv[3] = {(int)(j / ((int64_t)c->np[1] * c->np[2])),
                              (int)((j / c->np[2]) % c->np[1]), (int)(j % c->np[2])};
-                double pv[3];
-                for (int d = 0; d < 3; ++d) pv[d] = -c->L + ((double)jv[d] + 0.5) * dp[d];
-                double pp = (pv[0] * pv[0] + pv[1] * pv[1]) + pv[2] * pv[2];
-                double E = sqrt(pp + m);
+                float pf[3];
+                for (int d = 0; d < 3; ++d) pf[d] = (float)(-c->L + ((double)jv[d] + 0.5) * dp[d]);
+                float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
+                int64_t Efx = llrintf(sqrtf(ppf + m) * 16777216.0f);
                 int64_t n = state[((int64_t)sl * nxc + x) * npc + j];
-                double nd = (double)n;
                 ntot += n;
-                e += E * nd;
-                t1 += pv[0] * nd;
-                t2 += pv[1] * nd;
-                t3 += pv[2] * nd;
+                e += (__int128)Efx * n;
+                for (int d = 0; d < 3; ++d) t[d] += (__int128)(2 * jv[d] + 1 - c->np[d]) * n;
             }
-            nsum[sl] += ntot;
+            nsum[sl] += (int64_t)ntot;
             double* o = out + (x * ns + sl) * 5;
-            o[0] = (double)ntot * pref;
-            o[1] = e * pref;
-            o[2] = t1 * pref;
-            o[3] = t2 * pref;
-            o[4] = t3 * pref;
+            o[0] = i128_to_double(ntot) * pref;
+            o[1] = i128_to_double(e) * pref * (1.0 / 16777216.0);
+            for (int d = 0; d < 3; ++d) o[2 + d] = i128_to_double(t[d]) * pref * (0.5 * dp[d]);
         }
     }
     return 0;
