@@ -1,0 +1,170 @@
+/*
+ * bz.h -- C ABI of libbz: the Monte Carlo 2->2 collision term of the
+ * relativistic Boltzmann equation for g, u, d, s, ubar, dbar, sbar with
+ * symmetrical sampling, the upwind drift and the moments, on one GB300
+ * (sm_103a).  Method: Zhang, Wu, Pu, Qin, Wang, "Towards a full solution of
+ * relativistic Boltzmann equation for quark-gluon matter on GPUs",
+ * arXiv:1912.04457.
+ *
+ * Conventions
+ * -----------
+ * Units: momenta and masses in GeV, x in fm, t in fm/c (hbar c =
+ *   0.1973269804 GeV fm converts dt into GeV^-1).
+ * Species: 0 g, 1 u, 2 d, 3 s, 4 ubar, 5 dbar, 6 sbar.  Degeneracies
+ *   N_g = 16, N_q = 6 (Sec. II).  Only the species of the mask are stored.
+ * State: int64 n[slot][x][p] = N_s f_s(x, p) 2^40, round-half-even; slots
+ *   are the active species in increasing index order; x = (ix, iy, iz) and
+ *   p = (jx, jy, jz) row-major, last index fastest.  Momentum cells are
+ *   centred: p_j = -L + (j + 1/2) 2L/n_p.  Spatial cells are periodic.
+ * Memory: every pointer named "device" is CUDA device memory owned by the
+ *   caller (e.g. a torch tensor's data_ptr); pointers named "host" are host
+ *   memory.  The handle owns only its descriptors and device scratch.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *   work is enqueued on it; calls return without synchronising unless
+ *   stated.
+ * Errors: 0 on success; negative BZ_E* on error (nothing was enqueued
+ *   after the failing check; bz_last_error gives the message).  No C++
+ *   exception crosses this boundary.
+ */
+#ifndef BZ_H
+#define BZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BZ_OK 0
+#define BZ_EINVAL (-1)    /* bad argument                                    */
+#define BZ_ENOMEM (-2)    /* device allocation failed                        */
+#define BZ_ECUDA (-3)     /* a CUDA call or launch failed                    */
+#define BZ_EOVERFLOW (-4) /* fixed-point range exceeded (see bz_get_flags)   */
+#define BZ_ENODEV (-5)    /* no CUDA device / wrong architecture             */
+
+#define BZ_PREC_F64 0     /* integrand in FP64 (bit-exact with the CPU oracle) */
+#define BZ_PREC_F32 1     /* integrand in FP32, uniforms with 23-bit resolution */
+
+#define BZ_SAMPLER_SYMMETRIC 0 /* each root deposits +w/4 to p and k3, -w/4 to k1, k2 (Eq. small c relation) */
+#define BZ_SAMPLER_PLAIN 1     /* usual MC: full weight to the anchor cell only (Fig. 3, 4 "without") */
+
+#define BZ_MASS_THERMAL 0   /* Eqs. (mg), (mq) every call; E = sqrt(p^2 + m^2) everywhere        */
+#define BZ_MASS_MASSLESS 1  /* thermal m_g^2 as |M|^2 regulator only; E = |p| in kinematics     */
+#define BZ_MASS_FIXED 2     /* masses set by bz_set_masses, never recomputed (Fig. 5)            */
+
+typedef struct bz_handle_s* bz_handle;
+
+typedef struct bz_grid {
+    int32_t nx[3];   /* spatial cells per axis (1 = homogeneous along that axis)          */
+    double dx;       /* spatial cell size, fm                                              */
+    int32_t np[3];   /* momentum cells per axis; even n keeps cell centres off p = 0       */
+    double L;        /* momentum box [-L, L)^3, GeV; also the integration box of (k1_perp, k3) */
+    uint64_t seed;   /* Philox4x32-10 key (low word xor box id, high word)                  */
+    uint32_t box;    /* box id, xored into the key's low word                               */
+    uint32_t reserved;
+} bz_grid;
+
+/* Creates a handle on the current CUDA device for the grid *g (host
+ * pointer, copied).  Allocates the handle's device scratch (masses, flags,
+ * one f-sized work array).  Defaults: gluons only, alpha_s = 0.3, mass mode
+ * BZ_MASS_THERMAL, all anchors sampled, no equilibrium override.
+ * Grid and seed follow the statement of the problem in Sec. II / III.
+ * Errors: BZ_EINVAL (sizes <= 0, L <= 0, dx <= 0), BZ_ENODEV, BZ_ENOMEM. */
+int bz_init_grid(bz_handle* out, const bz_grid* g);
+
+/* Releases the handle and its scratch (synchronises the device first). */
+int bz_destroy(bz_handle h);
+
+/* Message of the last error on h (or of the last failed bz_init_grid when h
+ * is NULL).  Valid until the next call on h. */
+const char* bz_last_error(bz_handle h);
+
+/* Selects the species (bit s of species_mask = species s, Sec. II), the
+ * coupling (g^2 = 4 pi alpha_s) and the mass mode (BZ_MASS_*).  A term of
+ * Eqs. (C_quark)/(C_gluon) is evaluated only if all four of its species are
+ * active.  Reallocates scratch if the slot count changes and forgets the
+ * previous masses.  Errors: BZ_EINVAL (empty mask, alpha_s <= 0, mode). */
+int bz_set_species(bz_handle h, uint32_t species_mask, double alpha_s, int mass_mode);
+
+/* Number of active species (state slots), x cells, p cells; any out pointer
+ * may be NULL. */
+int bz_query_sizes(bz_handle h, int32_t* nslots, int64_t* nxcells, int64_t* npcells);
+
+/* Collision increment, Eqs. (C_a_b), (work out delta E), (MC C_gg), (ca),
+ * (small c relation):
+ *   1. thermal masses from `state` (Eqs. mg, mq) unless mass mode FIXED,
+ *      with E from the previous masses of this handle (E = |p| on the first
+ *      call after init / bz_reset_masses); they become the handle's masses;
+ *   2. for every anchor (species d, x cell, p cell) nsamples Philox samples
+ *      of (p jitter, k1x, k1y, k3) in [-L, L)^5; for every term of species
+ *      d's equation and every valid k1z root inside the box, the weight
+ *      w = c~ (2L)^5/(4 nsamples) dt/hbar_c 2^40 is rounded to an integer q
+ *      and deposited +q to (d, p), +q to (c, k3), -q to (a, k1), -q to (b, k2)
+ *      (BZ_SAMPLER_PLAIN: +4w rounded to (d, p) only).
+ * state (device, int64 [nslots][nx][np]) is read only.  A (device, int64,
+ * same shape) is zeroed and filled with the increment of N f 2^40 over dt.
+ * Sum of A is exactly 0 with the symmetric sampler.  step enters the
+ * Philox counter (counter = (2 sample + block, p, x, step << 3 | d)).
+ * prec: BZ_PREC_F64 (bit-exact with the FP64 CPU oracle) or BZ_PREC_F32.
+ * Errors: BZ_EINVAL (nsamples <= 0, step outside [0, 2^29), prec/sampler),
+ * BZ_ECUDA.  Overflows of the fixed point are counted (bz_get_flags). */
+int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples,
+                      int32_t step, double dt, int32_t prec, int32_t sampler, void* stream);
+
+/* Free streaming, Eq. (left handside) without the force term: first-order
+ * upwind in flux form, periodic in x, v = p/E_p(x) with the handle's current
+ * masses (E = |p| in mass mode MASSLESS).  Courant numbers in IEEE FP32 held
+ * in 2^-30 fixed point; each face flux is an exact rounded integer product
+ * applied with opposite signs to its two cells, so the sum of the state is
+ * invariant.  in, out: device int64 [nslots][nx][np], must not overlap. */
+int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt, void* stream);
+
+/* nsteps forward-Euler steps of Eq. (left handside) with all terms from
+ * f^n (unsplit): per step, masses from n^n, then
+ *   n^{n+1} = drift(n^n) + collision increment(n^n)
+ * with Philox step index step0 + k.  state (device int64) is updated in
+ * place.  moments_out (device, may be NULL): per step, the moments of
+ * n^{n+1} as bz_moments, [nsteps][nx][nslots][5] doubles. */
+int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, int32_t nsamples,
+            int32_t prec, int32_t step0, double* moments_out, void* stream);
+
+/* Moments, Eqs. (particle numbers), (energy momentum tensor), per x cell
+ * and active species: out[x][slot][0..4] = (n, eps, T^01, T^02, T^03) as
+ * densities (GeV^3, GeV^4), E at the bin centres with the handle's current
+ * masses.  state: device int64; out: device double [nx][nslots][5]. */
+int bz_moments(bz_handle h, const int64_t* state, double* out, void* stream);
+
+/* Current masses, host double [nx][4] = (m_g^2, m_u^2, m_d^2, m_s^2) in
+ * GeV^2.  bz_get_masses synchronises the stream of the last call.
+ * bz_set_masses also serves as the "previous" masses of the next call. */
+int bz_get_masses(bz_handle h, double* m2_host);
+int bz_set_masses(bz_handle h, const double* m2_host);
+/* Forgets the previous masses: the next mass evaluation uses E = |p|. */
+int bz_reset_masses(bz_handle h);
+
+/* Counters (host int64 [4], synchronising): [0] roots dropped because a
+ * regulated denominator t - m_g^2 or u - m_g^2 was >= 0 or s <= 0, [1]
+ * deposits whose fixed-point weight exceeded 2^62, [2] mass fixed-point
+ * overflows, [3] reserved.  bz_clear_flags zeroes them. */
+int bz_get_flags(bz_handle h, int64_t* flags_host);
+int bz_clear_flags(bz_handle h);
+
+/* Restricts the anchors to those with linear index a = (slot nx + x) np + p
+ * satisfying a % stride == offset (stride 1 = all).  Used to check full
+ * size workloads against the CPU oracle on a sample of anchors. */
+int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset);
+
+/* Equilibrium check mode: when enable != 0, f at each leg is the Bose-
+ * Einstein / Fermi-Dirac value at the leg's continuous momentum, Eqs. (fg),
+ * (fq), with temperature T and chemical potentials mu (host double [7]),
+ * instead of the bin value of the state. */
+int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host);
+
+/* Library version string. */
+const char* bz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BZ_H */

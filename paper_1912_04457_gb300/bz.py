@@ -1,0 +1,203 @@
+"""Thin ctypes binding of libbz (include/bz.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module checks the
+tensors (device, dtype, shape, contiguity), passes their data pointers and
+the current torch stream, and turns negative return codes into exceptions.
+There is no fallback: if libbz.so is missing, `load()` raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbz.so")
+
+BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA, BZ_EOVERFLOW, BZ_ENODEV = 0, -1, -2, -3, -4, -5
+PREC_F64, PREC_F32 = 0, 1
+SAMPLER_SYMMETRIC, SAMPLER_PLAIN = 0, 1
+MASS_THERMAL, MASS_MASSLESS, MASS_FIXED = 0, 1, 2
+
+
+class BzGrid(C.Structure):
+    _fields_ = [("nx", C.c_int32 * 3), ("dx", C.c_double), ("np", C.c_int32 * 3), ("L", C.c_double),
+                ("seed", C.c_uint64), ("box", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class BzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libbz error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P, _I32, _I64, _D, _U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_uint32
+SIGNATURES = {
+    "bz_init_grid": (C.c_int, [C.POINTER(_P), C.POINTER(BzGrid)]),
+    "bz_destroy": (C.c_int, [_P]),
+    "bz_last_error": (C.c_char_p, [_P]),
+    "bz_set_species": (C.c_int, [_P, _U32, _D, C.c_int]),
+    "bz_query_sizes": (C.c_int, [_P, _P, _P, _P]),
+    "bz_collision_term": (C.c_int, [_P, _P, _P, _I32, _I32, _D, _I32, _I32, _P]),
+    "bz_drift": (C.c_int, [_P, _P, _P, _D, _P]),
+    "bz_step": (C.c_int, [_P, _P, _D, _I32, _I32, _I32, _I32, _P, _P]),
+    "bz_moments": (C.c_int, [_P, _P, _P, _P]),
+    "bz_get_masses": (C.c_int, [_P, _P]),
+    "bz_set_masses": (C.c_int, [_P, _P]),
+    "bz_reset_masses": (C.c_int, [_P]),
+    "bz_get_flags": (C.c_int, [_P, _P]),
+    "bz_clear_flags": (C.c_int, [_P]),
+    "bz_set_anchor_subset": (C.c_int, [_P, _I64, _I64]),
+    "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
+    "bz_version": (C.c_char_p, []),
+}
+
+
+def load(path=LIB_PATH):
+    """Loads libbz.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libbz.so not found at %s; run __graft_entry__.build() first" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, numel=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return C.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """One phase-space grid on the current CUDA device (bz_init_grid)."""
+
+    def __init__(self, nx=(1, 1, 1), dx=1.0, np_=(20, 20, 20), L=2.0, seed=1, box=0,
+                 species_mask=1, alpha_s=0.3, mass_mode=MASS_THERMAL):
+        self.lib = load()
+        g = BzGrid()
+        g.nx[:] = list(nx)
+        g.dx = dx
+        g.np[:] = list(np_)
+        g.L = L
+        g.seed = seed
+        g.box = box
+        h = C.c_void_p()
+        rc = self.lib.bz_init_grid(C.byref(h), C.byref(g))
+        if rc != BZ_OK:
+            raise BzError(rc, self.lib.bz_last_error(None).decode())
+        self.h = h
+        self.nx, self.np_ = tuple(nx), tuple(np_)
+        self.set_species(species_mask, alpha_s, mass_mode)
+
+    def _check(self, rc):
+        if rc != BZ_OK:
+            raise BzError(rc, self.lib.bz_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ----------------------------------------------------
+    def set_species(self, species_mask, alpha_s=0.3, mass_mode=MASS_THERMAL):
+        self._check(self.lib.bz_set_species(self.h, species_mask, alpha_s, mass_mode))
+        ns, nx, npc = C.c_int32(), C.c_int64(), C.c_int64()
+        self._check(self.lib.bz_query_sizes(self.h, C.byref(ns), C.byref(nx), C.byref(npc)))
+        self.nslots, self.nxc, self.npc = ns.value, nx.value, npc.value
+        self.ncell = self.nslots * self.nxc * self.npc
+
+    @property
+    def shape(self):
+        return (self.nslots, self.nxc, self.npc)
+
+    def set_anchor_subset(self, stride=1, offset=0):
+        self._check(self.lib.bz_set_anchor_subset(self.h, stride, offset))
+
+    def set_equilibrium(self, enable, T=0.5, mu=None):
+        mu = np.ascontiguousarray(mu if mu is not None else np.zeros(7), dtype=np.float64)
+        self._check(self.lib.bz_set_equilibrium(self.h, 1 if enable else 0, T,
+                                                mu.ctypes.data_as(C.c_void_p)))
+
+    def get_masses(self):
+        out = np.zeros((self.nxc, 4))
+        self._check(self.lib.bz_get_masses(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_masses(self, m2):
+        m2 = np.ascontiguousarray(m2, dtype=np.float64).reshape(self.nxc, 4)
+        self._check(self.lib.bz_set_masses(self.h, m2.ctypes.data_as(C.c_void_p)))
+
+    def reset_masses(self):
+        self._check(self.lib.bz_reset_masses(self.h))
+
+    def flags(self):
+        out = np.zeros(4, dtype=np.int64)
+        self._check(self.lib.bz_get_flags(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def clear_flags(self):
+        self._check(self.lib.bz_clear_flags(self.h))
+
+    # -- the hot path -------------------------------------------------------
+    def collision_term(self, state, A, nsamples, step=0, dt=0.01, prec=PREC_F64,
+                       sampler=SAMPLER_SYMMETRIC, stream=None):
+        import torch
+        self._check(self.lib.bz_collision_term(
+            self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
+            _dev_ptr(A, torch.int64, self.ncell, "A"), nsamples, step, dt, prec, sampler,
+            _stream_ptr(stream)))
+
+    def drift(self, state_in, state_out, dt, stream=None):
+        import torch
+        self._check(self.lib.bz_drift(self.h, _dev_ptr(state_in, torch.int64, self.ncell, "in"),
+                                      _dev_ptr(state_out, torch.int64, self.ncell, "out"), dt,
+                                      _stream_ptr(stream)))
+
+    def step(self, state, dt, nsteps, nsamples, prec=PREC_F32, step0=0, moments_out=None,
+             stream=None):
+        import torch
+        mptr = None
+        if moments_out is not None:
+            mptr = _dev_ptr(moments_out, torch.float64, nsteps * self.nxc * self.nslots * 5,
+                            "moments_out")
+        self._check(self.lib.bz_step(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), dt,
+                                     nsteps, nsamples, prec, step0, mptr, _stream_ptr(stream)))
+
+    def moments(self, state, out, stream=None):
+        import torch
+        self._check(self.lib.bz_moments(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
+                                        _dev_ptr(out, torch.float64, self.nxc * self.nslots * 5, "out"),
+                                        _stream_ptr(stream)))
+
+
+def version():
+    return load().bz_version().decode()

@@ -1,0 +1,580 @@
+// C ABI of libbz (declared in include/bz.h): handle management, argument
+// checks, and the per-step orchestration of the kernels on the caller's
+// stream.  Host arithmetic that feeds bit-exact paths (grid spacings,
+// weights, |M|^2 prefactors) is written in the same operation order as the
+// formula it implements.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/bz.h"
+#include "bz_internal.h"
+
+using namespace bz;
+
+struct bz_handle_s {
+    bz_grid g{};
+    int device = 0;
+    int nsm = 0;
+    uint32_t mask = 1;
+    double alpha_s = 0.3;
+    int mass_mode = BZ_MASS_THERMAL;
+    int nslots = 1;
+    int slot_species[NSPEC] = {0};
+    int slot_of[NSPEC] = {0, -1, -1, -1, -1, -1, -1};
+    int64_t nxc = 0, npc = 0, ncell = 0;
+    double* d_m2[2] = {nullptr, nullptr};
+    int cur = 0;
+    bool have_masses = false;
+    long long* d_acc = nullptr;
+    long long* d_flags = nullptr;
+    void* d_freal = nullptr;       // f of the state, double-sized
+    long long* d_state2 = nullptr; // second state buffer for bz_step
+    int analytic = 0;
+    double T = 0.5;
+    double mu[NSPEC] = {0};
+    int64_t a_stride = 1, a_offset = 0;
+    std::string err;
+};
+
+static std::string g_init_error;
+
+static int fail(bz_handle h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_init_error = buf;
+    return code;
+}
+
+#define CK(h, call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((h), BZ_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+static void free_scratch(bz_handle h)
+{
+    cudaFree(h->d_m2[0]);
+    cudaFree(h->d_m2[1]);
+    cudaFree(h->d_acc);
+    cudaFree(h->d_flags);
+    cudaFree(h->d_freal);
+    cudaFree(h->d_state2);
+    h->d_m2[0] = h->d_m2[1] = nullptr;
+    h->d_acc = h->d_flags = h->d_state2 = nullptr;
+    h->d_freal = nullptr;
+}
+
+static int alloc_scratch(bz_handle h)
+{
+    cudaFree(h->d_freal);
+    cudaFree(h->d_state2);
+    h->d_freal = nullptr;
+    h->d_state2 = nullptr;
+    h->ncell = (int64_t)h->nslots * h->nxc * h->npc;
+    if (cudaMalloc(&h->d_freal, sizeof(double) * h->ncell) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for f", (long long)(8 * h->ncell));
+    return BZ_OK;
+}
+
+static void set_slots(bz_handle h)
+{
+    int n = 0;
+    for (int s = 0; s < NSPEC; ++s) {
+        if (h->mask & (1u << s)) {
+            h->slot_of[s] = n;
+            h->slot_species[n] = s;
+            ++n;
+        } else {
+            h->slot_of[s] = -1;
+        }
+    }
+    h->nslots = n;
+}
+
+extern "C" const char* bz_version(void) { return "libbz 0.1 (sm_103a)"; }
+
+extern "C" const char* bz_last_error(bz_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
+{
+    if (!out || !g) return fail(nullptr, BZ_EINVAL, "null argument");
+    *out = nullptr;
+    for (int d = 0; d < 3; ++d) {
+        if (g->nx[d] <= 0 || g->np[d] <= 0) return fail(nullptr, BZ_EINVAL, "grid sizes must be positive");
+        if (g->np[d] > MAX_NP) return fail(nullptr, BZ_EINVAL, "np[%d] = %d exceeds %d", d, g->np[d], MAX_NP);
+    }
+    if (!(g->L > 0) || !(g->dx > 0)) return fail(nullptr, BZ_EINVAL, "L and dx must be positive");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, BZ_ENODEV, "no CUDA device");
+    bz_handle h = new (std::nothrow) bz_handle_s();
+    if (!h) return fail(nullptr, BZ_ENOMEM, "out of host memory");
+    h->g = *g;
+    cudaGetDevice(&h->device);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, h->device);
+    if (prop.major * 10 + prop.minor < 100) {
+        delete h;
+        return fail(nullptr, BZ_ENODEV, "device %s (sm_%d%d) is not a Blackwell GPU", prop.name, prop.major,
+                    prop.minor);
+    }
+    h->nsm = prop.multiProcessorCount;
+    h->nxc = (int64_t)g->nx[0] * g->nx[1] * g->nx[2];
+    h->npc = (int64_t)g->np[0] * g->np[1] * g->np[2];
+    set_slots(h);
+    int rc;
+    if (cudaMalloc(&h->d_m2[0], sizeof(double) * 4 * h->nxc) != cudaSuccess ||
+        cudaMalloc(&h->d_m2[1], sizeof(double) * 4 * h->nxc) != cudaSuccess ||
+        cudaMalloc(&h->d_acc, sizeof(long long) * 4 * h->nxc) != cudaSuccess ||
+        cudaMalloc(&h->d_flags, sizeof(long long) * 4) != cudaSuccess) {
+        free_scratch(h);
+        delete h;
+        return fail(nullptr, BZ_ENOMEM, "cannot allocate handle scratch");
+    }
+    if ((rc = alloc_scratch(h)) != BZ_OK) {
+        g_init_error = h->err;
+        free_scratch(h);
+        delete h;
+        return rc;
+    }
+    cudaMemset(h->d_flags, 0, sizeof(long long) * 4);
+    cudaMemset(h->d_m2[0], 0, sizeof(double) * 4 * h->nxc);
+    cudaMemset(h->d_m2[1], 0, sizeof(double) * 4 * h->nxc);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_scratch(h);
+        delete h;
+        return fail(nullptr, BZ_ECUDA, "device initialisation failed");
+    }
+    *out = h;
+    return BZ_OK;
+}
+
+extern "C" int bz_destroy(bz_handle h)
+{
+    if (!h) return BZ_EINVAL;
+    cudaDeviceSynchronize();
+    free_scratch(h);
+    delete h;
+    return BZ_OK;
+}
+
+extern "C" int bz_set_species(bz_handle h, uint32_t species_mask, double alpha_s, int mass_mode)
+{
+    if (!h) return BZ_EINVAL;
+    if ((species_mask & 0x7Fu) == 0 || (species_mask & ~0x7Fu)) return fail(h, BZ_EINVAL, "bad species mask 0x%x", species_mask);
+    if (!(alpha_s > 0)) return fail(h, BZ_EINVAL, "alpha_s must be positive");
+    if (mass_mode < 0 || mass_mode > 2) return fail(h, BZ_EINVAL, "bad mass mode %d", mass_mode);
+    int old = h->nslots;
+    h->mask = species_mask;
+    h->alpha_s = alpha_s;
+    h->mass_mode = mass_mode;
+    set_slots(h);
+    h->have_masses = false;
+    if (h->nslots != old) return alloc_scratch(h);
+    return BZ_OK;
+}
+
+extern "C" int bz_query_sizes(bz_handle h, int32_t* nslots, int64_t* nxcells, int64_t* npcells)
+{
+    if (!h) return BZ_EINVAL;
+    if (nslots) *nslots = h->nslots;
+    if (nxcells) *nxcells = h->nxc;
+    if (npcells) *npcells = h->npc;
+    return BZ_OK;
+}
+
+extern "C" int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset)
+{
+    if (!h) return BZ_EINVAL;
+    if (stride < 1 || offset < 0 || offset >= stride) return fail(h, BZ_EINVAL, "bad anchor subset");
+    h->a_stride = stride;
+    h->a_offset = offset;
+    return BZ_OK;
+}
+
+extern "C" int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host)
+{
+    if (!h) return BZ_EINVAL;
+    if (enable && !(T > 0)) return fail(h, BZ_EINVAL, "T must be positive");
+    h->analytic = enable ? 1 : 0;
+    h->T = T;
+    for (int s = 0; s < NSPEC; ++s) h->mu[s] = mu_host ? mu_host[s] : 0.0;
+    return BZ_OK;
+}
+
+extern "C" int bz_get_masses(bz_handle h, double* m2_host)
+{
+    if (!h || !m2_host) return BZ_EINVAL;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(m2_host, h->d_m2[h->cur], sizeof(double) * 4 * h->nxc, cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
+extern "C" int bz_set_masses(bz_handle h, const double* m2_host)
+{
+    if (!h || !m2_host) return BZ_EINVAL;
+    for (int64_t i = 0; i < 4 * h->nxc; ++i)
+        if (!(m2_host[i] >= 0)) return fail(h, BZ_EINVAL, "masses squared must be >= 0");
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(h->d_m2[h->cur], m2_host, sizeof(double) * 4 * h->nxc, cudaMemcpyHostToDevice));
+    h->have_masses = true;
+    return BZ_OK;
+}
+
+extern "C" int bz_reset_masses(bz_handle h)
+{
+    if (!h) return BZ_EINVAL;
+    h->have_masses = false;
+    return BZ_OK;
+}
+
+extern "C" int bz_get_flags(bz_handle h, int64_t* flags_host)
+{
+    if (!h || !flags_host) return BZ_EINVAL;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(flags_host, h->d_flags, sizeof(long long) * 4, cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
+extern "C" int bz_clear_flags(bz_handle h)
+{
+    if (!h) return BZ_EINVAL;
+    CK(h, cudaMemset(h->d_flags, 0, sizeof(long long) * 4));
+    return BZ_OK;
+}
+
+// --------------------------------------------------------------------------
+// internal steps
+// --------------------------------------------------------------------------
+static double dp_of(const bz_handle h, int d) { return 2.0 * h->g.L / h->g.np[d]; }
+
+// Thermal masses of `state` (Eqs. mg, mq) into the other mass buffer, then
+// make them current.  E from the current masses if there are any (and not
+// in massless mode), else |p|.
+static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)
+{
+    if (h->mass_mode == BZ_MASS_FIXED) {
+        if (!h->have_masses) return fail(h, BZ_EINVAL, "mass mode FIXED needs bz_set_masses first");
+        return BZ_OK;
+    }
+    const double dA = 8.0, CF = 4.0 / 3.0;
+    double g2 = 4.0 * PI * h->alpha_s;
+    double dpx = 2.0 * h->g.L / h->g.np[0], dpy = 2.0 * h->g.L / h->g.np[1], dpz = 2.0 * h->g.L / h->g.np[2];
+    double twopi = 2.0 * PI;
+    MassArgs a{};
+    a.state = state;
+    a.acc = h->d_acc;
+    a.m2_out = h->d_m2[h->cur ^ 1];
+    a.m2_prev = (h->have_masses && h->mass_mode != BZ_MASS_MASSLESS) ? h->d_m2[h->cur] : nullptr;
+    a.flags = h->d_flags;
+    a.nxc = h->nxc;
+    a.npc = h->npc;
+    for (int d = 0; d < 3; ++d) a.np[d] = h->g.np[d];
+    a.L = h->g.L;
+    a.dp[0] = dpx;
+    a.dp[1] = dpy;
+    a.dp[2] = dpz;
+    for (int s2 = 0; s2 < NSPEC; ++s2) a.slot_of[s2] = h->slot_of[s2];
+    a.pref_g = 2.0 * g2 / dA;
+    a.pref_q = 2.0 * CF * g2;
+    a.meas = dpx * dpy * dpz / (twopi * twopi * twopi);
+    a.limit = INT64_MAX / (h->npc > 0 ? h->npc : 1) / 2;
+    CK(h, launch_masses(a, s));
+    h->cur ^= 1;
+    h->have_masses = true;
+    return BZ_OK;
+}
+
+static void fill_terms(bz_handle h, TermDev (*terms)[MAX_TERMS], int* nterms)
+{
+    struct T {
+        int leg[4];
+        double sym;
+        int cls;
+    };
+    for (int d = 0; d < NSPEC; ++d) {
+        T t[16];
+        int n = 0;
+        auto add = [&](int a, int b, int c, int dd, double sym, int cls) {
+            t[n].leg[0] = a; t[n].leg[1] = b; t[n].leg[2] = c; t[n].leg[3] = dd;
+            t[n].sym = sym; t[n].cls = cls; ++n;
+        };
+        // Eq. (C_gluon): 1/2 gg<->gg, and per flavour g q, g qbar, q qbar <-> gg
+        if (d == 0) {
+            add(0, 0, 0, 0, 0.5, M_GG);
+            for (int f = 0; f < 3; ++f) {
+                int q = 1 + f, qb = 4 + f;
+                add(q, 0, q, 0, 1.0, M_QG);
+                add(qb, 0, qb, 0, 1.0, M_QG);
+                add(q, qb, 0, 0, 1.0, M_QQBGG);
+            }
+        } else {
+            // Eq. (C_quark); the antiquark equation is its charge conjugate.
+            // Legs are labelled so that (k1, k3) is the like-species line.
+            bool anti = d >= 4;
+            int fa = (d - 1) % 3;
+            int me = anti ? 4 + fa : 1 + fa, bar = anti ? 1 + fa : 4 + fa;
+            add(me, me, me, me, 0.5, M_QQ);
+            add(bar, me, bar, me, 1.0, M_QQB);
+            add(0, 0, bar, me, 0.5, M_QQBGG);
+            add(0, me, 0, me, 1.0, M_QG);
+            for (int fb = 0; fb < 3; ++fb) {
+                if (fb == fa) continue;
+                int Qb = anti ? 4 + fb : 1 + fb, QBb = anti ? 1 + fb : 4 + fb;
+                add(Qb, me, Qb, me, 1.0, M_QQP);
+                add(QBb, me, QBb, me, 1.0, M_QQP);
+                add(Qb, QBb, bar, me, 1.0, M_QQB2);
+            }
+        }
+        int m = 0;
+        for (int i = 0; i < n; ++i) {
+            bool ok = true;
+            for (int l = 0; l < 4; ++l)
+                if (!(h->mask & (1u << t[i].leg[l]))) ok = false;
+            if (!ok) continue;
+            TermDev& o = terms[d][m++];
+            for (int l = 0; l < 4; ++l) {
+                o.slot[l] = (int8_t)h->slot_of[t[i].leg[l]];
+                o.mslot[l] = (int8_t)mass_slot(t[i].leg[l]);
+                o.quark[l] = (int8_t)(is_quark(t[i].leg[l]) ? 1 : 0);
+            }
+            o.cls = (int8_t)t[i].cls;
+            o.sym = t[i].sym;
+        }
+        nterms[d] = m;
+    }
+}
+
+template <typename R>
+static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamples, int step, double dt,
+                         int sampler)
+{
+    const double dF = 3.0, CA = 3.0, CF = 4.0 / 3.0, dA = 8.0;
+    double g2 = 4.0 * PI * h->alpha_s;
+    double g4 = g2 * g2;
+    double twoL = 2.0 * h->g.L;
+    double V = twoL * twoL * twoL * twoL * twoL;
+    double Kq = ((V * dt) / (4.0 * (double)nsamples)) / HBARC * TWO_POW_40;
+    double twopi = 2.0 * PI;
+    double twopi5 = twopi * twopi * twopi * twopi * twopi;
+    a.f = static_cast<const R*>(h->d_freal);
+    a.A = A;
+    a.m2 = h->d_m2[h->cur];
+    a.flags = h->d_flags;
+    a.nxc = h->nxc;
+    a.npc = h->npc;
+    for (int d = 0; d < 3; ++d) {
+        a.np[d] = h->g.np[d];
+        a.dp[d] = (R)(twoL / h->g.np[d]);
+    }
+    a.L = (R)h->g.L;
+    a.twoL = (R)twoL;
+    a.key0 = (uint32_t)(h->g.seed & 0xffffffffu) ^ h->g.box;
+    a.key1 = (uint32_t)(h->g.seed >> 32);
+    a.nsamples = nsamples;
+    a.step = step;
+    a.a_stride = h->a_stride;
+    a.a_offset = h->a_offset;
+    a.n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
+    a.sampler = sampler;
+    a.mass_mode = h->mass_mode;
+    a.analytic = h->analytic;
+    a.p_center = 0;
+    a.T = (R)h->T;
+    for (int s = 0; s < NSPEC; ++s) a.mu[s] = (R)h->mu[s];
+    a.Kq = (R)Kq;
+    a.Kown = (R)(sampler == BZ_SAMPLER_PLAIN ? Kq * 4.0 : Kq);
+    a.twopi5 = (R)twopi5;
+    a.A1 = (R)(8.0 * g4 * dF * dF * CF * CF / dA);
+    a.A2 = (R)(16.0 * g4 * dF * CF * (CF - CA / 2.0));
+    a.A3 = (R)(8.0 * g4 * dF * CF * CF);
+    a.A4 = (R)(8.0 * g4 * dF * CF * CA);
+    a.A5 = (R)(16.0 * g4 * dA * CA * CA);
+    for (int s = 0; s < NSPEC; ++s) a.slot_species[s] = s < h->nslots ? h->slot_species[s] : 0;
+    // terms indexed by species d
+    TermDev terms[NSPEC][MAX_TERMS];
+    int nterms[NSPEC];
+    std::memset(terms, 0, sizeof terms);
+    fill_terms(h, terms, nterms);
+    std::memcpy(a.terms, terms, sizeof terms);
+    std::memcpy(a.nterms, nterms, sizeof nterms);
+}
+
+static int run_collide(bz_handle h, long long* A, int nsamples, int step, double dt, int prec, int sampler,
+                       cudaStream_t s)
+{
+    int64_t total_est = (h->ncell / h->a_stride + 1) * (int64_t)nsamples;
+    int64_t blocks = (total_est + 255) / 256;
+    int64_t cap = (int64_t)h->nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (prec == BZ_PREC_F64) {
+        CollideArgs<double> a{};
+        fill_collide(h, a, A, nsamples, step, dt, sampler);
+        CK(h, launch_collide_f64(a, (int)blocks, s));
+    } else {
+        CollideArgs<float> a{};
+        fill_collide(h, a, A, nsamples, step, dt, sampler);
+        CK(h, launch_collide_f32(a, (int)blocks, s));
+    }
+    return BZ_OK;
+}
+
+static const double kDeg[NSPEC] = {16.0, 6.0, 6.0, 6.0, 6.0, 6.0, 6.0};
+
+static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long* out, double dt, void* freal,
+                      int freal_double)
+{
+    a.in = in;
+    a.out = out;
+    a.freal = freal;
+    a.freal_double = freal_double;
+    a.m2 = h->d_m2[h->cur];
+    a.nxc = h->nxc;
+    a.npc = h->npc;
+    a.ncell = h->ncell;
+    for (int d = 0; d < 3; ++d) {
+        a.nx[d] = h->g.nx[d];
+        a.np[d] = h->g.np[d];
+    }
+    a.mass_mode = h->mass_mode;
+    a.dtdxf = (float)(dt / h->g.dx);
+    for (int sl = 0; sl < NSPEC; ++sl) {
+        int sp = sl < h->nslots ? h->slot_species[sl] : 0;
+        a.slot_mslot[sl] = mass_slot(sp);
+        a.deg[sl] = kDeg[sp];
+        a.inv_deg[sl] = 1.0 / kDeg[sp];
+    }
+    for (int d = 0; d < 3; ++d) {
+        double dp = dp_of(h, d);
+        for (int j = 0; j < h->g.np[d]; ++j) a.pf[d][j] = (float)(-h->g.L + ((double)j + 0.5) * dp);
+    }
+    return BZ_OK;
+}
+
+static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, double* out)
+{
+    a.state = state;
+    a.out = out;
+    a.m2 = h->d_m2[h->cur];
+    a.nxc = h->nxc;
+    a.npc = h->npc;
+    a.nslots = h->nslots;
+    a.mass_mode = h->mass_mode;
+    double dp[3];
+    for (int d = 0; d < 3; ++d) {
+        a.np[d] = h->g.np[d];
+        dp[d] = dp_of(h, d);
+        a.half_dp[d] = 0.5 * dp[d];
+        for (int j = 0; j < h->g.np[d]; ++j) a.pf[d][j] = (float)(-h->g.L + ((double)j + 0.5) * dp[d]);
+    }
+    for (int sl = 0; sl < NSPEC; ++sl) a.slot_mslot[sl] = mass_slot(sl < h->nslots ? h->slot_species[sl] : 0);
+    double twopi = 2.0 * PI;
+    a.pref = dp[0] * dp[1] * dp[2] / (twopi * twopi * twopi) * TWO_POW_M40;
+    return BZ_OK;
+}
+
+static int check_common(bz_handle h, int nsamples, int step, double dt, int prec, int sampler)
+{
+    if (nsamples <= 0) return fail(h, BZ_EINVAL, "nsamples must be positive");
+    if (step < 0 || step >= (1 << 29)) return fail(h, BZ_EINVAL, "step must be in [0, 2^29)");
+    if (!(dt > 0)) return fail(h, BZ_EINVAL, "dt must be positive");
+    if (prec != BZ_PREC_F64 && prec != BZ_PREC_F32) return fail(h, BZ_EINVAL, "bad precision %d", prec);
+    if (sampler != BZ_SAMPLER_SYMMETRIC && sampler != BZ_SAMPLER_PLAIN)
+        return fail(h, BZ_EINVAL, "bad sampler %d", sampler);
+    return BZ_OK;
+}
+
+// --------------------------------------------------------------------------
+// public entry points
+// --------------------------------------------------------------------------
+extern "C" int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples, int32_t step,
+                                 double dt, int32_t prec, int32_t sampler, void* stream)
+{
+    if (!h || !state || !A) return BZ_EINVAL;
+    int rc = check_common(h, nsamples, step, dt, prec, sampler);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long* st = reinterpret_cast<const long long*>(state);
+    if ((rc = compute_masses(h, st, s))) return rc;
+    if (!h->analytic) {
+        double deg[NSPEC];
+        for (int sl = 0; sl < NSPEC; ++sl) deg[sl] = kDeg[sl < h->nslots ? h->slot_species[sl] : 0];
+        CK(h, launch_convert(st, h->d_freal, prec == BZ_PREC_F64, h->nxc, h->npc, h->nslots, deg, s));
+    }
+    CK(h, cudaMemsetAsync(A, 0, sizeof(int64_t) * h->ncell, s));
+    return run_collide(h, reinterpret_cast<long long*>(A), nsamples, step, dt, prec, sampler, s);
+}
+
+extern "C" int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt, void* stream)
+{
+    if (!h || !in || !out) return BZ_EINVAL;
+    if (!(dt > 0)) return fail(h, BZ_EINVAL, "dt must be positive");
+    if (in == out) return fail(h, BZ_EINVAL, "in and out must not overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (!h->have_masses && h->mass_mode == BZ_MASS_THERMAL)
+        if ((rc = compute_masses(h, reinterpret_cast<const long long*>(in), s))) return rc;
+    DriftArgs a{};
+    fill_drift(h, a, reinterpret_cast<const long long*>(in), reinterpret_cast<long long*>(out), dt, nullptr, 0);
+    CK(h, launch_drift(a, s));
+    return BZ_OK;
+}
+
+extern "C" int bz_moments(bz_handle h, const int64_t* state, double* out, void* stream)
+{
+    if (!h || !state || !out) return BZ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (!h->have_masses && h->mass_mode == BZ_MASS_THERMAL)
+        if ((rc = compute_masses(h, reinterpret_cast<const long long*>(state), s))) return rc;
+    MomentArgs a{};
+    fill_moments(h, a, reinterpret_cast<const long long*>(state), out);
+    CK(h, launch_moments(a, s));
+    return BZ_OK;
+}
+
+extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, int32_t nsamples, int32_t prec,
+                       int32_t step0, double* moments_out, void* stream)
+{
+    if (!h || !state) return BZ_EINVAL;
+    if (nsteps < 0) return fail(h, BZ_EINVAL, "nsteps must be >= 0");
+    int rc = check_common(h, nsamples, step0, dt, prec, BZ_SAMPLER_SYMMETRIC);
+    if (rc) return rc;
+    if ((int64_t)step0 + nsteps > (1 << 29)) return fail(h, BZ_EINVAL, "step index overflows 2^29");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!h->d_state2 && cudaMalloc(&h->d_state2, sizeof(long long) * h->ncell) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the second state buffer");
+    long long* cur = reinterpret_cast<long long*>(state);
+    long long* nxt = h->d_state2;
+    for (int k = 0; k < nsteps; ++k) {
+        if ((rc = compute_masses(h, cur, s))) return rc;
+        DriftArgs d{};
+        fill_drift(h, d, cur, nxt, dt, h->analytic ? nullptr : h->d_freal, prec == BZ_PREC_F64);
+        CK(h, launch_drift(d, s));
+        if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, BZ_SAMPLER_SYMMETRIC, s))) return rc;
+        if (moments_out) {
+            MomentArgs m{};
+            fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5);
+            CK(h, launch_moments(m, s));
+        }
+        long long* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    if (cur != reinterpret_cast<long long*>(state))
+        CK(h, cudaMemcpyAsync(state, cur, sizeof(long long) * h->ncell, cudaMemcpyDeviceToDevice, s));
+    return BZ_OK;
+}

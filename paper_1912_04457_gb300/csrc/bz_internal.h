@@ -1,0 +1,106 @@
+// Internal host/device interface of libbz: argument blocks passed by value
+// to the kernels and the launchers each translation unit exports.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bz {
+
+constexpr int NSPEC = 7;
+constexpr int MAX_TERMS = 10;
+constexpr int MAX_NP = 256;     // momentum cells per axis
+constexpr double HBARC = 0.1973269804;
+constexpr double PI = 3.14159265358979323846;
+constexpr double TWO_POW_40 = 1099511627776.0;
+constexpr double TWO_POW_M40 = 1.0 / 1099511627776.0;
+constexpr int MASS_SHIFT = 30;
+
+enum { M_QQP = 0, M_QQ, M_QQB, M_QQB2, M_QQBGG, M_QG, M_GG };
+
+inline __host__ __device__ int mass_slot(int s) { return s == 0 ? 0 : 1 + (s - 1) % 3; }
+inline __host__ __device__ bool is_quark(int s) { return s != 0; }
+
+// One term of a species' equation: legs (k1, k2, k3, p).
+struct TermDev {
+    int8_t slot[4];   // state slot of each leg's species
+    int8_t mslot[4];  // mass slot (0 g, 1..3 flavour) of each leg
+    int8_t quark[4];  // 1 if the leg is a (anti)quark: F = 1 - f, else F = 1 + f
+    int8_t cls;       // |M|^2 row
+    int8_t pad[3];
+    double sym;       // 1/2 for identical initial particles
+};
+
+template <typename R>
+struct CollideArgs {
+    const R* f;             // f per cell [slot][x][p] (unused in equilibrium mode)
+    long long* A;           // deposit target, int64 [slot][x][p]
+    const double* m2;       // [x][4]
+    long long* flags;       // [4]
+    int64_t nxc, npc;
+    int np[3];
+    R L, twoL, dp[3];
+    uint32_t key0, key1;
+    int nsamples, step;
+    int64_t n_sel, a_stride, a_offset;
+    int sampler, mass_mode, analytic, p_center;
+    R T, mu[NSPEC];
+    R Kq, Kown, twopi5;
+    R A1, A2, A3, A4, A5;
+    int slot_species[NSPEC];
+    int nterms[NSPEC];
+    TermDev terms[NSPEC][MAX_TERMS];
+};
+
+struct MassArgs {
+    const long long* state;
+    long long* acc;         // [x][4] fixed-point sums (zeroed by the caller)
+    double* m2_out;         // [x][4]
+    const double* m2_prev;  // [x][4] or null (E = |p|)
+    long long* flags;
+    int64_t nxc, npc;
+    int np[3];
+    double L, dp[3];
+    int slot_of[NSPEC];     // -1 if inactive
+    double pref_g, pref_q, meas;
+    long long limit;
+};
+
+struct DriftArgs {
+    const long long* in;
+    long long* out;
+    void* freal;            // optional f of `in` (float or double) written alongside
+    int freal_double;
+    const double* m2;
+    int64_t nxc, npc, ncell;
+    int nx[3], np[3];
+    int mass_mode;
+    float dtdxf;
+    int slot_mslot[NSPEC];
+    double inv_deg[NSPEC];  // per slot: 1 / N_s (f = n 2^-40 / N_s in the FP64 conversion)
+    double deg[NSPEC];
+    float pf[3][MAX_NP];    // FP32 cell-centre momenta per axis
+};
+
+struct MomentArgs {
+    const long long* state;
+    double* out;            // [x][slot][5]
+    const double* m2;
+    int64_t nxc, npc;
+    int nslots;
+    int np[3];
+    int mass_mode;
+    int slot_mslot[NSPEC];
+    double pref, half_dp[3];
+    float pf[3][MAX_NP];
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
+cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
+cudaError_t launch_masses(const MassArgs& a, cudaStream_t s);
+cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s);
+cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
+cudaError_t launch_convert(const long long* state, void* freal, int as_double, int64_t nxc,
+                           int64_t npc, int nslots, const double* deg, cudaStream_t s);
+
+}  // namespace bz

@@ -1,0 +1,302 @@
+// Thermal masses, drift and moments.  Compiled with -fmad=false so the FP64
+// mass integrand and the FP32 Courant numbers round exactly as written; all
+// sums are exact integer sums, so results do not depend on the order in
+// which threads accumulate.
+#include <cstdint>
+#include "bz_internal.h"
+
+namespace bz {
+
+__device__ __forceinline__ void red_add_ll(long long* addr, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long*>(addr), static_cast<unsigned long long>(v));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long lo = (unsigned long long)v;
+        long long hi = (long long)(v >> 64);
+        unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        v += ((__int128)hi2 << 64) | (__int128)lo2;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Thermal masses, Eqs. (mg), (mq).  Per bin, in FP64 (same order as the
+// definition):  N_g C_A f_g/(2E_g) + sum_i N_q C_F (f_qi + f_qbi)/(2E_qi) and
+// 2 f_g/(2E_g) + (f_qi + f_qbi)/(2E_qi), each rounded to 2^-30 fixed point
+// and summed exactly.  Grid: one block per (x cell, chunk of 2048 bins).
+// ---------------------------------------------------------------------------
+constexpr int MASS_CHUNK = 2048;
+
+__global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs P)
+{
+    const int64_t nchunk = (P.npc + MASS_CHUNK - 1) / MASS_CHUNK;
+    const int64_t x = blockIdx.x / nchunk;
+    const int64_t c0 = (blockIdx.x % nchunk) * MASS_CHUNK;
+    const double CA = 3.0, CF = 4.0 / 3.0;
+    double m2p[4] = {0.0, 0.0, 0.0, 0.0};
+    if (P.m2_prev)
+        for (int i = 0; i < 4; ++i) m2p[i] = P.m2_prev[x * 4 + i];
+    long long sg = 0, sq[3] = {0, 0, 0};
+    bool ovf = false;
+    const double scale = (double)(1LL << MASS_SHIFT);
+    for (int64_t j = c0 + threadIdx.x; j < c0 + MASS_CHUNK && j < P.npc; j += blockDim.x) {
+        const int jx = (int)(j / ((int64_t)P.np[1] * P.np[2]));
+        const int jy = (int)((j / P.np[2]) % P.np[1]);
+        const int jz = (int)(j % P.np[2]);
+        const double px = -P.L + ((double)jx + 0.5) * P.dp[0];
+        const double py = -P.L + ((double)jy + 0.5) * P.dp[1];
+        const double pz = -P.L + ((double)jz + 0.5) * P.dp[2];
+        const double pp = (px * px + py * py) + pz * pz;
+        double fs[NSPEC];
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) {
+            const int sl = P.slot_of[s];
+            const double deg = s == 0 ? 16.0 : 6.0;
+            fs[s] = sl < 0 ? 0.0 : (double)P.state[((int64_t)sl * P.nxc + x) * P.npc + j] * TWO_POW_M40 / deg;
+        }
+        const double Eg = sqrt(pp + m2p[0]);
+        double tg = 16.0 * CA * fs[0] / (2.0 * Eg);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double Eq = sqrt(pp + m2p[1 + i]);
+            tg = tg + 6.0 * CF * (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
+        }
+        const long long qg = __double2ll_rn(tg * scale);
+        ovf |= qg > P.limit || qg < -P.limit;
+        sg += qg;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double Eq = sqrt(pp + m2p[1 + i]);
+            const double tq = 2.0 * fs[0] / (2.0 * Eg) + (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
+            const long long qq = __double2ll_rn(tq * scale);
+            ovf |= qq > P.limit || qq < -P.limit;
+            sq[i] += qq;
+        }
+    }
+    __shared__ long long red[4][8];
+    long long v[4] = {sg, sq[0], sq[1], sq[2]};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] = warp_sum(v[i]);
+        if (lane == 0) red[i][warp] = v[i];
+    }
+    if (ovf) red_add_ll(&P.flags[2], 1);
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        red_add_ll(&P.acc[x * 4 + threadIdx.x], t);
+    }
+}
+
+__global__ void k_masses_finish(const __grid_constant__ MassArgs P)
+{
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.nxc) return;
+    const double inv = 1.0 / (double)(1LL << MASS_SHIFT);
+    P.m2_out[x * 4 + 0] = P.pref_g * P.meas * ((double)P.acc[x * 4 + 0] * inv);
+    for (int i = 0; i < 3; ++i)
+        P.m2_out[x * 4 + 1 + i] = P.pref_q * P.meas * ((double)P.acc[x * 4 + 1 + i] * inv);
+}
+
+cudaError_t launch_masses(const MassArgs& a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * a.nxc, s);
+    if (e != cudaSuccess) return e;
+    const int64_t nchunk = (a.npc + MASS_CHUNK - 1) / MASS_CHUNK;
+    k_masses<<<(unsigned)(nchunk * a.nxc), 256, 0, s>>>(a);
+    k_masses_finish<<<(unsigned)((a.nxc + 127) / 128), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Drift, Eq. (left handside) in flux form: first-order upwind, periodic in
+// x.  Courant number c_d = (p_d (1/sqrt(p^2 + m^2(x)))) dt/dx in IEEE FP32,
+// held as C = rint(c 2^30); face flux = floor((n C + 2^29) / 2^30) exactly
+// (128-bit product), taken at the upwind cell and shared by both cells.
+// One thread per cell, p fastest, so every load and store is coalesced.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long courant_fx(const DriftArgs& P, int64_t x, int ms, float pdf, float ppf)
+{
+    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + ms];
+    const float inv = 1.0f / sqrtf(ppf + m);
+    const float cf = (pdf * inv) * P.dtdxf;
+    return __float2ll_rn(cf * 1073741824.0f);
+}
+
+__device__ __forceinline__ long long flux_fx(long long n, long long C)
+{
+    const __int128 prod = (__int128)n * (__int128)C + ((__int128)1 << 29);
+    return (long long)(prod >> 30);
+}
+
+__global__ void __launch_bounds__(256) k_drift(const __grid_constant__ DriftArgs P)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < P.ncell; cell += stride) {
+        const int sl = (int)(cell / (P.nxc * P.npc));
+        const int64_t x = (cell / P.npc) % P.nxc;
+        const int64_t j = cell % P.npc;
+        const int ms = P.slot_mslot[sl];
+        const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]),
+                           (int)(j % P.np[2])};
+        const float pf[3] = {P.pf[0][jv[0]], P.pf[1][jv[1]], P.pf[2][jv[2]]};
+        const float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
+        const long long nc = __ldg(&P.in[cell]);
+        const int xi[3] = {(int)(x / ((int64_t)P.nx[1] * P.nx[2])), (int)((x / P.nx[2]) % P.nx[1]),
+                           (int)(x % P.nx[2])};
+        const int64_t xs[3] = {(int64_t)P.nx[1] * P.nx[2], (int64_t)P.nx[2], 1};
+        long long acc = 0;
+        bool own_done = false;
+        long long own_C[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (P.nx[d] == 1) continue;
+            if (!own_done) {
+                const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + ms];
+                const float inv = 1.0f / sqrtf(ppf + m);
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+                    own_C[e] = __float2ll_rn(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
+                own_done = true;
+            }
+            long long fplus, fminus;
+            if (pf[d] > 0.0f) {
+                const int64_t xl = x + (int64_t)((xi[d] == 0 ? P.nx[d] - 1 : -1)) * xs[d];
+                fplus = flux_fx(nc, own_C[d]);
+                fminus = flux_fx(__ldg(&P.in[cell + (xl - x) * P.npc]), courant_fx(P, xl, ms, pf[d], ppf));
+            } else {
+                const int64_t xh = x + (int64_t)((xi[d] == P.nx[d] - 1 ? 1 - P.nx[d] : 1)) * xs[d];
+                fplus = flux_fx(__ldg(&P.in[cell + (xh - x) * P.npc]), courant_fx(P, xh, ms, pf[d], ppf));
+                fminus = flux_fx(nc, own_C[d]);
+            }
+            acc += fplus - fminus;
+        }
+        P.out[cell] = nc - acc;
+        if (P.freal) {
+            if (P.freal_double)
+                static_cast<double*>(P.freal)[cell] = (double)nc * TWO_POW_M40 / P.deg[sl];
+            else
+                static_cast<float*>(P.freal)[cell] = __ll2float_rn(nc) * (float)(TWO_POW_M40 * P.inv_deg[sl]);
+        }
+    }
+}
+
+cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (a.ncell + 255) / 256;
+    const int64_t cap = (int64_t)nsm * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_drift<<<(unsigned)blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// f of the state for the collision lookups: f = n 2^-40 / N_s (FP64) or its
+// FP32 rounding.
+// ---------------------------------------------------------------------------
+__global__ void k_convert(const long long* state, void* freal, int as_double, int64_t nxc, int64_t npc,
+                          int nslots, double deg0, double deg1, double deg2, double deg3, double deg4,
+                          double deg5, double deg6)
+{
+    const double degs[NSPEC] = {deg0, deg1, deg2, deg3, deg4, deg5, deg6};
+    const int64_t n = (int64_t)nslots * nxc * npc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int sl = (int)(i / (nxc * npc));
+        const long long v = state[i];
+        if (as_double)
+            static_cast<double*>(freal)[i] = (double)v * TWO_POW_M40 / degs[sl];
+        else
+            static_cast<float*>(freal)[i] = __ll2float_rn(v) * (float)(TWO_POW_M40 / degs[sl]);
+    }
+}
+
+cudaError_t launch_convert(const long long* state, void* freal, int as_double, int64_t nxc, int64_t npc,
+                           int nslots, const double* deg, cudaStream_t s)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t n = (int64_t)nslots * nxc * npc;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)nsm * 8) blocks = (int64_t)nsm * 8;
+    if (blocks < 1) blocks = 1;
+    k_convert<<<(unsigned)blocks, 256, 0, s>>>(state, freal, as_double, nxc, npc, nslots, deg[0], deg[1],
+                                               deg[2], deg[3], deg[4], deg[5], deg[6]);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Moments, Eqs. (particle numbers), (energy momentum tensor): one block per
+// (x cell, slot); exact 128-bit integer sums of n, E_fx n and (2j+1-n) n.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double i128_to_double(__int128 v)
+{
+    return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
+}
+
+__global__ void __launch_bounds__(256) k_moments(const __grid_constant__ MomentArgs P)
+{
+    const int64_t x = blockIdx.x / P.nslots;
+    const int sl = blockIdx.x % P.nslots;
+    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
+    const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
+    __int128 v[5] = {0, 0, 0, 0, 0};
+    for (int64_t j = threadIdx.x; j < P.npc; j += blockDim.x) {
+        const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]),
+                           (int)(j % P.np[2])};
+        const float pf0 = P.pf[0][jv[0]], pf1 = P.pf[1][jv[1]], pf2 = P.pf[2][jv[2]];
+        const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
+        const long long Efx = __float2ll_rn(sqrtf(ppf + m) * 16777216.0f);
+        const long long n = __ldg(&st[j]);
+        v[0] += n;
+        v[1] += (__int128)Efx * n;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[2 + d] += (__int128)(2 * jv[d] + 1 - P.np[d]) * n;
+    }
+    __shared__ __int128 red[5][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        v[i] = warp_sum_i128(v[i]);
+        if (lane == 0) red[i][warp] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 t[5] = {0, 0, 0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            for (int i = 0; i < 5; ++i) t[i] += red[i][w];
+        double* o = P.out + (x * P.nslots + sl) * 5;
+        o[0] = i128_to_double(t[0]) * P.pref;
+        o[1] = i128_to_double(t[1]) * P.pref * (1.0 / 16777216.0);
+        for (int d = 0; d < 3; ++d) o[2 + d] = i128_to_double(t[2 + d]) * P.pref * P.half_dp[d];
+    }
+}
+
+cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s)
+{
+    k_moments<<<(unsigned)(a.nxc * a.nslots), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bz
