@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Throughput of the MC 2->2 collision term with symmetrical sampling + drift.
+
+One step = one pass of the whole hot path on the workload: thermal masses,
+drift (+ f for the lookups), collision sampling and deposition (FP32
+integrand with FP64 re-evaluation of ill-conditioned terms), moments.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bz|reference]
+                  [--workload qgp|gluon_step|gluon_bump]
+
+Prints one JSON line (rank 0).  Metric: collision samples/s, a sample being
+one (species, x cell, p cell, sample) anchor evaluated over all terms of its
+species' equation.  The reference arm (--impl reference) is the FP64 CPU
+oracle on a bounded sample of anchors of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collision samples/s and cell-updates/s vs plain FP64 GPU path at equal MC error"
+L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+# algorithmic FP32 operations (add, sub, mul, div, sqrt each 1) of the formula:
+FLOP_PER_SAMPLE = 60           # jitter, k1_perp, k3, |p|^2, |k3|^2, P, a^2, b^2, bin of k3
+FLOP_PER_TERM = 29             # Ep, E3, D, kappa, H, sqrt(H), Q, two root candidates
+FLOP_PER_ROOT = 81             # validity, E1, E2, J, s, t, u, |M|^2, three bins, W, c~, weight
+
+
+def workloads():
+    from paper_1912_04457_gb300 import inputs as I
+    return {"qgp": I.qgp_box, "gluon_step": I.gluon_step_box, "gluon_bump": I.gluon_bump_xp}
+
+
+def describe(w):
+    return {"workload": w.name, "species": w.nslots, "x_cells": w.nxc, "p_grid": list(w.np_),
+            "L_GeV": w.L, "samples_per_cell": w.nsamples, "dt_fm": w.dt, "alpha_s": w.alpha_s,
+            "anchors_per_step": w.nslots * w.nxc * w.npc, "l2": "flushed between timed steps",
+            "initial_state": "synthetic closed form (seeded)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("collide.cuh", "k_collide_f32.cu", "bz_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1912_04457_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per collision launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "collide_%s_traffic.json" % workload)
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def term_counts(w):
+    """(term evaluations, terms per anchor averaged) of one step."""
+    from paper_1912_04457_gb300 import inputs as I
+    per_species = []
+    for s in I.slots(w.species_mask):
+        per_species.append(_nterms(s, w.species_mask))
+    anchors_per_slot = w.nxc * w.npc
+    return sum(per_species) * anchors_per_slot * w.nsamples
+
+
+def _nterms(d, mask):
+    """Number of terms of species d's equation whose four species are all active."""
+    def active(*ss):
+        return all(mask & (1 << s) for s in ss)
+    n = 0
+    if d == 0:
+        n += active(0)
+        for f in range(3):
+            q, qb = 1 + f, 4 + f
+            n += active(q, 0) + active(qb, 0) + active(q, qb)
+    else:
+        anti = d >= 4
+        fa = (d - 1) % 3
+        me, bar = (4 + fa, 1 + fa) if anti else (1 + fa, 4 + fa)
+        n += active(me) + active(bar, me) + active(0, bar, me) + active(0, me)
+        for fb in range(3):
+            if fb == fa:
+                continue
+            Qb, QBb = (4 + fb, 1 + fb) if anti else (1 + fb, 4 + fb)
+            n += active(Qb, me) + active(QBb, me) + active(Qb, QBb, bar, me)
+    return n
+
+
+def oracle_sample(w, target_s, step=0):
+    """Times the oracle's step pieces on an anchor subset sized to ~target_s.
+    Returns (samples/s, anchors, cores, seconds, accepted roots per term-eval)."""
+    import numpy as np
+    import oracle as O
+    cfg = O.make_config(nx=w.nx, dx=w.dx, np_=w.np_, L=w.L, seed=w.seed,
+                        species_mask=w.species_mask, alpha_s=w.alpha_s)
+    st = w.state()
+    total = st.size
+    m2 = O.masses(cfg, st)
+    stride = max(1, total // 64)
+    t0 = time.perf_counter()
+    r = O.collision(cfg, st, m2, w.nsamples, step=step, dt=w.dt, anchor_stride=stride,
+                    want_audit=True)
+    dt0 = time.perf_counter() - t0
+    n0 = (total + stride - 1) // stride
+    rate = n0 / max(dt0, 1e-6)
+    n_target = max(n0, int(rate * target_s))
+    stride = max(1, total // n_target)
+    t0 = time.perf_counter()
+    m2 = O.masses(cfg, st)
+    r = O.collision(cfg, st, m2, w.nsamples, step=step, dt=w.dt, anchor_stride=stride,
+                    want_audit=True)
+    if w.nxc > 1:
+        O.drift(cfg, st, m2, w.dt)
+    O.moments(cfg, st, m2)
+    secs = time.perf_counter() - t0
+    anchors = (total + stride - 1) // stride
+    terms = term_counts(w) * anchors / total
+    roots_per_term = float(r["audit"][5]) / max(terms, 1)
+    return anchors * w.nsamples / secs, anchors, O.num_threads(), secs, roots_per_term, stride
+
+
+def run_reference(args):
+    """FP64 CPU oracle as the reference arm, on a bounded sample of anchors."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle.build import build_oracle
+    build_oracle()
+    w = workloads()[args.workload]()
+    per_step = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        rate, anchors, cores, secs, _, stride = oracle_sample(w, 2.0, step=k)
+        if k >= args.warmup:
+            per_step.append((anchors * w.nsamples, secs))
+            info = (anchors, cores, stride)
+    samples = sum(s for s, _ in per_step)
+    secs = sum(t for _, t in per_step)
+    value = samples / secs
+    anchors, cores, stride = info
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / len(per_step), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": "every %d-th anchor (%d of %d) of one step per timed step, "
+                                       "plus full-grid masses and moments" %
+                                       (stride, anchors, w.nslots * w.nxc * w.npc)},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_bz(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    from paper_1912_04457_gb300 import build as B
+    B.build()
+    from paper_1912_04457_gb300 import bz
+    from paper_1912_04457_gb300 import inputs as I
+
+    mk = workloads()[args.workload]
+    w = mk(seed=mk().seed + 1000 * rank) if world > 1 else mk()
+    prec = bz.PREC_F32 if args.prec == "f32" else bz.PREC_F64
+    h = bz.Handle(nx=w.nx, dx=w.dx, np_=w.np_, L=w.L, seed=w.seed, species_mask=w.species_mask,
+                  alpha_s=w.alpha_s)
+    host_state = torch.from_numpy(w.state().reshape(-1)).pin_memory()
+    state = host_state.cuda()
+    mom = torch.empty(w.nxc * w.nslots * 5, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for k in range(args.warmup):
+        h.step(state, w.dt, 1, w.nsamples, prec, step0=k, moments_out=mom)
+    barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    h.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        h.step(state, w.dt, 1, w.nsamples, prec, step0=args.warmup + k, moments_out=mom)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    prof = h.profile_read()
+    h.profile(False)
+    clk = clocks.stop()
+    t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_max = t_steps
+    if world > 1:
+        t = torch.tensor([t_steps], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+
+    anchors = w.nslots * w.nxc * w.npc
+    samples_step = anchors * w.nsamples
+    value = samples_step * args.steps * world / t_max
+    cell_updates = anchors * args.steps * world / t_max
+
+    # e2e through the public API with host buffers
+    n_e2e = min(args.steps, 5)
+    out_host = torch.empty_like(host_state).pin_memory()
+    mom_host = torch.empty(mom.numel(), dtype=torch.float64).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(n_e2e):
+        state.copy_(host_state, non_blocking=True)
+        h.step(state, w.dt, 1, w.nsamples, prec, step0=1000 + k, moments_out=mom)
+        out_host.copy_(state, non_blocking=True)
+        mom_host.copy_(mom, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    e2e_value = samples_step * n_e2e * world / t_e2e
+
+    result = None
+    if rank == 0:
+        coll_ms, coll_n = prof["collide"]
+        launches = (2 * prof["masses"][1] + prof["drift"][1] + prof["collide"][1] + prof["fixup"][1]
+                    + prof["moments"][1] + prof["convert"][1])
+        # algorithmic work of one collision launch
+        cpu_rate, cpu_anchors, cores, cpu_secs, roots_per_term, cpu_stride = (None,) * 6
+        if not args.no_cpu_baseline and world == 1:
+            cpu_rate, cpu_anchors, cores, cpu_secs, roots_per_term, cpu_stride = oracle_sample(w, 15.0)
+        terms = term_counts(w)
+        rpt = roots_per_term if roots_per_term is not None else 0.36
+        flops = FLOP_PER_SAMPLE * samples_step + FLOP_PER_TERM * terms + FLOP_PER_ROOT * rpt * terms
+        coll_s = coll_ms / 1e3 / max(coll_n, 1)
+        achieved = flops / coll_s / 1e12
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.get("sm_mhz") or 1447.0
+        peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
+        traffic = ncu_traffic(args.workload)
+
+        # the plain FP64 GPU path on the same workload (one step, same samples)
+        fp64 = None
+        if not args.no_fp64:
+            h.step(state, w.dt, 1, w.nsamples, bz.PREC_F64, step0=2000)
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.step(state, w.dt, 1, w.nsamples, bz.PREC_F64, step0=2001, moments_out=mom)
+            b.record(stream)
+            barrier()
+            t64 = a.elapsed_time(b) / 1e3
+            fp64 = {"samples_per_s": samples_step / t64, "ms_per_step": 1e3 * t64,
+                    "speedup_at_equal_samples": (samples_step / t64) and value / (samples_step / t64),
+                    "note": "FP32 path evaluates the same Philox samples; its deviation from the "
+                            "FP64 estimate (<= 2e-5 relative L2) is far below the MC error, so equal "
+                            "samples means equal MC error"}
+
+        result = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == bz.PREC_F32 else "f64", "data": "synthetic",
+            "config": describe(w),
+            "cell_updates_per_s": cell_updates,
+            "wall_s_timed_loop": wall,
+            "kernel_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_collide<float> (FP32 pipe)",
+                         "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop (FMA) x %.0f MHz sampled "
+                                       "median SM clock" % (nsm, mhz),
+                         "work_basis": "%d flop/sample + %d flop/term + %d flop/accepted root, "
+                                       "%.3f accepted roots per term evaluation (oracle audit)" %
+                                       (FLOP_PER_SAMPLE, FLOP_PER_TERM, FLOP_PER_ROOT, rpt)},
+            "cpu_baseline": None if cpu_rate is None else {
+                "value": cpu_rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                "sample": "one step of the same workload on every %d-th anchor (%d anchors x %d "
+                          "samples, %.1f s)" % (cpu_stride, cpu_anchors, w.nsamples, cpu_secs)},
+            "e2e": {"value": e2e_value, "unit": "samples/s",
+                    "h2d_bytes_per_step": host_state.numel() * 8,
+                    "d2h_bytes_per_step": host_state.numel() * 8 + mom.numel() * 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "fp64_gpu_path": fp64,
+        }
+        print(json.dumps(result), flush=True)
+    h.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bz", choices=["bz", "reference"])
+    ap.add_argument("--workload", default="qgp", choices=["qgp", "gluon_step", "gluon_bump"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_bz(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

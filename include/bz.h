@@ -160,6 +160,23 @@ int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset);
  * instead of the bin value of the state. */
 int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host);
 
+/* Per-kernel timing of this handle's own launches (CUDA events recorded on
+ * the caller's stream around each launch while enabled).  Kernel ids:
+ * BZ_K_MASSES, BZ_K_DRIFT, BZ_K_COLLIDE, BZ_K_FIXUP, BZ_K_MOMENTS,
+ * BZ_K_CONVERT.  bz_profile(h, 1) clears and starts, bz_profile(h, 0) stops;
+ * bz_profile_read synchronises the device and returns, for the first n ids,
+ * the summed milliseconds (host double [n]) and launch counts (host int64
+ * [n]); either pointer may be NULL. */
+#define BZ_K_MASSES 0
+#define BZ_K_DRIFT 1
+#define BZ_K_COLLIDE 2
+#define BZ_K_FIXUP 3
+#define BZ_K_MOMENTS 4
+#define BZ_K_CONVERT 5
+#define BZ_NKERNELS 6
+int bz_profile(bz_handle h, int enable);
+int bz_profile_read(bz_handle h, double* ms_host, int64_t* launches_host, int32_t n);
+
 /* Library version string. */
 const char* bz_version(void);
 

@@ -17,6 +17,7 @@ BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA, BZ_EOVERFLOW, BZ_ENODEV = 0, -1, -2, -3, 
 PREC_F64, PREC_F32 = 0, 1
 SAMPLER_SYMMETRIC, SAMPLER_PLAIN = 0, 1
 MASS_THERMAL, MASS_MASSLESS, MASS_FIXED = 0, 1, 2
+KERNELS = ("masses", "drift", "collide", "fixup", "moments", "convert")
 
 
 class BzGrid(C.Structure):
@@ -51,6 +52,8 @@ SIGNATURES = {
     "bz_clear_flags": (C.c_int, [_P]),
     "bz_set_anchor_subset": (C.c_int, [_P, _I64, _I64]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
+    "bz_profile": (C.c_int, [_P, C.c_int]),
+    "bz_profile_read": (C.c_int, [_P, _P, _P, _I32]),
     "bz_version": (C.c_char_p, []),
 }
 
@@ -166,6 +169,18 @@ class Handle:
 
     def clear_flags(self):
         self._check(self.lib.bz_clear_flags(self.h))
+
+    def profile(self, enable=True):
+        self._check(self.lib.bz_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel: (ms summed, launches)} of this handle's launches while profiling."""
+        n = len(KERNELS)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        self._check(self.lib.bz_profile_read(self.h, ms.ctypes.data_as(C.c_void_p),
+                                             cnt.ctypes.data_as(C.c_void_p), n))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
 
     # -- the hot path -------------------------------------------------------
     def collision_term(self, state, A, nsamples, step=0, dt=0.01, prec=PREC_F64,

@@ -9,6 +9,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/bz.h"
 #include "bz_internal.h"
@@ -33,6 +35,15 @@ struct bz_handle_s {
     long long* d_flags = nullptr;
     void* d_freal = nullptr;       // f of the state, double-sized
     long long* d_state2 = nullptr; // second state buffer for bz_step
+    int* d_qcount = nullptr;       // FP32 deferral queue: per-warp counts
+    unsigned long long* d_qitems = nullptr;
+    int64_t q_warps = 0, q_items = 0;
+    // opt-in per-kernel timing: event pairs recorded around each launch
+    bool prof = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    double prof_ms[BZ_NKERNELS] = {0};
+    int64_t prof_n[BZ_NKERNELS] = {0};
     int analytic = 0;
     double T = 0.5;
     double mu[NSPEC] = {0};
@@ -63,6 +74,52 @@ static int fail(bz_handle h, int code, const char* fmt, ...)
             return fail((h), BZ_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
     } while (0)
 
+// Timing scope around one launch (no-op unless profiling is enabled).
+struct ProfScope {
+    bz_handle h;
+    int id;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(bz_handle h_, int id_, cudaStream_t s_) : h(h_), id(id_), s(s_)
+    {
+        if (!h->prof) return;
+        e0 = take();
+        e1 = take();
+        cudaEventRecord(e0, s);
+    }
+    cudaEvent_t take()
+    {
+        cudaEvent_t e;
+        if (!h->prof_free.empty()) {
+            e = h->prof_free.back();
+            h->prof_free.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    }
+    ~ProfScope()
+    {
+        if (!h->prof) return;
+        cudaEventRecord(e1, s);
+        h->prof_pending.push_back({id, {e0, e1}});
+    }
+};
+
+static void prof_drain(bz_handle h)
+{
+    for (auto& p : h->prof_pending) {
+        float ms = 0;
+        cudaEventSynchronize(p.second.second);
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+        h->prof_ms[p.first] += ms;
+        h->prof_n[p.first] += 1;
+        h->prof_free.push_back(p.second.first);
+        h->prof_free.push_back(p.second.second);
+    }
+    h->prof_pending.clear();
+}
+
 static void free_scratch(bz_handle h)
 {
     cudaFree(h->d_m2[0]);
@@ -71,6 +128,11 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_flags);
     cudaFree(h->d_freal);
     cudaFree(h->d_state2);
+    cudaFree(h->d_qcount);
+    cudaFree(h->d_qitems);
+    h->d_qcount = nullptr;
+    h->d_qitems = nullptr;
+    h->q_warps = h->q_items = 0;
     h->d_m2[0] = h->d_m2[1] = nullptr;
     h->d_acc = h->d_flags = h->d_state2 = nullptr;
     h->d_freal = nullptr;
@@ -161,10 +223,37 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
     return BZ_OK;
 }
 
+extern "C" int bz_profile(bz_handle h, int enable)
+{
+    if (!h) return BZ_EINVAL;
+    if (enable) {
+        prof_drain(h);
+        for (int i = 0; i < BZ_NKERNELS; ++i) {
+            h->prof_ms[i] = 0;
+            h->prof_n[i] = 0;
+        }
+    }
+    h->prof = enable != 0;
+    return BZ_OK;
+}
+
+extern "C" int bz_profile_read(bz_handle h, double* ms_host, int64_t* launches_host, int32_t n)
+{
+    if (!h || n < 0) return BZ_EINVAL;
+    prof_drain(h);
+    for (int i = 0; i < n && i < BZ_NKERNELS; ++i) {
+        if (ms_host) ms_host[i] = h->prof_ms[i];
+        if (launches_host) launches_host[i] = h->prof_n[i];
+    }
+    return BZ_OK;
+}
+
 extern "C" int bz_destroy(bz_handle h)
 {
     if (!h) return BZ_EINVAL;
     cudaDeviceSynchronize();
+    prof_drain(h);
+    for (cudaEvent_t e : h->prof_free) cudaEventDestroy(e);
     free_scratch(h);
     delete h;
     return BZ_OK;
@@ -291,7 +380,10 @@ static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)
     a.pref_q = 2.0 * CF * g2;
     a.meas = dpx * dpy * dpz / (twopi * twopi * twopi);
     a.limit = INT64_MAX / (h->npc > 0 ? h->npc : 1) / 2;
-    CK(h, launch_masses(a, s));
+    {
+        ProfScope ps(h, BZ_K_MASSES, s);
+        CK(h, launch_masses(a, s));
+    }
     h->cur ^= 1;
     h->have_masses = true;
     return BZ_OK;
@@ -369,7 +461,13 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     double Kq = ((V * dt) / (4.0 * (double)nsamples)) / HBARC * TWO_POW_40;
     double twopi = 2.0 * PI;
     double twopi5 = twopi * twopi * twopi * twopi * twopi;
-    a.f = static_cast<const R*>(h->d_freal);
+    a.f = h->d_freal;
+    a.f_is_float = sizeof(R) == 4 ? 1 : 0;
+    a.ubits = sizeof(R) == 4 ? 23 : 32;
+    a.tau = 0;
+    a.qcount = nullptr;
+    a.qitems = nullptr;
+    a.qcap = 0;
     a.A = A;
     a.m2 = h->d_m2[h->cur];
     a.flags = h->d_flags;
@@ -415,19 +513,56 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
 static int run_collide(bz_handle h, long long* A, int nsamples, int step, double dt, int prec, int sampler,
                        cudaStream_t s)
 {
-    int64_t total_est = (h->ncell / h->a_stride + 1) * (int64_t)nsamples;
-    int64_t blocks = (total_est + 255) / 256;
+    const int64_t n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
+    const int64_t total = n_sel * (int64_t)nsamples;
+    int64_t blocks = (total + 255) / 256;
     int64_t cap = (int64_t)h->nsm * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     if (prec == BZ_PREC_F64) {
         CollideArgs<double> a{};
         fill_collide(h, a, A, nsamples, step, dt, sampler);
+        ProfScope ps(h, BZ_K_COLLIDE, s);
         CK(h, launch_collide_f64(a, (int)blocks, s));
-    } else {
-        CollideArgs<float> a{};
-        fill_collide(h, a, A, nsamples, step, dt, sampler);
+        return BZ_OK;
+    }
+    // FP32 integrand; ill-conditioned terms queued per warp for FP64.
+    const int64_t warps = blocks * 8;
+    const int64_t items_per_warp = ((total + blocks * 256 - 1) / (blocks * 256)) * 32;
+    const int64_t qcap = items_per_warp * MAX_TERMS / 50 + 64;  // 2% of the warp's term evaluations
+    if (warps > h->q_warps || warps * qcap > h->q_items) {
+        cudaFree(h->d_qcount);
+        cudaFree(h->d_qitems);
+        h->d_qcount = nullptr;
+        h->d_qitems = nullptr;
+        h->q_warps = h->q_items = 0;
+        if (cudaMalloc(&h->d_qcount, sizeof(int) * warps) != cudaSuccess ||
+            cudaMalloc(&h->d_qitems, sizeof(unsigned long long) * warps * qcap) != cudaSuccess)
+            return fail(h, BZ_ENOMEM, "cannot allocate the FP32 deferral queue (%lld items)",
+                        (long long)(warps * qcap));
+        h->q_warps = warps;
+        h->q_items = warps * qcap;
+    }
+    CollideArgs<float> a{};
+    fill_collide(h, a, A, nsamples, step, dt, sampler);
+    a.tau = (float)DEFER_TAU;
+    a.qcount = h->d_qcount;
+    a.qitems = h->d_qitems;
+    a.qcap = qcap;
+    {
+        ProfScope ps(h, BZ_K_COLLIDE, s);
         CK(h, launch_collide_f32(a, (int)blocks, s));
+    }
+    CollideArgs<double> b{};
+    fill_collide(h, b, A, nsamples, step, dt, sampler);
+    b.f_is_float = 1;
+    b.ubits = 23;
+    b.qcount = h->d_qcount;
+    b.qitems = h->d_qitems;
+    b.qcap = qcap;
+    {
+        ProfScope ps(h, BZ_K_FIXUP, s);
+        CK(h, launch_fixup(b, (int)warps, s));
     }
     return BZ_OK;
 }
@@ -488,7 +623,7 @@ static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, doub
 
 static int check_common(bz_handle h, int nsamples, int step, double dt, int prec, int sampler)
 {
-    if (nsamples <= 0) return fail(h, BZ_EINVAL, "nsamples must be positive");
+    if (nsamples <= 0 || nsamples > MAX_SAMPLES) return fail(h, BZ_EINVAL, "nsamples must be in [1, 2^20]");
     if (step < 0 || step >= (1 << 29)) return fail(h, BZ_EINVAL, "step must be in [0, 2^29)");
     if (!(dt > 0)) return fail(h, BZ_EINVAL, "dt must be positive");
     if (prec != BZ_PREC_F64 && prec != BZ_PREC_F32) return fail(h, BZ_EINVAL, "bad precision %d", prec);
@@ -512,6 +647,7 @@ extern "C" int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, 
     if (!h->analytic) {
         double deg[NSPEC];
         for (int sl = 0; sl < NSPEC; ++sl) deg[sl] = kDeg[sl < h->nslots ? h->slot_species[sl] : 0];
+        ProfScope ps(h, BZ_K_CONVERT, s);
         CK(h, launch_convert(st, h->d_freal, prec == BZ_PREC_F64, h->nxc, h->npc, h->nslots, deg, s));
     }
     CK(h, cudaMemsetAsync(A, 0, sizeof(int64_t) * h->ncell, s));
@@ -529,7 +665,10 @@ extern "C" int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt,
         if ((rc = compute_masses(h, reinterpret_cast<const long long*>(in), s))) return rc;
     DriftArgs a{};
     fill_drift(h, a, reinterpret_cast<const long long*>(in), reinterpret_cast<long long*>(out), dt, nullptr, 0);
-    CK(h, launch_drift(a, s));
+    {
+        ProfScope ps(h, BZ_K_DRIFT, s);
+        CK(h, launch_drift(a, s));
+    }
     return BZ_OK;
 }
 
@@ -542,7 +681,10 @@ extern "C" int bz_moments(bz_handle h, const int64_t* state, double* out, void* 
         if ((rc = compute_masses(h, reinterpret_cast<const long long*>(state), s))) return rc;
     MomentArgs a{};
     fill_moments(h, a, reinterpret_cast<const long long*>(state), out);
-    CK(h, launch_moments(a, s));
+    {
+        ProfScope ps(h, BZ_K_MOMENTS, s);
+        CK(h, launch_moments(a, s));
+    }
     return BZ_OK;
 }
 
@@ -563,11 +705,15 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
         if ((rc = compute_masses(h, cur, s))) return rc;
         DriftArgs d{};
         fill_drift(h, d, cur, nxt, dt, h->analytic ? nullptr : h->d_freal, prec == BZ_PREC_F64);
-        CK(h, launch_drift(d, s));
+        {
+            ProfScope ps(h, BZ_K_DRIFT, s);
+            CK(h, launch_drift(d, s));
+        }
         if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, BZ_SAMPLER_SYMMETRIC, s))) return rc;
         if (moments_out) {
             MomentArgs m{};
             fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5);
+            ProfScope ps(h, BZ_K_MOMENTS, s);
             CK(h, launch_moments(m, s));
         }
         long long* t = cur;

@@ -32,7 +32,9 @@ struct TermDev {
 
 template <typename R>
 struct CollideArgs {
-    const R* f;             // f per cell [slot][x][p] (unused in equilibrium mode)
+    const void* f;          // f per cell [slot][x][p] (unused in equilibrium mode)
+    int f_is_float;         // f holds float (1) or double (0)
+    int ubits;              // uniforms: 32-bit (FP64 path) or 23-bit (FP32 path and its fixup)
     long long* A;           // deposit target, int64 [slot][x][p]
     const double* m2;       // [x][4]
     long long* flags;       // [4]
@@ -49,6 +51,11 @@ struct CollideArgs {
     int slot_species[NSPEC];
     int nterms[NSPEC];
     TermDev terms[NSPEC][MAX_TERMS];
+    // FP32 path: terms with |H| < tau kappa^2 are queued per warp for FP64
+    R tau;                          // 0: never defer
+    int* qcount;                    // [warps] items queued by each warp
+    unsigned long long* qitems;     // [warps][qcap] packed (anchor << 24 | sample << 4 | term)
+    long long qcap;
 };
 
 struct MassArgs {
@@ -97,6 +104,9 @@ struct MomentArgs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
+cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
+constexpr double DEFER_TAU = 2e-3;
+constexpr int MAX_SAMPLES = 1 << 20;
 cudaError_t launch_masses(const MassArgs& a, cudaStream_t s);
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);

@@ -1,4 +1,4 @@
-// Collision kernel, templated on the integrand precision R (double: the
+// Collision kernels, templated on the integrand precision R (double: the
 // FP64 path, compiled without FMA contraction so every operation matches
 // the written formula order; float: the FP32 path).
 //
@@ -13,6 +13,14 @@
 // q = rint(c~ K) goes +q to (d, p) and (c, k3) and -q to (a, k1), (b, k2).
 // The +q of the anchor cell is summed in registers and over the warp
 // (exact int64), the other legs use 64-bit global reductions.
+//
+// FP32 conditioning: near the tangency of the k1_perp line to the energy
+// ellipsoid the discriminant H = kappa^2 - a^2 D is a small difference of
+// O(E^4) numbers and the integrand goes like 1/sqrt(H), so FP32 rounding
+// of the inputs alone gives O(eps kappa^2 / H) relative error.  The FP32
+// kernel therefore queues every term with |H| < tau kappa^2 (about 0.4% of
+// them at tau = 2e-3) and k_fixup re-evaluates those in FP64 from the same
+// Philox counter; deposits are still exact integers.
 #pragma once
 #include <cstdint>
 #include "bz_internal.h"
@@ -39,8 +47,11 @@ template <> struct Ops<double> {
     static __device__ __forceinline__ double fabs_(double x) { return fabs(x); }
     static __device__ __forceinline__ double exp_(double x) { return exp(x); }
     static __device__ __forceinline__ long long rint_(double x) { return __double2ll_rn(x); }
-    // u = (x + 1/2) 2^-32
-    static __device__ __forceinline__ double unif(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+    // u = (x + 1/2) 2^-32, or ((x >> 9) + 1/2) 2^-23 when re-evaluating FP32 samples
+    static __device__ __forceinline__ double unif(uint32_t x, int ubits)
+    {
+        return ubits == 23 ? ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0) : ((double)x + 0.5) * (1.0 / 4294967296.0);
+    }
     static constexpr double LIM = 4611686018427387904.0;  // 2^62
 };
 template <> struct Ops<float> {
@@ -50,7 +61,7 @@ template <> struct Ops<float> {
     static __device__ __forceinline__ float exp_(float x) { return expf(x); }
     static __device__ __forceinline__ long long rint_(float x) { return __float2ll_rn(x); }
     // u = ((x >> 9) + 1/2) 2^-23, exact in FP32
-    static __device__ __forceinline__ float unif(uint32_t x) { return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f); }
+    static __device__ __forceinline__ float unif(uint32_t x, int) { return ((float)(x >> 9) + 0.5f) * (1.0f / 8388608.0f); }
     static constexpr float LIM = 4611686018427387904.0f;
 };
 
@@ -96,6 +107,13 @@ __device__ __forceinline__ R f_equilibrium(const CollideArgs<R>& P, int s, R E)
     return is_quark(s) ? R(1) / (Ops<R>::exp_(x) + R(1)) : R(1) / (Ops<R>::exp_(x) - R(1));
 }
 
+template <typename R>
+__device__ __forceinline__ R load_f(const CollideArgs<R>& P, int64_t i)
+{
+    return P.f_is_float ? (R)__ldg(static_cast<const float*>(P.f) + i)
+                        : (R)__ldg(static_cast<const double*>(P.f) + i);
+}
+
 __device__ __forceinline__ void red_add(long long* addr, long long v)
 {
     atomicAdd(reinterpret_cast<unsigned long long*>(addr), static_cast<unsigned long long>(v));
@@ -108,164 +126,244 @@ __device__ __forceinline__ long long warp_sum_ll(long long v)
     return v;
 }
 
+// Everything of one sample that does not depend on the term.
 template <typename R>
-__global__ void __launch_bounds__(256) k_collide(const __grid_constant__ CollideArgs<R> P)
+struct Geom {
+    int64_t x, xoff, lin3;
+    int d;
+    R p[3], k3[3], k1x, k1y, pp, kk3, Pz, PP, bx, by, a2m, b2m;
+    bool k2xy_in;
+    R mdisp[4], mg2;
+};
+
+template <typename R>
+__device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, int smp, Geom<R>& G)
 {
     using O = Ops<R>;
-    const int64_t total = P.n_sel * (int64_t)P.nsamples;
-    const int lane = threadIdx.x & 31;
-    const bool warp_anchor = (P.nsamples & 31) == 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const R L = P.L, twoL = P.twoL;
     const int64_t nxc = P.nxc, npc = P.npc;
+    const int sl = (int)(a / (nxc * npc));
+    const int64_t x = (a / npc) % nxc;
+    const int64_t j = a % npc;
+    G.x = x;
+    G.xoff = x * npc;
+    G.d = P.slot_species[sl];
+    const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]), (int)(j % P.np[2])};
+    const uint32_t ctr3 = ((uint32_t)P.step << 3) | (uint32_t)G.d;
+    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    const R u[8] = {O::unif(r0.x, P.ubits), O::unif(r0.y, P.ubits), O::unif(r0.z, P.ubits), O::unif(r0.w, P.ubits),
+                    O::unif(r1.x, P.ubits), O::unif(r1.y, P.ubits), O::unif(r1.z, P.ubits), O::unif(r1.w, P.ubits)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R pc = -L + ((R)jv[i] + R(0.5)) * P.dp[i];
+        G.p[i] = P.p_center ? pc : pc + P.dp[i] * (u[i] - R(0.5));
+    }
+    G.k1x = -L + twoL * u[3];
+    G.k1y = -L + twoL * u[4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) G.k3[i] = -L + twoL * u[5 + i];
+    G.pp = (G.p[0] * G.p[0] + G.p[1] * G.p[1]) + G.p[2] * G.p[2];
+    G.kk3 = (G.k3[0] * G.k3[0] + G.k3[1] * G.k3[1]) + G.k3[2] * G.k3[2];
+    G.lin3 = ((int64_t)bin_of(G.k3[0], L, P.dp[0], P.np[0]) * P.np[1] + bin_of(G.k3[1], L, P.dp[1], P.np[1])) * P.np[2]
+             + bin_of(G.k3[2], L, P.dp[2], P.np[2]);
+    const R Px = G.p[0] + G.k3[0], Py = G.p[1] + G.k3[1];
+    G.Pz = G.p[2] + G.k3[2];
+    G.PP = (Px * Px + Py * Py) + G.Pz * G.Pz;
+    G.bx = Px - G.k1x;
+    G.by = Py - G.k1y;
+    G.a2m = G.k1x * G.k1x + G.k1y * G.k1y;
+    G.b2m = G.bx * G.bx + G.by * G.by;
+    G.k2xy_in = in_box(G.bx, L) && in_box(G.by, L);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) G.mdisp[i] = P.mass_mode == 1 ? R(0) : (R)P.m2[x * 4 + i];
+    G.mg2 = (R)P.m2[x * 4 + 0];
+}
 
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += stride) {
+// Per-warp queue of deferred (anchor, sample, term) items (FP32 path).
+struct DeferCtx {
+    int* s_count;          // this warp's counter in shared memory
+    unsigned long long* seg;
+    int cap;
+};
+
+// Evaluates term ti of sample (a, smp); deposits the k1, k2, k3 legs and
+// returns the anchor cell's +q.  With DEFER, an ill-conditioned term is
+// queued instead (returns 0) unless the warp's queue segment is full.
+template <typename R, bool DEFER>
+__device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Geom<R>& G, int64_t a, int smp, int ti,
+                                               DeferCtx* dq)
+{
+    using O = Ops<R>;
+    const R L = P.L;
+    const int64_t nxc = P.nxc, npc = P.npc;
+    const TermDev& T = P.terms[G.d][ti];
+    const R ma2 = G.mdisp[T.mslot[0]], mb2 = G.mdisp[T.mslot[1]];
+    const R mc2 = G.mdisp[T.mslot[2]], md2 = G.mdisp[T.mslot[3]];
+    const R Ep = O::sqrt_(G.pp + md2);
+    const R E3 = O::sqrt_(G.kk3 + mc2);
+    // k1z roots, stable quadratic
+    const R E = Ep + E3;
+    const R Pz = G.Pz;
+    const R a2 = G.a2m + ma2;
+    const R b2 = G.b2m + mb2;
+    const R D = E * E - Pz * Pz;
+    const R kap = (E * E + a2 - b2 - Pz * Pz) * R(0.5);
+    const R H = kap * kap - a2 * D;
+    if (DEFER) {
+        if (G.k2xy_in && D > R(0) && O::fabs_(H) < P.tau * (kap * kap)) {
+            const int slot = atomicAdd(dq->s_count, 1);
+            if (slot < dq->cap) {
+                dq->seg[slot] = ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
+                return 0;
+            }
+            red_add(&P.flags[3], 1);  // queue full: evaluate in FP32 below
+        }
+    }
+    if (H < R(0) || D <= R(0)) return 0;
+    if (!G.k2xy_in) return 0;
+    const R kp = kap * Pz;
+    const R sq = E * O::sqrt_(H);
+    const R Q = kp >= R(0) ? kp + sq : kp - sq;
+    if (Q == R(0)) return 0;
+    R zc[2];
+    zc[0] = Q / D;
+    zc[1] = (E * E * a2 - kap * kap) / Q;
+    long long own = 0;
+#pragma unroll
+    for (int ri = 0; ri < 2; ++ri) {
+        const R z = zc[ri];
+        const R e1 = (kap + Pz * z) / E;
+        if (!(e1 > R(0) && e1 < E)) continue;
+        const R E1 = O::sqrt_(a2 + z * z);
+        const R dz = Pz - z;
+        const R E2 = O::sqrt_(b2 + dz * dz);
+        const R J = z / E1 - dz / E2;
+        if (J == R(0)) continue;
+        if (!in_box(z, L) || !in_box(dz, L)) continue;
+        const R s = E * E - G.PP;
+        const R k1k3 = (G.k1x * G.k3[0] + G.k1y * G.k3[1]) + z * G.k3[2];
+        const R k1p = (G.k1x * G.p[0] + G.k1y * G.p[1]) + z * G.p[2];
+        const R t = (ma2 + mc2) - R(2) * (E1 * E3 - k1k3);
+        const R uu = (ma2 + md2) - R(2) * (E1 * Ep - k1p);
+        const R mg2 = G.mg2;
+        if (s <= R(0) || t - mg2 >= R(0) || uu - mg2 >= R(0)) {
+            red_add(&P.flags[0], 1);
+            continue;
+        }
+        const R M2 = msq<R>(T.cls, P, s, t, uu, mg2);
+        const int64_t lin1 = ((int64_t)bin_of(G.k1x, L, P.dp[0], P.np[0]) * P.np[1] + bin_of(G.k1y, L, P.dp[1], P.np[1]))
+                                 * P.np[2]
+                             + bin_of(z, L, P.dp[2], P.np[2]);
+        const int64_t lin2 = ((int64_t)bin_of(G.bx, L, P.dp[0], P.np[0]) * P.np[1] + bin_of(G.by, L, P.dp[1], P.np[1]))
+                                 * P.np[2]
+                             + bin_of(dz, L, P.dp[2], P.np[2]);
+        const int64_t i1 = (int64_t)T.slot[0] * nxc * npc + G.xoff + lin1;
+        const int64_t i2 = (int64_t)T.slot[1] * nxc * npc + G.xoff + lin2;
+        const int64_t i3 = (int64_t)T.slot[2] * nxc * npc + G.xoff + G.lin3;
+        R f1, f2, f3, fp;
+        if (P.analytic) {
+            f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
+            f2 = f_equilibrium(P, P.slot_species[T.slot[1]], E2);
+            f3 = f_equilibrium(P, P.slot_species[T.slot[2]], E3);
+            fp = f_equilibrium(P, P.slot_species[T.slot[3]], Ep);
+        } else {
+            f1 = load_f(P, i1);
+            f2 = load_f(P, i2);
+            f3 = load_f(P, i3);
+            fp = load_f(P, a);
+        }
+        const R F1 = T.quark[0] ? R(1) - f1 : R(1) + f1;
+        const R F2 = T.quark[1] ? R(1) - f2 : R(1) + f2;
+        const R F3 = T.quark[2] ? R(1) - f3 : R(1) + f3;
+        const R Fp = T.quark[3] ? R(1) - fp : R(1) + fp;
+        const R gain = f1 * f2 * F3 * Fp;
+        const R W = gain - F1 * F2 * f3 * fp;
+        const R den = O::fabs_(J) * P.twopi5 * R(16) * E1 * E2 * E3 * Ep;
+        const R ct = (R)T.sym * W * M2 / den;
+        const R wq = ct * P.Kown;
+        if (!(O::fabs_(wq) < O::LIM)) {
+            red_add(&P.flags[1], 1);
+            continue;
+        }
+        const long long q = O::rint_(wq);
+        if (q == 0) continue;
+        own += q;
+        if (P.sampler == 0) {
+            red_add(&P.A[i3], q);
+            red_add(&P.A[i1], -q);
+            red_add(&P.A[i2], -q);
+        }
+    }
+    return own;
+}
+
+// Main kernel: grid-stride over (anchor, sample) items, 32 consecutive items
+// per warp.  With DEFER, each warp owns a queue segment of P.qcap items.
+template <typename R, bool DEFER>
+__global__ void __launch_bounds__(256) k_collide(const __grid_constant__ CollideArgs<R> P)
+{
+    const int64_t total = P.n_sel * (int64_t)P.nsamples;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const bool warp_anchor = (P.nsamples & 31) == 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    __shared__ int s_count[8];
+    DeferCtx dq;
+    if (DEFER) {
+        if (lane == 0) s_count[warp] = 0;
+        __syncwarp();
+        const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        dq.s_count = &s_count[warp];
+        dq.seg = P.qitems + gw * P.qcap;
+        dq.cap = (int)P.qcap;
+    }
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
         const int64_t item = base + lane;
         long long own = 0;
-        int64_t own_idx = 0;
+        int64_t a = 0;
         if (item < total) {
             const int64_t al = item / P.nsamples;
             const int smp = (int)(item - al * P.nsamples);
-            const int64_t a = P.a_offset + al * P.a_stride;
-            const int sl = (int)(a / (nxc * npc));
-            const int64_t x = (a / npc) % nxc;
-            const int64_t j = a % npc;
-            const int d = P.slot_species[sl];
-            const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]),
-                               (int)(j % P.np[2])};
-            own_idx = a;
-
-            uint32_t ctr3 = ((uint32_t)P.step << 3) | (uint32_t)d;
-            uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-            uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-            R u[8] = {O::unif(r0.x), O::unif(r0.y), O::unif(r0.z), O::unif(r0.w),
-                      O::unif(r1.x), O::unif(r1.y), O::unif(r1.z), O::unif(r1.w)};
-            R p[3], k3[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                R pc = -L + ((R)jv[i] + R(0.5)) * P.dp[i];
-                p[i] = P.p_center ? pc : pc + P.dp[i] * (u[i] - R(0.5));
-            }
-            const R k1x = -L + twoL * u[3];
-            const R k1y = -L + twoL * u[4];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];
-            const R pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
-            const R kk3 = (k3[0] * k3[0] + k3[1] * k3[1]) + k3[2] * k3[2];
-            const int64_t lin3 = ((int64_t)bin_of(k3[0], L, P.dp[0], P.np[0]) * P.np[1]
-                                  + bin_of(k3[1], L, P.dp[1], P.np[1])) * P.np[2]
-                                 + bin_of(k3[2], L, P.dp[2], P.np[2]);
-            const R Px = p[0] + k3[0], Py = p[1] + k3[1], Pz = p[2] + k3[2];
-            const R PP = (Px * Px + Py * Py) + Pz * Pz;
-            const R bx = Px - k1x, by = Py - k1y;
-            const R a2m = k1x * k1x + k1y * k1y;
-            const R b2m = bx * bx + by * by;
-            const bool k2xy_in = in_box(bx, L) && in_box(by, L);
-
-            R mdisp[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) mdisp[i] = P.mass_mode == 1 ? R(0) : (R)P.m2[x * 4 + i];
-            const R mg2 = (R)P.m2[x * 4 + 0];
-            const int64_t xoff = x * npc;
-
-            const int nt = P.nterms[d];
-            for (int ti = 0; ti < nt; ++ti) {
-                const TermDev& T = P.terms[d][ti];
-                const R ma2 = mdisp[T.mslot[0]], mb2 = mdisp[T.mslot[1]];
-                const R mc2 = mdisp[T.mslot[2]], md2 = mdisp[T.mslot[3]];
-                const R Ep = O::sqrt_(pp + md2);
-                const R E3 = O::sqrt_(kk3 + mc2);
-                // k1z roots, stable quadratic
-                const R E = Ep + E3;
-                const R a2 = a2m + ma2;
-                const R b2 = b2m + mb2;
-                const R D = E * E - Pz * Pz;
-                const R kap = (E * E + a2 - b2 - Pz * Pz) * R(0.5);
-                const R H = kap * kap - a2 * D;
-                if (H < R(0) || D <= R(0)) continue;
-                if (!k2xy_in) continue;
-                const R kp = kap * Pz;
-                const R sq = E * O::sqrt_(H);
-                const R Q = kp >= R(0) ? kp + sq : kp - sq;
-                if (Q == R(0)) continue;
-                R zc[2];
-                zc[0] = Q / D;
-                zc[1] = (E * E * a2 - kap * kap) / Q;
-#pragma unroll
-                for (int ri = 0; ri < 2; ++ri) {
-                    const R z = zc[ri];
-                    const R e1 = (kap + Pz * z) / E;
-                    if (!(e1 > R(0) && e1 < E)) continue;
-                    const R E1 = O::sqrt_(a2 + z * z);
-                    const R dz = Pz - z;
-                    const R E2 = O::sqrt_(b2 + dz * dz);
-                    const R J = z / E1 - dz / E2;
-                    if (J == R(0)) continue;
-                    if (!in_box(z, L) || !in_box(dz, L)) continue;
-                    const R s = E * E - PP;
-                    const R k1k3 = (k1x * k3[0] + k1y * k3[1]) + z * k3[2];
-                    const R k1p = (k1x * p[0] + k1y * p[1]) + z * p[2];
-                    const R t = (ma2 + mc2) - R(2) * (E1 * E3 - k1k3);
-                    const R uu = (ma2 + md2) - R(2) * (E1 * Ep - k1p);
-                    if (s <= R(0) || t - mg2 >= R(0) || uu - mg2 >= R(0)) {
-                        red_add(&P.flags[0], 1);
-                        continue;
-                    }
-                    const R M2 = msq<R>(T.cls, P, s, t, uu, mg2);
-                    const int64_t lin1 = ((int64_t)bin_of(k1x, L, P.dp[0], P.np[0]) * P.np[1]
-                                          + bin_of(k1y, L, P.dp[1], P.np[1])) * P.np[2]
-                                         + bin_of(z, L, P.dp[2], P.np[2]);
-                    const int64_t lin2 = ((int64_t)bin_of(bx, L, P.dp[0], P.np[0]) * P.np[1]
-                                          + bin_of(by, L, P.dp[1], P.np[1])) * P.np[2]
-                                         + bin_of(dz, L, P.dp[2], P.np[2]);
-                    const int64_t i1 = (int64_t)T.slot[0] * nxc * npc + xoff + lin1;
-                    const int64_t i2 = (int64_t)T.slot[1] * nxc * npc + xoff + lin2;
-                    const int64_t i3 = (int64_t)T.slot[2] * nxc * npc + xoff + lin3;
-                    R f1, f2, f3, fp;
-                    if (P.analytic) {
-                        const int d0 = P.slot_species[T.slot[0]], d1 = P.slot_species[T.slot[1]];
-                        const int d2 = P.slot_species[T.slot[2]], d3 = P.slot_species[T.slot[3]];
-                        f1 = f_equilibrium(P, d0, E1);
-                        f2 = f_equilibrium(P, d1, E2);
-                        f3 = f_equilibrium(P, d2, E3);
-                        fp = f_equilibrium(P, d3, Ep);
-                    } else {
-                        f1 = __ldg(&P.f[i1]);
-                        f2 = __ldg(&P.f[i2]);
-                        f3 = __ldg(&P.f[i3]);
-                        fp = __ldg(&P.f[a]);
-                    }
-                    const R F1 = T.quark[0] ? R(1) - f1 : R(1) + f1;
-                    const R F2 = T.quark[1] ? R(1) - f2 : R(1) + f2;
-                    const R F3 = T.quark[2] ? R(1) - f3 : R(1) + f3;
-                    const R Fp = T.quark[3] ? R(1) - fp : R(1) + fp;
-                    const R gain = f1 * f2 * F3 * Fp;
-                    const R W = gain - F1 * F2 * f3 * fp;
-                    const R den = O::fabs_(J) * P.twopi5 * R(16) * E1 * E2 * E3 * Ep;
-                    const R ct = (R)T.sym * W * M2 / den;
-                    const R wq = ct * P.Kown;
-                    if (!(O::fabs_(wq) < O::LIM)) {
-                        red_add(&P.flags[1], 1);
-                        continue;
-                    }
-                    const long long q = O::rint_(wq);
-                    if (q == 0) continue;
-                    own += q;
-                    if (P.sampler == 0) {
-                        red_add(&P.A[i3], q);
-                        red_add(&P.A[i1], -q);
-                        red_add(&P.A[i2], -q);
-                    }
-                }
-            }
+            a = P.a_offset + al * P.a_stride;
+            Geom<R> G;
+            make_geom(P, a, smp, G);
+            const int nt = P.nterms[G.d];
+            for (int ti = 0; ti < nt; ++ti) own += eval_term<R, DEFER>(P, G, a, smp, ti, &dq);
         }
         if (warp_anchor) {
             own = warp_sum_ll(own);
-            if (lane == 0 && own != 0) red_add(&P.A[own_idx], own);
+            if (lane == 0 && own != 0) red_add(&P.A[a], own);
         } else if (own != 0) {
-            red_add(&P.A[own_idx], own);
+            red_add(&P.A[a], own);
         }
+    }
+    if (DEFER) {
+        __syncwarp();
+        if (lane == 0) {
+            const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+            const int c = s_count[warp];
+            P.qcount[gw] = c < P.qcap ? c : (int)P.qcap;
+        }
+    }
+}
+
+// Re-evaluates the queued terms in FP64 (one block per warp segment).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fixup(const __grid_constant__ CollideArgs<R> P, const int* qcount,
+                                               const unsigned long long* qitems, int64_t qcap)
+{
+    const int64_t seg = blockIdx.x;
+    const int n = qcount[seg];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long it = qitems[seg * qcap + i];
+        const int64_t a = (int64_t)(it >> 24);
+        const int smp = (int)((it >> 4) & 0xFFFFFu);
+        const int ti = (int)(it & 0xFu);
+        Geom<R> G;
+        make_geom(P, a, smp, G);
+        const long long own = eval_term<R, false>(P, G, a, smp, ti, nullptr);
+        if (own != 0) red_add(&P.A[a], own);
     }
 }
 

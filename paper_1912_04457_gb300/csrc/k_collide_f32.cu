@@ -1,5 +1,6 @@
 // FP32 collision path: the integrand in single precision with FMA
-// contraction, uniforms with 23-bit resolution; deposits stay int64 fixed
+// contraction, uniforms with 23-bit resolution; ill-conditioned terms are
+// queued for FP64 re-evaluation (launch_fixup); deposits stay int64 fixed
 // point, so number conservation is still exact.
 #include "collide.cuh"
 
@@ -7,7 +8,10 @@ namespace bz {
 
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
 {
-    k_collide<float><<<grid, 256, 0, s>>>(a);
+    if (a.tau > 0.0f)
+        k_collide<float, true><<<grid, 256, 0, s>>>(a);
+    else
+        k_collide<float, false><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
