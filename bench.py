@@ -239,7 +239,8 @@ def run_bz(args):
     from paper_1912_04457_gb300 import inputs as I
 
     mk = workloads()[args.workload]
-    w = mk(seed=mk().seed + 1000 * rank) if world > 1 else mk()
+    kw = {"nsamples": args.nsamples} if args.nsamples else {}
+    w = mk(seed=mk().seed + 1000 * rank, **kw) if world > 1 else mk(**kw)
     prec = bz.PREC_F32 if args.prec == "f32" else bz.PREC_F64
     h = bz.Handle(nx=w.nx, dx=w.dx, np_=w.np_, L=w.L, seed=w.seed, species_mask=w.species_mask,
                   alpha_s=w.alpha_s)
@@ -385,6 +386,7 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--nsamples", type=int, default=0, help="override samples per cell (small profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
