@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags)
 UNITS = [
     ("k_collide_f64.cu", ["-fmad=false"]),
-    ("k_collide_f32.cu", []),
+    ("k_collide_f32.cu", ["-use_fast_math"]),
     ("k_transport.cu", ["-fmad=false"]),
     ("bz_api.cu", ["-fmad=false"]),
 ]
@@ -30,8 +30,8 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
+def _compile(src, extra, out=OUT):
+    obj = os.path.join(out, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
            "-I", os.path.join(ROOT, "include"), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,19 +51,25 @@ def _stale():
     return False
 
 
-def build(force: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, out_dir: str = None, extra=(), unit_extra=None) -> str:
+    """Builds libbz.so into out_dir (default: the in-tree _build).  `extra`
+    adds nvcc flags to every unit, `unit_extra` maps a source to flags that
+    replace its own."""
+    out = out_dir or OUT
+    lib = os.path.join(out, "libbz.so")
+    if not force and out == OUT and not _stale():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(lambda u: _compile(*u), UNITS))
-    tmp = LIB + ".tmp.%d" % os.getpid()
+    os.makedirs(out, exist_ok=True)
+    units = [(src, list((unit_extra or {}).get(src, fl)) + list(extra)) for src, fl in UNITS]
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(lambda u: _compile(u[0], u[1], out), units))
+    tmp = lib + ".tmp.%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

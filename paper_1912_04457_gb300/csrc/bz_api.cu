@@ -526,10 +526,15 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         CK(h, launch_collide_f64(a, (int)blocks, s));
         return BZ_OK;
     }
-    // FP32 integrand; ill-conditioned terms queued per warp for FP64.
+    // FP32 integrand, one warp per (anchor, 32 samples) unit; ill-conditioned
+    // terms queued per warp for FP64.
+    const int64_t units = n_sel * (int64_t)((nsamples + 31) / 32);
+    blocks = (units + 7) / 8;
+    if (blocks > (int64_t)h->nsm * 24) blocks = (int64_t)h->nsm * 24;
+    if (blocks < 1) blocks = 1;
     const int64_t warps = blocks * 8;
-    const int64_t items_per_warp = ((total + blocks * 256 - 1) / (blocks * 256)) * 32;
-    const int64_t qcap = items_per_warp * MAX_TERMS / 50 + 64;  // 2% of the warp's term evaluations
+    const int64_t samples_per_warp = ((units + warps - 1) / warps) * 32;
+    const int64_t qcap = samples_per_warp * MAX_TERMS / DEFER_CAP_DIV + 64;
     if (warps > h->q_warps || warps * qcap > h->q_items) {
         cudaFree(h->d_qcount);
         cudaFree(h->d_qitems);

@@ -105,7 +105,14 @@ struct MomentArgs {
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
 cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
-constexpr double DEFER_TAU = 2e-3;
+#ifndef BZ_DEFER_TAU
+#define BZ_DEFER_TAU 2e-3
+#endif
+constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2 are re-evaluated in FP64
+#ifndef BZ_DEFER_CAP_DIV
+#define BZ_DEFER_CAP_DIV 50
+#endif
+constexpr int DEFER_CAP_DIV = BZ_DEFER_CAP_DIV;  // queue room: 1/DIV of a warp's term evaluations
 constexpr int MAX_SAMPLES = 1 << 20;
 cudaError_t launch_masses(const MassArgs& a, cudaStream_t s);
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s);

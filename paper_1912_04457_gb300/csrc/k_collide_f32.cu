@@ -1,17 +1,348 @@
-// FP32 collision path: the integrand in single precision with FMA
-// contraction, uniforms with 23-bit resolution; ill-conditioned terms are
-// queued for FP64 re-evaluation (launch_fixup); deposits stay int64 fixed
-// point, so number conservation is still exact.
+// FP32 collision path (warp-cooperative).
+//
+// Work unit: one anchor (species d, x cell, p cell) and 32 of its samples,
+// one sample per lane, so the anchor's index decode, masses and f_p are
+// warp-uniform.  Per term of d's equation (Eqs. C_gluon / C_quark):
+//   phase A (every lane): E3, D, kappa, H and the two k1z candidates of
+//     Eq. (work out delta E); ill-conditioned terms (|H| < tau kappa^2) go to
+//     the FP64 queue; each valid root inside the box is appended, as
+//     (lane, term, z, E3, sqrt H), to a per-warp ring in shared memory;
+//   phase B (whenever 32 roots are pending, and at the end): all 32 lanes
+//     take one root each and evaluate E1, s, t, u, |M|^2, the leg bins, W
+//     and c~ (Eq. ca), using |J| E1 E2 = sqrt(H) at a root, then deposit the
+//     int64 weight to the k1, k2, k3 legs; the anchor's own +q is summed in
+//     registers and over the warp, one reduction per unit.
+// The per-lane sample geometry lives in shared memory so phase B can read
+// any lane's sample.  Uniforms: u = ((x >> 9) + 1/2) 2^-23 built from the
+// mantissa bits; weights are rounded to int64 with integer operations only,
+// so the FP64 pipe is never used.
 #include "collide.cuh"
 
 namespace bz {
 
+namespace {
+
+constexpr int RING = 128;         // pending roots per warp (power of 2)
+constexpr int WARPS = 8;          // warps per block
+
+struct WarpSmem {
+    // sample geometry, [field][lane]
+    float p0[32], p1[32], p2[32], k30[32], k31[32], k32[32], k1x[32], k1y[32];
+    float Pz[32], PP[32], bx[32], by[32], a2m[32], b2m[32], Ep[32];
+    int lin3[32], b1xy[32];       // exact bins of k3 and of (k1x, k1y)
+    // pending roots
+    float z[RING], E3[RING], sqH[RING];
+    int tag[RING];                // lane | term << 5
+};
+
+__device__ __forceinline__ float unif23(uint32_t x)
+{
+    // ((x >> 9) + 1/2) 2^-23, exactly: 1.m - 1 gives m 2^-23, + 2^-24 is exact
+    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-8f;
+}
+
+// round-half-even of |w| < 2^62 to int64 without conversion instructions
+__device__ __forceinline__ long long rint_ll(float w)
+{
+    const float aw = fabsf(w);
+    if (aw < 4194304.0f) {  // 2^22: the 1.5 2^23 shifter puts round(w) in the low mantissa bits
+        return (long long)(__float_as_int(w + 12582912.0f) - 0x4B400000);
+    }
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xffu) - 150;  // |w| >= 2^22: w is m 2^e with e >= -1
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    long long v;
+    if (e >= 0) {
+        v = m << e;
+    } else {  // e == -1: m/2, half even
+        v = (m >> 1) + ((m & 1) & ((m >> 1) & 1));
+    }
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)
+{
+    return k == 0 ? a : (k == 1 ? b : (k == 2 ? c : d));
+}
+
+__device__ __forceinline__ int binf(float k, float L, float inv_dp, int n)
+{
+    int j = (int)floorf((k + L) * inv_dp);
+    j = j < 0 ? 0 : j;
+    return j >= n ? n - 1 : j;
+}
+
+// Bin of a sampled coordinate k = -L + 2L u, u = ((x >> 9) + 1/2) 2^-23:
+// floor(u n) = ((2 (x >> 9) + 1) n) >> 24 exactly (u n is never within 2^-24
+// of an integer, so the FP64 definition floor((k + L)/dp) gives the same bin).
+__device__ __forceinline__ int bin_word(uint32_t x, int n)
+{
+    return (int)((((x >> 9) * 2u + 1u) * (uint32_t)n) >> 24);
+}
+
+// A solved coordinate within EDGE_NU of a bin width of a bin (or box) edge:
+// FP32 rounding could put it on the other side, so the term goes to FP64.
+constexpr float EDGE_NU = 2e-4f;
+__device__ __forceinline__ bool near_edge(float v, float L, float inv_dp)
+{
+    const float t = (v + L) * inv_dp;
+    const float r = t - floorf(t);
+    return r < EDGE_NU || r > 1.0f - EDGE_NU;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__ CollideArgs<float> P)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ int s_qcount[WARPS];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    WarpSmem& S = smem[warp];
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    if (lane == 0) s_qcount[warp] = 0;
+    __syncwarp();
+    DeferCtx dq;
+    dq.s_count = &s_qcount[warp];
+    dq.seg = P.qitems + gw * P.qcap;
+    dq.cap = (int)P.qcap;
+
+    const float L = P.L, twoL = P.twoL;
+    const float inv_dp0 = 1.0f / P.dp[0], inv_dp1 = 1.0f / P.dp[1], inv_dp2 = 1.0f / P.dp[2];
+    const int64_t nxc = P.nxc, npc = P.npc;
+    const int nchunk = (P.nsamples + 31) >> 5;
+    const int64_t units = P.n_sel * nchunk;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (int64_t unit = gw; unit < units; unit += nwarps) {
+        const int64_t al = unit / nchunk;
+        const int chunk = (int)(unit - al * nchunk);
+        const int64_t a = P.a_offset + al * P.a_stride;
+        const int sl = (int)(a / (nxc * npc));
+        const int64_t x = (a / npc) % nxc;
+        const int j = (int)(a % npc);
+        const int d = P.slot_species[sl];
+        const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
+        const int64_t xoff = x * npc;
+        const int64_t slot_stride = nxc * npc;
+        // warp-uniform masses: lanes 0..4 convert one double each, then broadcast
+        float mv = 0.0f;
+        if (lane < 5) mv = (float)P.m2[x * 4 + (lane < 4 ? lane : 0)];
+        const float mg2 = __shfl_sync(0xffffffffu, mv, 4);
+        float m0 = __shfl_sync(0xffffffffu, mv, 0), m1 = __shfl_sync(0xffffffffu, mv, 1);
+        float m2v = __shfl_sync(0xffffffffu, mv, 2), m3 = __shfl_sync(0xffffffffu, mv, 3);
+        if (P.mass_mode == 1) m0 = m1 = m2v = m3 = 0.0f;
+        const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
+
+        const int smp = chunk * 32 + lane;
+        const bool live = smp < P.nsamples;
+        // ---- sample geometry (one sample per lane) ----
+        {
+            const uint32_t ctr3 = ((uint32_t)P.step << 3) | (uint32_t)d;
+            const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+            const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+            const float p0 = (-L + ((float)jx + 0.5f) * P.dp[0]) + P.dp[0] * (unif23(r0.x) - 0.5f);
+            const float p1 = (-L + ((float)jy + 0.5f) * P.dp[1]) + P.dp[1] * (unif23(r0.y) - 0.5f);
+            const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
+            const float k1x = -L + twoL * unif23(r0.w);
+            const float k1y = -L + twoL * unif23(r1.x);
+            const float k30 = -L + twoL * unif23(r1.y);
+            const float k31 = -L + twoL * unif23(r1.z);
+            const float k32 = -L + twoL * unif23(r1.w);
+            const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+            const float bx = Px - k1x, by = Py - k1y;
+            const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
+            S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
+            S.k30[lane] = k30; S.k31[lane] = k31; S.k32[lane] = k32;
+            S.k1x[lane] = k1x; S.k1y[lane] = k1y;
+            S.Pz[lane] = Pz;
+            S.PP[lane] = (Px * Px + Py * Py) + Pz * Pz;
+            S.bx[lane] = bx; S.by[lane] = by;
+            S.a2m[lane] = k1x * k1x + k1y * k1y;
+            S.b2m[lane] = bx * bx + by * by;
+            S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
+            S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+            S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+        }
+        __syncwarp();
+        const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
+        const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0) || near_edge(S.by[lane], L, inv_dp1));
+        const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
+
+        int head = 0, tail = 0;  // ring indices (warp-uniform)
+        long long own = 0;
+        const int nt = P.nterms[d];
+
+        // phase B on n pending roots starting at head
+        auto process = [&](int n) {
+            if (lane < n) {
+                const int slot_i = (head + lane) & (RING - 1);
+                const int tg = S.tag[slot_i];
+                const int src = tg & 31, ti = tg >> 5;
+                const float z = S.z[slot_i], E3 = S.E3[slot_i], sqH = S.sqH[slot_i];
+                const TermDev& T = P.terms[d][ti];
+                const float ma2 = sel4(T.mslot[0], m0, m1, m2v, m3), mb2 = sel4(T.mslot[1], m0, m1, m2v, m3);
+                const float mc2 = sel4(T.mslot[2], m0, m1, m2v, m3), md2 = sel4(T.mslot[3], m0, m1, m2v, m3);
+                const float Ep = S.Ep[src];
+                const float E = Ep + E3;
+                const float a2 = S.a2m[src] + ma2;
+                const float E1 = sqrtf(a2 + z * z);
+                const float Pz = S.Pz[src];
+                const float dz = Pz - z;
+                const float k1x = S.k1x[src], k1y = S.k1y[src];
+                const float s = E * E - S.PP[src];
+                const float k1k3 = (k1x * S.k30[src] + k1y * S.k31[src]) + z * S.k32[src];
+                const float k1p = (k1x * S.p0[src] + k1y * S.p1[src]) + z * S.p2[src];
+                const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
+                const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
+                if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
+                    red_add(&P.flags[0], 1);
+                } else {
+                    const float M2 = msq<float>(T.cls, P, s, t, uu, mg2);
+                    const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
+                    const int lin2 = (binf(S.bx[src], L, inv_dp0, P.np[0]) * P.np[1]
+                                      + binf(S.by[src], L, inv_dp1, P.np[1])) * P.np[2]
+                                     + binf(dz, L, inv_dp2, P.np[2]);
+                    const int64_t i1 = (int64_t)T.slot[0] * slot_stride + xoff + lin1;
+                    const int64_t i2 = (int64_t)T.slot[1] * slot_stride + xoff + lin2;
+                    const int64_t i3 = (int64_t)T.slot[2] * slot_stride + xoff + S.lin3[src];
+                    float f1, f2, f3, fpp;
+                    if (P.analytic) {
+                        const float E2 = E - E1;
+                        f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
+                        f2 = f_equilibrium(P, P.slot_species[T.slot[1]], E2);
+                        f3 = f_equilibrium(P, P.slot_species[T.slot[2]], E3);
+                        fpp = f_equilibrium(P, d, Ep);
+                    } else {
+                        const float* F = static_cast<const float*>(P.f);
+                        f1 = __ldg(F + i1);
+                        f2 = __ldg(F + i2);
+                        f3 = __ldg(F + i3);
+                        fpp = fp;
+                    }
+                    const float F1 = T.quark[0] ? 1.0f - f1 : 1.0f + f1;
+                    const float F2 = T.quark[1] ? 1.0f - f2 : 1.0f + f2;
+                    const float F3 = T.quark[2] ? 1.0f - f3 : 1.0f + f3;
+                    const float Fp = T.quark[3] ? 1.0f - fpp : 1.0f + fpp;
+                    const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
+                    // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
+                    const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
+                    const float wq = (float)T.sym * W * M2 / den * P.Kown;
+                    if (!(fabsf(wq) < 4611686018427387904.0f)) {
+                        red_add(&P.flags[1], 1);
+                    } else {
+                        const long long q = rint_ll(wq);
+                        if (q != 0) {
+                            own += q;
+                            if (P.sampler == 0) {
+                                red_add(&P.A[i3], q);
+                                red_add(&P.A[i1], -q);
+                                red_add(&P.A[i2], -q);
+                            }
+                        }
+                    }
+                }
+            }
+            head += n;
+            __syncwarp();
+        };
+
+        for (int ti = 0; ti < nt; ++ti) {
+            // ---- phase A: roots of term ti for this lane's sample ----
+            const TermDev& T = P.terms[d][ti];
+            const float ma2 = sel4(T.mslot[0], m0, m1, m2v, m3), mb2 = sel4(T.mslot[1], m0, m1, m2v, m3);
+            const float mc2 = sel4(T.mslot[2], m0, m1, m2v, m3);
+            const float Ep = S.Ep[lane];
+            const float E3 = sqrtf(kk3 + mc2);
+            const float E = Ep + E3;
+            const float Pz = S.Pz[lane];
+            const float a2 = S.a2m[lane] + ma2;
+            const float b2 = S.b2m[lane] + mb2;
+            const float D = E * E - Pz * Pz;
+            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+            const float H = kap * kap - a2 * D;
+            bool v0 = false, v1 = false;
+            float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
+            if ((k2xy_in || marg_xy) && D > 0.0f) {
+                // FP64 re-evaluation of this term when it is ill-conditioned
+                // (|H| < tau kappa^2) or a solved coordinate sits on an edge
+                bool defer = fabsf(H) < P.tau * (kap * kap);
+                bool e0 = false, e1v = false;
+                if (!defer && H > 0.0f) {
+                    sqH = sqrtf(H);
+                    const float kp = kap * Pz;
+                    const float sq = E * sqH;
+                    const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                    if (Q != 0.0f) {
+                        z0 = Q / D;
+                        z1 = (E * E * a2 - kap * kap) / Q;
+                        const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
+                        e0 = e10 > 0.0f && e10 < E;
+                        e1v = e11 > 0.0f && e11 < E;
+                        defer = (marg_xy && (e0 || e1v))
+                                || (e0 && (near_edge(z0, L, inv_dp2) || near_edge(Pz - z0, L, inv_dp2)))
+                                || (e1v && (near_edge(z1, L, inv_dp2) || near_edge(Pz - z1, L, inv_dp2)));
+                    }
+                }
+                if (defer) {
+                    const int qs = atomicAdd(dq.s_count, 1);
+                    if (qs < dq.cap) {
+                        dq.seg[qs] = ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
+                    } else {
+                        red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
+                        defer = false;
+                    }
+                }
+                if (!defer && k2xy_in && H > 0.0f) {
+                    if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
+                        sqH = sqrtf(H);
+                        const float kp = kap * Pz;
+                        const float sq = E * sqH;
+                        const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                        if (Q != 0.0f) {
+                            z0 = Q / D;
+                            z1 = (E * E * a2 - kap * kap) / Q;
+                            const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
+                            e0 = e10 > 0.0f && e10 < E;
+                            e1v = e11 > 0.0f && e11 < E;
+                        }
+                    }
+                    v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
+                    v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
+                }
+            }
+            // ---- append valid roots to the ring ----
+            const unsigned b0 = __ballot_sync(0xffffffffu, v0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, v1);
+            const int n0 = __popc(b0);
+            if (v0) {
+                const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
+                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
+            }
+            if (v1) {
+                const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
+                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
+            }
+            tail += n0 + __popc(b1);
+            __syncwarp();
+            while (tail - head >= 32) process(32);
+        }
+        if (tail > head) process(tail - head);
+        own = warp_sum_ll(own);
+        if (lane == 0 && own != 0) red_add(&P.A[a], own);
+        __syncwarp();
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int c = s_qcount[warp];
+        P.qcount[gw] = c < P.qcap ? c : (int)P.qcap;
+    }
+}
+
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
 {
-    if (a.tau > 0.0f)
-        k_collide<float, true><<<grid, 256, 0, s>>>(a);
-    else
-        k_collide<float, false><<<grid, 256, 0, s>>>(a);
+    k_collide_f32w<<<grid, 32 * WARPS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
