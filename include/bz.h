@@ -177,6 +177,42 @@ int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host)
 int bz_profile(bz_handle h, int enable);
 int bz_profile_read(bz_handle h, double* ms_host, int64_t* launches_host, int32_t n);
 
+/* No-allocation variant of bz_collision_term (FP64 integrand, symmetric
+ * sampler, all anchors).  The paper has no counterpart; this entry point
+ * exists for callers that cannot allocate device memory themselves or let
+ * a library do it -- code that runs inside another framework's memory pool,
+ * under an allocator that forbids cudaMalloc, or in a plug-in that may only
+ * touch the buffers it is handed.  It needs no handle and calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch (f of the
+ * state, the mass accumulators, the counters) is a fixed set of file-scope
+ * device arrays, about 2.2 MB, which every GPU that loads the library
+ * holds until the process exits.
+ *   Limits: nslots x nx x np <= BZ_STATIC_MAX_CELLS and nx <= BZ_STATIC_MAX_XCELLS
+ *   (BZ_EINVAL with a message otherwise).
+ *   Arguments: g (host), the species mask, alpha_s and mass mode as for
+ *   bz_set_species; state (device int64 [nslots][nx][np], read only);
+ *   m2_in (device double [nx][4]): BZ_MASS_THERMAL -- the previous masses
+ *   giving E in Eqs. (mg), (mq), or NULL for E = |p|; BZ_MASS_MASSLESS --
+ *   ignored; BZ_MASS_FIXED -- the masses to use (required); m2_out (device
+ *   double [nx][4]) receives the masses used; A (device int64, same shape as
+ *   state) is zeroed and filled exactly as bz_collision_term fills it with
+ *   BZ_PREC_F64 and BZ_SAMPLER_SYMMETRIC; nsamples, step, dt as there.
+ *   errbuf (host, may be NULL) receives a message of at most errbuf_len
+ *   bytes when the return value is not BZ_OK.
+ *   Set-up: the first call on a device looks up the device addresses of the
+ *   scratch arrays (with that device current) and caches them; make that
+ *   first call before any stream capture.
+ *   Sharing: every call on a device uses the same scratch, which keeps the
+ *   last call's contents; what must start at zero is cleared on the stream
+ *   at the start of each call.  Calls that overlap on the GPU (different
+ *   streams, or different threads) race and give wrong results. */
+#define BZ_STATIC_MAX_CELLS (1 << 18)
+#define BZ_STATIC_MAX_XCELLS 4096
+int bz_collision_term_static(const bz_grid* g, uint32_t species_mask, double alpha_s, int32_t mass_mode,
+                             const int64_t* state, const double* m2_in, double* m2_out, int64_t* A,
+                             int32_t nsamples, int32_t step, double dt, void* stream, char* errbuf,
+                             int32_t errbuf_len);
+
 /* Library version string. */
 const char* bz_version(void);
 

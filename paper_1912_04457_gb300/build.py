@@ -22,6 +22,7 @@ UNITS = [
     ("k_collide_f32.cu", ["-use_fast_math"]),
     ("k_transport.cu", ["-fmad=false"]),
     ("bz_api.cu", ["-fmad=false"]),
+    ("bz_static.cu", ["-fmad=false"]),
 ]
 
 

@@ -54,6 +54,8 @@ SIGNATURES = {
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
     "bz_profile_read": (C.c_int, [_P, _P, _P, _I32]),
+    "bz_collision_term_static": (C.c_int, [C.POINTER(BzGrid), _U32, _D, _I32, _P, _P, _P, _P, _I32,
+                                           _I32, _D, _P, C.c_char_p, _I32]),
     "bz_version": (C.c_char_p, []),
 }
 
@@ -212,6 +214,32 @@ class Handle:
         self._check(self.lib.bz_moments(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
                                         _dev_ptr(out, torch.float64, self.nxc * self.nslots * 5, "out"),
                                         _stream_ptr(stream)))
+
+
+def collision_term_static(nx, dx, np_, L, seed, species_mask, alpha_s, mass_mode, state, m2_in,
+                          m2_out, A, nsamples, step=0, dt=0.01, box=0, stream=None):
+    """bz_collision_term_static: the FP64 collision increment with no device
+    allocation (scratch in the library's static device arrays)."""
+    import torch
+    lib = load()
+    g = BzGrid()
+    g.nx[:] = list(nx)
+    g.dx = dx
+    g.np[:] = list(np_)
+    g.L = L
+    g.seed = seed
+    g.box = box
+    nxc = int(np.prod(nx))
+    ncell = bin(species_mask).count("1") * nxc * int(np.prod(np_))
+    m2p = None if m2_in is None else _dev_ptr(m2_in, torch.float64, nxc * 4, "m2_in")
+    buf = C.create_string_buffer(512)
+    rc = lib.bz_collision_term_static(C.byref(g), species_mask, alpha_s, mass_mode,
+                                      _dev_ptr(state, torch.int64, ncell, "state"), m2p,
+                                      _dev_ptr(m2_out, torch.float64, nxc * 4, "m2_out"),
+                                      _dev_ptr(A, torch.int64, ncell, "A"), nsamples, step, dt,
+                                      _stream_ptr(stream), buf, 512)
+    if rc != BZ_OK:
+        raise BzError(rc, buf.value.decode())
 
 
 def version():
