@@ -527,7 +527,9 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         return BZ_OK;
     }
     // FP32 integrand, one warp per (anchor, 32 samples) unit; ill-conditioned
-    // terms queued per warp for FP64.
+    // terms queued per warp for FP64.  Cell indices are 32-bit there.
+    if (h->ncell >= (int64_t)1 << 31)
+        return fail(h, BZ_EINVAL, "the FP32 path needs fewer than 2^31 cells (has %lld)", (long long)h->ncell);
     const int64_t units = n_sel * (int64_t)((nsamples + 31) / 32);
     blocks = (units + 7) / 8;
     if (blocks > (int64_t)h->nsm * 24) blocks = (int64_t)h->nsm * 24;

@@ -106,7 +106,7 @@ cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStrea
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
 cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
 #ifndef BZ_DEFER_TAU
-#define BZ_DEFER_TAU 2e-3
+#define BZ_DEFER_TAU 1e-3
 #endif
 constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2 are re-evaluated in FP64
 #ifndef BZ_DEFER_CAP_DIV

@@ -33,6 +33,9 @@ struct WarpSmem {
     // pending roots
     float z[RING], E3[RING], sqH[RING];
     int tag[RING];                // lane | term << 5
+    // this unit's terms: masses of the legs and sym, packed leg slots / flags / row
+    float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
+    int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
 };
 
 __device__ __forceinline__ float unif23(uint32_t x)
@@ -80,14 +83,17 @@ __device__ __forceinline__ int bin_word(uint32_t x, int n)
     return (int)((((x >> 9) * 2u + 1u) * (uint32_t)n) >> 24);
 }
 
-// A solved coordinate within EDGE_NU of a bin width of a bin (or box) edge:
-// FP32 rounding could put it on the other side, so the term goes to FP64.
-constexpr float EDGE_NU = 2e-4f;
-__device__ __forceinline__ bool near_edge(float v, float L, float inv_dp)
+// A solved coordinate within nu bin widths of a bin (or box) edge: FP32
+// rounding could put it on the other side, so the term goes to FP64.  k2x,
+// k2y carry a few ulps (EDGE_XY); a root's error grows with the
+// conditioning |kappa|/sqrt(H) of the quadratic (EDGE_Z per unit of it).
+constexpr float EDGE_XY = 1e-5f;
+constexpr float EDGE_Z = 1e-5f;
+__device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float nu)
 {
     const float t = (v + L) * inv_dp;
     const float r = t - floorf(t);
-    return r < EDGE_NU || r > 1.0f - EDGE_NU;
+    return r < nu || r > 1.0f - nu;
 }
 
 }  // namespace
@@ -124,8 +130,8 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
         const int j = (int)(a % npc);
         const int d = P.slot_species[sl];
         const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
-        const int64_t xoff = x * npc;
-        const int64_t slot_stride = nxc * npc;
+        const unsigned xoff = (unsigned)(x * npc);
+        const unsigned slot_stride = (unsigned)(nxc * npc);
         // warp-uniform masses: lanes 0..4 convert one double each, then broadcast
         float mv = 0.0f;
         if (lane < 5) mv = (float)P.m2[x * 4 + (lane < 4 ? lane : 0)];
@@ -135,6 +141,15 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
         if (P.mass_mode == 1) m0 = m1 = m2v = m3 = 0.0f;
         const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
 
+        const int nt = P.nterms[d];
+        if (lane < nt) {
+            const TermDev& T = P.terms[d][lane];
+            S.tm[lane] = make_float4(sel4(T.mslot[0], m0, m1, m2v, m3), sel4(T.mslot[1], m0, m1, m2v, m3),
+                                     sel4(T.mslot[2], m0, m1, m2v, m3), (float)T.sym);
+            S.tinfo[lane] = T.slot[0] | (T.slot[1] << 3) | (T.slot[2] << 6) | (T.quark[0] << 9) | (T.quark[1] << 10)
+                            | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
+        }
+        const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
         const int smp = chunk * 32 + lane;
         const bool live = smp < P.nsamples;
         // ---- sample geometry (one sample per lane) ----
@@ -152,7 +167,6 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
             const float k32 = -L + twoL * unif23(r1.w);
             const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
             const float bx = Px - k1x, by = Py - k1y;
-            const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
             S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
             S.k30[lane] = k30; S.k31[lane] = k31; S.k32[lane] = k32;
             S.k1x[lane] = k1x; S.k1y[lane] = k1y;
@@ -167,12 +181,11 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
         }
         __syncwarp();
         const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
-        const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0) || near_edge(S.by[lane], L, inv_dp1));
+        const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY));
         const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
 
         int head = 0, tail = 0;  // ring indices (warp-uniform)
         long long own = 0;
-        const int nt = P.nterms[d];
 
         // phase B on n pending roots starting at head
         auto process = [&](int n) {
@@ -181,9 +194,9 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
                 const int tg = S.tag[slot_i];
                 const int src = tg & 31, ti = tg >> 5;
                 const float z = S.z[slot_i], E3 = S.E3[slot_i], sqH = S.sqH[slot_i];
-                const TermDev& T = P.terms[d][ti];
-                const float ma2 = sel4(T.mslot[0], m0, m1, m2v, m3), mb2 = sel4(T.mslot[1], m0, m1, m2v, m3);
-                const float mc2 = sel4(T.mslot[2], m0, m1, m2v, m3), md2 = sel4(T.mslot[3], m0, m1, m2v, m3);
+                const float4 tmv = S.tm[ti];
+                const int info = S.tinfo[ti];
+                const float ma2 = tmv.x, mc2 = tmv.z;
                 const float Ep = S.Ep[src];
                 const float E = Ep + E3;
                 const float a2 = S.a2m[src] + ma2;
@@ -199,20 +212,20 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
                 if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
                     red_add(&P.flags[0], 1);
                 } else {
-                    const float M2 = msq<float>(T.cls, P, s, t, uu, mg2);
+                    const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
                     const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
                     const int lin2 = (binf(S.bx[src], L, inv_dp0, P.np[0]) * P.np[1]
                                       + binf(S.by[src], L, inv_dp1, P.np[1])) * P.np[2]
                                      + binf(dz, L, inv_dp2, P.np[2]);
-                    const int64_t i1 = (int64_t)T.slot[0] * slot_stride + xoff + lin1;
-                    const int64_t i2 = (int64_t)T.slot[1] * slot_stride + xoff + lin2;
-                    const int64_t i3 = (int64_t)T.slot[2] * slot_stride + xoff + S.lin3[src];
+                    const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
+                    const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
+                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
                     float f1, f2, f3, fpp;
                     if (P.analytic) {
                         const float E2 = E - E1;
-                        f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
-                        f2 = f_equilibrium(P, P.slot_species[T.slot[1]], E2);
-                        f3 = f_equilibrium(P, P.slot_species[T.slot[2]], E3);
+                        f1 = f_equilibrium(P, P.slot_species[info & 7], E1);
+                        f2 = f_equilibrium(P, P.slot_species[(info >> 3) & 7], E2);
+                        f3 = f_equilibrium(P, P.slot_species[(info >> 6) & 7], E3);
                         fpp = f_equilibrium(P, d, Ep);
                     } else {
                         const float* F = static_cast<const float*>(P.f);
@@ -221,14 +234,14 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
                         f3 = __ldg(F + i3);
                         fpp = fp;
                     }
-                    const float F1 = T.quark[0] ? 1.0f - f1 : 1.0f + f1;
-                    const float F2 = T.quark[1] ? 1.0f - f2 : 1.0f + f2;
-                    const float F3 = T.quark[2] ? 1.0f - f3 : 1.0f + f3;
-                    const float Fp = T.quark[3] ? 1.0f - fpp : 1.0f + fpp;
+                    const float F1 = (info & (1 << 9)) ? 1.0f - f1 : 1.0f + f1;
+                    const float F2 = (info & (1 << 10)) ? 1.0f - f2 : 1.0f + f2;
+                    const float F3 = (info & (1 << 11)) ? 1.0f - f3 : 1.0f + f3;
+                    const float Fp = (info & (1 << 12)) ? 1.0f - fpp : 1.0f + fpp;
                     const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
                     // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                     const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
-                    const float wq = (float)T.sym * W * M2 / den * P.Kown;
+                    const float wq = tmv.w * W * M2 / den * P.Kown;
                     if (!(fabsf(wq) < 4611686018427387904.0f)) {
                         red_add(&P.flags[1], 1);
                     } else {
@@ -250,9 +263,8 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
 
         for (int ti = 0; ti < nt; ++ti) {
             // ---- phase A: roots of term ti for this lane's sample ----
-            const TermDev& T = P.terms[d][ti];
-            const float ma2 = sel4(T.mslot[0], m0, m1, m2v, m3), mb2 = sel4(T.mslot[1], m0, m1, m2v, m3);
-            const float mc2 = sel4(T.mslot[2], m0, m1, m2v, m3);
+            const float4 tmv = S.tm[ti];
+            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
             const float Ep = S.Ep[lane];
             const float E3 = sqrtf(kk3 + mc2);
             const float E = Ep + E3;
@@ -280,9 +292,10 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
                         const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
                         e0 = e10 > 0.0f && e10 < E;
                         e1v = e11 > 0.0f && e11 < E;
+                        const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
                         defer = (marg_xy && (e0 || e1v))
-                                || (e0 && (near_edge(z0, L, inv_dp2) || near_edge(Pz - z0, L, inv_dp2)))
-                                || (e1v && (near_edge(z1, L, inv_dp2) || near_edge(Pz - z1, L, inv_dp2)));
+                                || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
+                                || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
                     }
                 }
                 if (defer) {
