@@ -177,6 +177,56 @@ int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host)
 int bz_profile(bz_handle h, int enable);
 int bz_profile_read(bz_handle h, double* ms_host, int64_t* launches_host, int32_t n);
 
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent, spatially homogeneous boxes (one x
+ * cell each) with their own momentum grid, species set, coupling, mass mode
+ * (THERMAL or MASSLESS) and sample count, advanced together with the FP32
+ * integrand.  Each step runs the whole hot path of every box -- masses
+ * (Eqs. mg, mq), collision sampling with symmetrical deposition (Eqs. ca,
+ * small c relation) into the state in place, moments -- as one persistent
+ * collision launch (warps take chunks of (box, anchor, 32 samples) units
+ * from a global counter, so ragged boxes share the GPU evenly) inside one
+ * captured CUDA graph that is replayed every step.
+ * ------------------------------------------------------------------------ */
+typedef struct bz_box {
+    int32_t np[3];          /* momentum cells per axis                               */
+    double L;               /* momentum box [-L, L)^3, GeV                           */
+    uint32_t species_mask;  /* as bz_set_species                                     */
+    int32_t nsamples;       /* samples per anchor, 1..2^20                           */
+    double alpha_s;         /* coupling                                              */
+    int32_t mass_mode;      /* BZ_MASS_THERMAL or BZ_MASS_MASSLESS                   */
+    uint32_t box_id;        /* xored into the Philox key's low word                  */
+    uint64_t seed;          /* Philox key                                            */
+} bz_box;
+typedef struct bz_batch_s* bz_batch;
+
+/* Creates a batch of nboxes boxes (host array, copied) on the current
+ * device and allocates its buffers.  Errors: BZ_EINVAL (sizes, masks,
+ * nsamples, mass mode FIXED), BZ_ENODEV, BZ_ENOMEM. */
+int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxes);
+int bz_batch_destroy(bz_batch b);
+const char* bz_batch_last_error(bz_batch b);
+/* Layout of the concatenated state and moments (host int64 / int32
+ * [nboxes + 1]; either may be NULL): box i owns cells [cell_offsets[i],
+ * cell_offsets[i+1]) of the state, laid out [slot][p] as for a handle, and
+ * moment rows [slot_offsets[i], slot_offsets[i+1]) of 5 doubles each. */
+int bz_batch_layout(bz_batch b, int64_t* cell_offsets, int32_t* slot_offsets);
+/* nsteps Euler steps of every box; state (device int64, concatenated) is
+ * updated in place; Philox step index step0 + k.  moments_out (device, may
+ * be NULL): [nsteps][total slots][5] doubles as bz_moments.  The first call
+ * runs the autotuner (on a copy of the state) and every call whose state,
+ * moments_out or dt differs from the previous one re-captures the step
+ * graph.  The previous masses persist across calls, as with a handle. */
+int bz_batch_step(bz_batch b, int64_t* state, double dt, int32_t nsteps, int32_t step0, double* moments_out,
+                  void* stream);
+/* Tuned work-chunk size (units per grab), blocks per SM and the collision
+ * time (ms per step) the autotuner measured; BZ_EINVAL before the first step. */
+int bz_batch_tuning(bz_batch b, int32_t* chunk, int32_t* blocks_per_sm, double* ms_collide);
+/* Current masses (host double [nboxes][4]) and counters (host int64 [4], as
+ * bz_get_flags); both synchronise the device. */
+int bz_batch_get_masses(bz_batch b, double* m2_host);
+int bz_batch_get_flags(bz_batch b, int64_t* flags_host);
+
 /* No-allocation variant of bz_collision_term (FP64 integrand, symmetric
  * sampler, all anchors).  The paper has no counterpart; this entry point
  * exists for callers that cannot allocate device memory themselves or let

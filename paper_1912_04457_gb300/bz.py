@@ -25,6 +25,12 @@ class BzGrid(C.Structure):
                 ("seed", C.c_uint64), ("box", C.c_uint32), ("reserved", C.c_uint32)]
 
 
+class BzBox(C.Structure):
+    _fields_ = [("np", C.c_int32 * 3), ("L", C.c_double), ("species_mask", C.c_uint32),
+                ("nsamples", C.c_int32), ("alpha_s", C.c_double), ("mass_mode", C.c_int32),
+                ("box_id", C.c_uint32), ("seed", C.c_uint64)]
+
+
 class BzError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("libbz error %d: %s" % (code, msg))
@@ -56,6 +62,14 @@ SIGNATURES = {
     "bz_profile_read": (C.c_int, [_P, _P, _P, _I32]),
     "bz_collision_term_static": (C.c_int, [C.POINTER(BzGrid), _U32, _D, _I32, _P, _P, _P, _P, _I32,
                                            _I32, _D, _P, C.c_char_p, _I32]),
+    "bz_batch_create": (C.c_int, [C.POINTER(_P), _I32, _P]),
+    "bz_batch_destroy": (C.c_int, [_P]),
+    "bz_batch_last_error": (C.c_char_p, [_P]),
+    "bz_batch_layout": (C.c_int, [_P, _P, _P]),
+    "bz_batch_step": (C.c_int, [_P, _P, _D, _I32, _I32, _P, _P]),
+    "bz_batch_tuning": (C.c_int, [_P, _P, _P, _P]),
+    "bz_batch_get_masses": (C.c_int, [_P, _P]),
+    "bz_batch_get_flags": (C.c_int, [_P, _P]),
     "bz_version": (C.c_char_p, []),
 }
 
@@ -214,6 +228,75 @@ class Handle:
         self._check(self.lib.bz_moments(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
                                         _dev_ptr(out, torch.float64, self.nxc * self.nslots * 5, "out"),
                                         _stream_ptr(stream)))
+
+
+class Batch:
+    """Independent homogeneous boxes stepped together (bz_batch_*).  `boxes`:
+    list of dicts with np_, L, species_mask, nsamples, alpha_s, mass_mode,
+    box_id, seed."""
+
+    def __init__(self, boxes):
+        self.lib = load()
+        arr = (BzBox * len(boxes))()
+        for i, b in enumerate(boxes):
+            arr[i].np[:] = list(b["np_"])
+            arr[i].L = b["L"]
+            arr[i].species_mask = b["species_mask"]
+            arr[i].nsamples = b["nsamples"]
+            arr[i].alpha_s = b["alpha_s"]
+            arr[i].mass_mode = b.get("mass_mode", MASS_THERMAL)
+            arr[i].box_id = b.get("box_id", i)
+            arr[i].seed = b.get("seed", 1)
+        h = C.c_void_p()
+        rc = self.lib.bz_batch_create(C.byref(h), len(boxes), C.cast(arr, C.c_void_p))
+        if rc != BZ_OK:
+            raise BzError(rc, self.lib.bz_batch_last_error(None).decode())
+        self.h = h
+        self.nboxes = len(boxes)
+        self.cell_offsets = np.zeros(self.nboxes + 1, dtype=np.int64)
+        self.slot_offsets = np.zeros(self.nboxes + 1, dtype=np.int32)
+        self._check(self.lib.bz_batch_layout(self.h, self.cell_offsets.ctypes.data_as(C.c_void_p),
+                                             self.slot_offsets.ctypes.data_as(C.c_void_p)))
+        self.ncell = int(self.cell_offsets[-1])
+        self.nslots_total = int(self.slot_offsets[-1])
+
+    def _check(self, rc):
+        if rc != BZ_OK:
+            raise BzError(rc, self.lib.bz_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bz_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, state, dt, nsteps, step0=0, moments_out=None, stream=None):
+        import torch
+        mptr = None
+        if moments_out is not None:
+            mptr = _dev_ptr(moments_out, torch.float64, nsteps * self.nslots_total * 5, "moments_out")
+        self._check(self.lib.bz_batch_step(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), dt,
+                                           nsteps, step0, mptr, _stream_ptr(stream)))
+
+    def tuning(self):
+        ch, bps, ms = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(self.lib.bz_batch_tuning(self.h, C.byref(ch), C.byref(bps), C.byref(ms)))
+        return {"chunk": ch.value, "blocks_per_sm": bps.value, "collide_ms": ms.value}
+
+    def get_masses(self):
+        out = np.zeros((self.nboxes, 4))
+        self._check(self.lib.bz_batch_get_masses(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def flags(self):
+        out = np.zeros(4, dtype=np.int64)
+        self._check(self.lib.bz_batch_get_flags(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
 
 
 def collision_term_static(nx, dx, np_, L, seed, species_mask, alpha_s, mass_mode, state, m2_in,

@@ -352,21 +352,17 @@ static double dp_of(const bz_handle h, int d) { return 2.0 * h->g.L / h->g.np[d]
 // Thermal masses of `state` (Eqs. mg, mq) into the other mass buffer, then
 // make them current.  E from the current masses if there are any (and not
 // in massless mode), else |p|.
-static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)
+static void fill_masses(bz_handle h, MassArgs& a, const long long* state, long long* acc, double* m2_out,
+                        const double* m2_prev)
 {
-    if (h->mass_mode == BZ_MASS_FIXED) {
-        if (!h->have_masses) return fail(h, BZ_EINVAL, "mass mode FIXED needs bz_set_masses first");
-        return BZ_OK;
-    }
     const double dA = 8.0, CF = 4.0 / 3.0;
     double g2 = 4.0 * PI * h->alpha_s;
     double dpx = 2.0 * h->g.L / h->g.np[0], dpy = 2.0 * h->g.L / h->g.np[1], dpz = 2.0 * h->g.L / h->g.np[2];
     double twopi = 2.0 * PI;
-    MassArgs a{};
     a.state = state;
-    a.acc = h->d_acc;
-    a.m2_out = h->d_m2[h->cur ^ 1];
-    a.m2_prev = (h->have_masses && h->mass_mode != BZ_MASS_MASSLESS) ? h->d_m2[h->cur] : nullptr;
+    a.acc = acc;
+    a.m2_out = m2_out;
+    a.m2_prev = m2_prev;
     a.flags = h->d_flags;
     a.nxc = h->nxc;
     a.npc = h->npc;
@@ -380,6 +376,17 @@ static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)
     a.pref_q = 2.0 * CF * g2;
     a.meas = dpx * dpy * dpz / (twopi * twopi * twopi);
     a.limit = INT64_MAX / (h->npc > 0 ? h->npc : 1) / 2;
+}
+
+static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)
+{
+    if (h->mass_mode == BZ_MASS_FIXED) {
+        if (!h->have_masses) return fail(h, BZ_EINVAL, "mass mode FIXED needs bz_set_masses first");
+        return BZ_OK;
+    }
+    MassArgs a{};
+    fill_masses(h, a, state, h->d_acc, h->d_m2[h->cur ^ 1],
+                (h->have_masses && h->mass_mode != BZ_MASS_MASSLESS) ? h->d_m2[h->cur] : nullptr);
     {
         ProfScope ps(h, BZ_K_MASSES, s);
         CK(h, launch_masses(a, s));
@@ -729,5 +736,413 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
     }
     if (cur != reinterpret_cast<long long*>(state))
         CK(h, cudaMemcpyAsync(state, cur, sizeof(long long) * h->ncell, cudaMemcpyDeviceToDevice, s));
+    return BZ_OK;
+}
+
+// --------------------------------------------------------------------------
+// Batched ensemble: independent homogeneous boxes of any grid size, species
+// set, coupling and sample count, stepped together.  Per step: thermal
+// masses of every box (one launch), f of the concatenated state (one
+// launch), collision of every (box, anchor, 32 samples) unit in one
+// persistent launch with dynamic work distribution, FP64 fixup of queued
+// terms, moments, and the end-of-step bookkeeping; the step is captured
+// once as a CUDA graph and replayed, the step index living in device memory.
+// The collision increment is deposited into the state in place: the kernels
+// read f, the FP32 snapshot of the state taken at the start of the step.
+// --------------------------------------------------------------------------
+struct bz_batch_s {
+    int nboxes = 0;
+    int device = 0, nsm = 0;
+    std::vector<bz_box> desc;
+    std::vector<bz_handle_s> hb;  // per-box descriptors; their device pointers alias the batch buffers
+    std::vector<int64_t> cell_prefix, unit_prefix, mchunk_prefix, cchunk_prefix;
+    std::vector<int> slot_prefix;
+    int64_t ncell = 0, nunits = 0, nmchunks = 0, ncchunks = 0;
+    int total_slots = 0;
+    float* d_f = nullptr;
+    double *d_m2_cur = nullptr, *d_m2_prev = nullptr;
+    long long *d_acc = nullptr, *d_flags = nullptr;
+    int *d_have_prev = nullptr, *d_step = nullptr, *d_kidx = nullptr;
+    unsigned long long* d_counter = nullptr;
+    int64_t *d_cell_prefix = nullptr, *d_unit_prefix = nullptr, *d_mchunk_prefix = nullptr, *d_cchunk_prefix = nullptr;
+    int* d_slot_prefix = nullptr;
+    float* d_scale = nullptr;
+    int* d_slot_cells = nullptr;
+    CollideArgs<float>* d_a32 = nullptr;
+    CollideArgs<double>* d_a64 = nullptr;
+    MassArgs* d_mass = nullptr;
+    MomentArgs* d_mom = nullptr;
+    std::vector<CollideArgs<float>> a32;
+    std::vector<CollideArgs<double>> a64;
+    std::vector<MassArgs> mass;
+    std::vector<MomentArgs> mom;
+    int* d_qcount = nullptr;
+    unsigned long long* d_qitems = nullptr;
+    int64_t qcap = 0, qwarps = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const long long* g_state = nullptr;
+    const double* g_mom = nullptr;
+    double g_dt = 0;
+    bool tuned = false;
+    int chunk = 4, bps = 3;
+    double tuned_ms = 0;
+    std::string err;
+};
+
+static int bfail(bz_batch b, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b)
+        b->err = buf;
+    else
+        g_init_error = buf;
+    return code;
+}
+
+#define CKB(b, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return bfail((b), BZ_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static void batch_free(bz_batch b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    void* ptrs[] = {b->d_f, b->d_m2_cur, b->d_m2_prev, b->d_acc, b->d_flags, b->d_have_prev, b->d_step, b->d_kidx,
+                    b->d_counter, b->d_cell_prefix, b->d_unit_prefix, b->d_mchunk_prefix, b->d_cchunk_prefix,
+                    b->d_slot_prefix, b->d_scale, b->d_slot_cells, b->d_a32, b->d_a64, b->d_mass, b->d_mom,
+                    b->d_qcount, b->d_qitems};
+    for (void* p : ptrs) cudaFree(p);
+    for (auto& h : b->hb) {
+        h.d_m2[0] = h.d_m2[1] = nullptr;  // aliases, owned by the batch
+        h.d_freal = nullptr;
+        h.d_flags = h.d_acc = nullptr;
+    }
+}
+
+template <typename T>
+static bool dalloc(T** p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)) == cudaSuccess;
+}
+
+extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxes)
+{
+    if (!out || !boxes || nboxes <= 0 || nboxes > 65535) return bfail(nullptr, BZ_EINVAL, "need 1..65535 boxes");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return bfail(nullptr, BZ_ENODEV, "no CUDA device");
+    bz_batch b = new (std::nothrow) bz_batch_s();
+    if (!b) return bfail(nullptr, BZ_ENOMEM, "out of host memory");
+    b->nboxes = nboxes;
+    b->desc.assign(boxes, boxes + nboxes);
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    b->hb.resize(nboxes);
+    b->cell_prefix.assign(nboxes + 1, 0);
+    b->unit_prefix.assign(nboxes + 1, 0);
+    b->mchunk_prefix.assign(nboxes + 1, 0);
+    b->cchunk_prefix.assign(nboxes + 1, 0);
+    b->slot_prefix.assign(nboxes + 1, 0);
+    for (int i = 0; i < nboxes; ++i) {
+        const bz_box& d = boxes[i];
+        for (int k = 0; k < 3; ++k)
+            if (d.np[k] <= 0 || d.np[k] > MAX_NP) {
+                delete b;
+                return bfail(nullptr, BZ_EINVAL, "box %d: np out of range", i);
+            }
+        if (!(d.L > 0) || !(d.alpha_s > 0) || (d.species_mask & 0x7Fu) == 0 || (d.species_mask & ~0x7Fu) ||
+            d.nsamples <= 0 || d.nsamples > MAX_SAMPLES ||
+            (d.mass_mode != BZ_MASS_THERMAL && d.mass_mode != BZ_MASS_MASSLESS)) {
+            delete b;
+            return bfail(nullptr, BZ_EINVAL, "box %d: bad L, alpha_s, species, nsamples or mass mode", i);
+        }
+        bz_handle_s& h = b->hb[i];
+        h.g.nx[0] = h.g.nx[1] = h.g.nx[2] = 1;
+        h.g.dx = 1.0;
+        for (int k = 0; k < 3; ++k) h.g.np[k] = d.np[k];
+        h.g.L = d.L;
+        h.g.seed = d.seed;
+        h.g.box = d.box_id;
+        h.mask = d.species_mask;
+        h.alpha_s = d.alpha_s;
+        h.mass_mode = d.mass_mode;
+        set_slots(&h);
+        h.nxc = 1;
+        h.npc = (int64_t)d.np[0] * d.np[1] * d.np[2];
+        h.ncell = h.nslots * h.npc;
+        h.nsm = b->nsm;
+        b->cell_prefix[i + 1] = b->cell_prefix[i] + h.ncell;
+        b->unit_prefix[i + 1] = b->unit_prefix[i] + h.ncell * ((d.nsamples + 31) / 32);
+        b->mchunk_prefix[i + 1] = b->mchunk_prefix[i] + (h.npc + 2047) / 2048;
+        b->cchunk_prefix[i + 1] = b->cchunk_prefix[i] + (h.ncell + 2047) / 2048;
+        b->slot_prefix[i + 1] = b->slot_prefix[i] + h.nslots;
+    }
+    b->ncell = b->cell_prefix[nboxes];
+    b->nunits = b->unit_prefix[nboxes];
+    b->nmchunks = b->mchunk_prefix[nboxes];
+    b->ncchunks = b->cchunk_prefix[nboxes];
+    b->total_slots = b->slot_prefix[nboxes];
+    if (b->ncell >= ((int64_t)1 << 31)) {
+        delete b;
+        return bfail(nullptr, BZ_EINVAL, "the batch needs fewer than 2^31 cells");
+    }
+    // persistent grid of up to 3 blocks per SM; per-warp queue room for 4% of an even share
+    b->qwarps = (int64_t)b->nsm * 3 * 8;
+    b->qcap = (b->nunits * 32 * MAX_TERMS) / b->qwarps / 25 + 64;
+    bool ok = dalloc(&b->d_f, b->ncell) && dalloc(&b->d_m2_cur, 4 * nboxes) && dalloc(&b->d_m2_prev, 4 * nboxes) &&
+              dalloc(&b->d_acc, 4 * nboxes) && dalloc(&b->d_flags, 4) && dalloc(&b->d_have_prev, 1) &&
+              dalloc(&b->d_step, 1) && dalloc(&b->d_kidx, 1) && dalloc(&b->d_counter, 1) &&
+              dalloc(&b->d_cell_prefix, nboxes + 1) && dalloc(&b->d_unit_prefix, nboxes + 1) &&
+              dalloc(&b->d_mchunk_prefix, nboxes + 1) && dalloc(&b->d_cchunk_prefix, nboxes + 1) &&
+              dalloc(&b->d_slot_prefix, nboxes + 1) && dalloc(&b->d_scale, 2 * nboxes) &&
+              dalloc(&b->d_slot_cells, nboxes) && dalloc(&b->d_a32, nboxes) && dalloc(&b->d_a64, nboxes) &&
+              dalloc(&b->d_mass, nboxes) && dalloc(&b->d_mom, nboxes) && dalloc(&b->d_qcount, b->qwarps) &&
+              dalloc(&b->d_qitems, b->qwarps * b->qcap);
+    if (!ok) {
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, BZ_ENOMEM, "cannot allocate the batch buffers");
+    }
+    std::vector<float> scale(2 * nboxes);
+    std::vector<int> slot_cells(nboxes);
+    for (int i = 0; i < nboxes; ++i) {
+        bz_handle_s& h = b->hb[i];
+        h.d_freal = b->d_f + b->cell_prefix[i];
+        h.d_m2[0] = b->d_m2_cur + 4 * i;
+        h.cur = 0;
+        h.have_masses = true;
+        h.d_flags = b->d_flags;
+        h.d_acc = b->d_acc + 4 * i;
+        const bool has_g = (h.mask & 1u) != 0;
+        scale[2 * i] = (float)(TWO_POW_M40 / 16.0);
+        scale[2 * i + 1] = (float)(TWO_POW_M40 / 6.0);
+        slot_cells[i] = has_g ? (int)h.npc : 0;
+    }
+    cudaMemcpy(b->d_cell_prefix, b->cell_prefix.data(), sizeof(int64_t) * (nboxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_unit_prefix, b->unit_prefix.data(), sizeof(int64_t) * (nboxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_mchunk_prefix, b->mchunk_prefix.data(), sizeof(int64_t) * (nboxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_cchunk_prefix, b->cchunk_prefix.data(), sizeof(int64_t) * (nboxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_slot_prefix, b->slot_prefix.data(), sizeof(int) * (nboxes + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_scale, scale.data(), sizeof(float) * 2 * nboxes, cudaMemcpyHostToDevice);
+    cudaMemcpy(b->d_slot_cells, slot_cells.data(), sizeof(int) * nboxes, cudaMemcpyHostToDevice);
+    cudaMemset(b->d_have_prev, 0, sizeof(int));
+    cudaMemset(b->d_flags, 0, sizeof(long long) * 4);
+    cudaMemset(b->d_m2_prev, 0, sizeof(double) * 4 * nboxes);
+    cudaMemset(b->d_m2_cur, 0, sizeof(double) * 4 * nboxes);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, BZ_ECUDA, "batch initialisation failed");
+    }
+    *out = b;
+    return BZ_OK;
+}
+
+extern "C" int bz_batch_destroy(bz_batch b)
+{
+    if (!b) return BZ_EINVAL;
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+    return BZ_OK;
+}
+
+extern "C" const char* bz_batch_last_error(bz_batch b) { return b ? b->err.c_str() : g_init_error.c_str(); }
+
+extern "C" int bz_batch_layout(bz_batch b, int64_t* cell_offsets, int32_t* slot_offsets)
+{
+    if (!b) return BZ_EINVAL;
+    for (int i = 0; i <= b->nboxes; ++i) {
+        if (cell_offsets) cell_offsets[i] = b->cell_prefix[i];
+        if (slot_offsets) slot_offsets[i] = b->slot_prefix[i];
+    }
+    return BZ_OK;
+}
+
+extern "C" int bz_batch_get_masses(bz_batch b, double* m2_host)
+{
+    if (!b || !m2_host) return BZ_EINVAL;
+    CKB(b, cudaDeviceSynchronize());
+    CKB(b, cudaMemcpy(m2_host, b->d_m2_cur, sizeof(double) * 4 * b->nboxes, cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
+extern "C" int bz_batch_get_flags(bz_batch b, int64_t* flags_host)
+{
+    if (!b || !flags_host) return BZ_EINVAL;
+    CKB(b, cudaDeviceSynchronize());
+    CKB(b, cudaMemcpy(flags_host, b->d_flags, sizeof(long long) * 4, cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
+extern "C" int bz_batch_tuning(bz_batch b, int32_t* chunk, int32_t* blocks_per_sm, double* ms_collide)
+{
+    if (!b) return BZ_EINVAL;
+    if (chunk) *chunk = b->chunk;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
+    if (ms_collide) *ms_collide = b->tuned_ms;
+    return b->tuned ? BZ_OK : BZ_EINVAL;
+}
+
+// Per-box argument blocks for the state buffer `state` and time step dt.
+static int batch_fill_args(bz_batch b, long long* state, double dt, cudaStream_t s)
+{
+    const int n = b->nboxes;
+    b->a32.assign(n, CollideArgs<float>{});
+    b->a64.assign(n, CollideArgs<double>{});
+    b->mass.assign(n, MassArgs{});
+    b->mom.assign(n, MomentArgs{});
+    for (int i = 0; i < n; ++i) {
+        bz_handle_s* h = &b->hb[i];
+        long long* st = state + b->cell_prefix[i];
+        fill_collide(h, b->a32[i], st, b->desc[i].nsamples, 0, dt, BZ_SAMPLER_SYMMETRIC);
+        fill_collide(h, b->a64[i], st, b->desc[i].nsamples, 0, dt, BZ_SAMPLER_SYMMETRIC);
+        b->a64[i].f_is_float = 1;
+        b->a64[i].ubits = 23;
+        b->a32[i].tau = (float)DEFER_TAU;
+        fill_masses(h, b->mass[i], st, b->d_acc + 4 * i, b->d_m2_cur + 4 * i,
+                    h->mass_mode == BZ_MASS_MASSLESS ? nullptr : b->d_m2_prev + 4 * i);
+        fill_moments(h, b->mom[i], st, nullptr);
+    }
+    CKB(b, cudaMemcpyAsync(b->d_a32, b->a32.data(), sizeof(CollideArgs<float>) * n, cudaMemcpyHostToDevice, s));
+    CKB(b, cudaMemcpyAsync(b->d_a64, b->a64.data(), sizeof(CollideArgs<double>) * n, cudaMemcpyHostToDevice, s));
+    CKB(b, cudaMemcpyAsync(b->d_mass, b->mass.data(), sizeof(MassArgs) * n, cudaMemcpyHostToDevice, s));
+    CKB(b, cudaMemcpyAsync(b->d_mom, b->mom.data(), sizeof(MomentArgs) * n, cudaMemcpyHostToDevice, s));
+    return BZ_OK;
+}
+
+static int batch_collide(bz_batch b, int chunk, int bps, cudaStream_t s)
+{
+    const int grid = b->nsm * bps;
+    CKB(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
+    CKB(b, launch_collide_f32_batch(b->d_a32, b->d_unit_prefix, b->nboxes, b->d_counter, b->d_step, chunk, grid,
+                                    b->d_qcount, b->d_qitems, b->qcap, s));
+    CKB(b, launch_fixup_batch(b->d_a64, b->d_qcount, b->d_qitems, b->qcap, b->d_step, grid * 8, s));
+    return BZ_OK;
+}
+
+static int batch_record_step(bz_batch b, long long* state, double* moments_out, cudaStream_t s)
+{
+    int rc;
+    CKB(b, launch_masses_batch(b->d_mass, b->d_mchunk_prefix, b->nboxes, b->nmchunks, b->d_have_prev, b->d_acc, s));
+    CKB(b, launch_convert_batch(state, b->d_f, b->d_cell_prefix, b->d_cchunk_prefix, b->d_scale, b->d_slot_cells,
+                                b->nboxes, b->ncchunks, s));
+    if ((rc = batch_collide(b, b->chunk, b->bps, s))) return rc;
+    if (moments_out)
+        CKB(b, launch_moments_batch(b->d_mom, b->d_slot_prefix, b->nboxes, b->total_slots, moments_out, b->d_kidx,
+                                    5 * b->total_slots, s));
+    CKB(b, launch_batch_end_step(b->d_m2_prev, b->d_m2_cur, 4 * b->nboxes, b->d_have_prev, b->d_step, b->d_kidx, s));
+    return BZ_OK;
+}
+
+// Autotuner: times the persistent collision launch for each (chunk, blocks
+// per SM) candidate on a copy of the state and keeps the fastest.
+static int batch_autotune(bz_batch b, long long* state, double dt, cudaStream_t s)
+{
+    long long* scratch = nullptr;
+    if (!dalloc(&scratch, b->ncell)) return bfail(b, BZ_ENOMEM, "cannot allocate the tuning copy");
+    int rc = BZ_OK;
+    const int chunks[] = {1, 2, 4, 8, 16};
+    const int bpss[] = {2, 3};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    int zero = 0;
+    do {
+        if (cudaMemcpyAsync(scratch, state, sizeof(long long) * b->ncell, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            rc = bfail(b, BZ_ECUDA, "tuning copy failed");
+            break;
+        }
+        if ((rc = batch_fill_args(b, scratch, dt, s))) break;
+        if (cudaMemcpyAsync(b->d_step, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            rc = bfail(b, BZ_ECUDA, "tuning set-up failed");
+            break;
+        }
+        if (launch_masses_batch(b->d_mass, b->d_mchunk_prefix, b->nboxes, b->nmchunks, b->d_have_prev, b->d_acc, s) !=
+                cudaSuccess ||
+            launch_convert_batch(scratch, b->d_f, b->d_cell_prefix, b->d_cchunk_prefix, b->d_scale, b->d_slot_cells,
+                                 b->nboxes, b->ncchunks, s) != cudaSuccess) {
+            rc = bfail(b, BZ_ECUDA, "tuning set-up launch failed");
+            break;
+        }
+        for (int bps : bpss) {
+            for (int ch : chunks) {
+                if ((rc = batch_collide(b, ch, bps, s))) break;  // warm-up
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 2; ++r)
+                    if ((rc = batch_collide(b, ch, bps, s))) break;
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / 2 < best) {
+                    best = ms / 2;
+                    b->chunk = ch;
+                    b->bps = bps;
+                }
+            }
+            if (rc) break;
+        }
+    } while (0);
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(scratch);
+    cudaMemsetAsync(b->d_flags, 0, sizeof(long long) * 4, s);
+    if (rc) return rc;
+    b->tuned = true;
+    b->tuned_ms = best;
+    b->g_state = nullptr;  // argument blocks now point at the copy: rebuild
+    return BZ_OK;
+}
+
+extern "C" int bz_batch_step(bz_batch b, int64_t* state, double dt, int32_t nsteps, int32_t step0, double* moments_out,
+                             void* stream)
+{
+    if (!b || !state) return BZ_EINVAL;
+    if (nsteps < 0 || step0 < 0 || (int64_t)step0 + nsteps > (1 << 29))
+        return bfail(b, BZ_EINVAL, "steps must stay in [0, 2^29)");
+    if (!(dt > 0)) return bfail(b, BZ_EINVAL, "dt must be positive");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    long long* st = reinterpret_cast<long long*>(state);
+    int rc;
+    if (!b->tuned && (rc = batch_autotune(b, st, dt, s))) return rc;
+    if (b->g_state != st || b->g_mom != moments_out || b->g_dt != dt || !b->exec) {
+        if ((rc = batch_fill_args(b, st, dt, s))) return rc;
+        CKB(b, cudaStreamSynchronize(s));
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CKB(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        rc = batch_record_step(b, st, moments_out, b->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return bfail(b, BZ_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return bfail(b, BZ_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+        b->g_state = st;
+        b->g_mom = moments_out;
+        b->g_dt = dt;
+    }
+    int zero = 0;
+    CKB(b, cudaMemcpyAsync(b->d_step, &step0, sizeof(int), cudaMemcpyHostToDevice, s));
+    CKB(b, cudaMemcpyAsync(b->d_kidx, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < nsteps; ++k) CKB(b, cudaGraphLaunch(b->exec, s));
     return BZ_OK;
 }

@@ -105,6 +105,21 @@ struct MomentArgs {
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
 cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
+cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int64_t* prefix, int nboxes,
+                                     unsigned long long* counter, const int* step_dev, int chunk, int grid,
+                                     int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s);
+cudaError_t launch_fixup_batch(const CollideArgs<double>* boxes, const int* qcount, const unsigned long long* qitems,
+                               int64_t qcap, const int* step_dev, int nseg, cudaStream_t s);
+// batched transport kernels over independent homogeneous boxes
+cudaError_t launch_masses_batch(const MassArgs* boxes, const int64_t* chunk_prefix, int nboxes, int64_t nchunks,
+                                const int* have_prev, long long* acc_all, cudaStream_t s);
+cudaError_t launch_convert_batch(const long long* state, float* f, const int64_t* cell_prefix,
+                                 const int64_t* chunk_prefix, const float* scale, const int* slot_cells, int nboxes,
+                                 int64_t nchunks, cudaStream_t s);
+cudaError_t launch_moments_batch(const MomentArgs* boxes, const int* slot_prefix, int nboxes, int nblocks,
+                                 double* out, const int* kidx, int per_step, cudaStream_t s);
+cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, int* have_prev, int* step_dev,
+                                  int* kidx, cudaStream_t s);
 #ifndef BZ_DEFER_TAU
 #define BZ_DEFER_TAU 1e-3
 #endif

@@ -137,7 +137,7 @@ struct Geom {
 };
 
 template <typename R>
-__device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, int smp, Geom<R>& G)
+__device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, int smp, Geom<R>& G, int step)
 {
     using O = Ops<R>;
     const R L = P.L, twoL = P.twoL;
@@ -149,7 +149,7 @@ __device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, in
     G.xoff = x * npc;
     G.d = P.slot_species[sl];
     const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]), (int)(j % P.np[2])};
-    const uint32_t ctr3 = ((uint32_t)P.step << 3) | (uint32_t)G.d;
+    const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)G.d;
     const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
     const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
     const R u[8] = {O::unif(r0.x, P.ubits), O::unif(r0.y, P.ubits), O::unif(r0.z, P.ubits), O::unif(r0.w, P.ubits),
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ Collide
             const int smp = (int)(item - al * P.nsamples);
             a = P.a_offset + al * P.a_stride;
             Geom<R> G;
-            make_geom(P, a, smp, G);
+            make_geom(P, a, smp, G, P.step);
             const int nt = P.nterms[G.d];
             for (int ti = 0; ti < nt; ++ti) own += eval_term<R, DEFER>(P, G, a, smp, ti, &dq);
         }
@@ -361,7 +361,30 @@ __global__ void __launch_bounds__(256) k_fixup(const __grid_constant__ CollideAr
         const int smp = (int)((it >> 4) & 0xFFFFFu);
         const int ti = (int)(it & 0xFu);
         Geom<R> G;
-        make_geom(P, a, smp, G);
+        make_geom(P, a, smp, G, P.step);
+        const long long own = eval_term<R, false>(P, G, a, smp, ti, nullptr);
+        if (own != 0) red_add(&P.A[a], own);
+    }
+}
+
+// Batch form: the item carries its box (bits 48..63); the step is read from
+// device memory.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fixup_batch(const CollideArgs<R>* __restrict__ boxes, const int* qcount,
+                                                     const unsigned long long* qitems, int64_t qcap, const int* step_dev)
+{
+    const int64_t seg = blockIdx.x;
+    const int n = qcount[seg];
+    const int step = *step_dev;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long it = qitems[seg * qcap + i];
+        const int b = (int)(it >> 48);
+        const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
+        const int smp = (int)((it >> 4) & 0xFFFFFu);
+        const int ti = (int)(it & 0xFu);
+        const CollideArgs<R>& P = boxes[b];
+        Geom<R> G;
+        make_geom(P, a, smp, G, step);
         const long long own = eval_term<R, false>(P, G, a, smp, ti, nullptr);
         if (own != 0) red_add(&P.A[a], own);
     }

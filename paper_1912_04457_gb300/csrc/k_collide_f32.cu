@@ -98,190 +98,204 @@ __device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float 
 
 }  // namespace
 
-__global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__ CollideArgs<float> P)
+// One unit: the anchor of unit / nchunk and its samples [32 chunk, 32 chunk + 32).
+// box_tag is or-ed into queued items (the box index << 48 in a batch).
+__device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
+                                             DeferCtx& dq, unsigned long long box_tag)
 {
-    __shared__ WarpSmem smem[WARPS];
-    __shared__ int s_qcount[WARPS];
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    WarpSmem& S = smem[warp];
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    if (lane == 0) s_qcount[warp] = 0;
-    __syncwarp();
-    DeferCtx dq;
-    dq.s_count = &s_qcount[warp];
-    dq.seg = P.qitems + gw * P.qcap;
-    dq.cap = (int)P.qcap;
-
+    const unsigned lt_mask = (1u << lane) - 1u;
     const float L = P.L, twoL = P.twoL;
     const float inv_dp0 = 1.0f / P.dp[0], inv_dp1 = 1.0f / P.dp[1], inv_dp2 = 1.0f / P.dp[2];
     const int64_t nxc = P.nxc, npc = P.npc;
     const int nchunk = (P.nsamples + 31) >> 5;
-    const int64_t units = P.n_sel * nchunk;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t al = unit / nchunk;
+    const int chunk = (int)(unit - al * nchunk);
+    const int64_t a = P.a_offset + al * P.a_stride;
+    const int sl = (int)(a / (nxc * npc));
+    const int64_t x = (a / npc) % nxc;
+    const int j = (int)(a % npc);
+    const int d = P.slot_species[sl];
+    const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
+    const unsigned xoff = (unsigned)(x * npc);
+    const unsigned slot_stride = (unsigned)(nxc * npc);
+    // warp-uniform masses: lanes 0..4 convert one double each, then broadcast
+    float mv = 0.0f;
+    if (lane < 5) mv = (float)P.m2[x * 4 + (lane < 4 ? lane : 0)];
+    const float mg2 = __shfl_sync(0xffffffffu, mv, 4);
+    float m0 = __shfl_sync(0xffffffffu, mv, 0), m1 = __shfl_sync(0xffffffffu, mv, 1);
+    float m2v = __shfl_sync(0xffffffffu, mv, 2), m3 = __shfl_sync(0xffffffffu, mv, 3);
+    if (P.mass_mode == 1) m0 = m1 = m2v = m3 = 0.0f;
+    const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
 
-    for (int64_t unit = gw; unit < units; unit += nwarps) {
-        const int64_t al = unit / nchunk;
-        const int chunk = (int)(unit - al * nchunk);
-        const int64_t a = P.a_offset + al * P.a_stride;
-        const int sl = (int)(a / (nxc * npc));
-        const int64_t x = (a / npc) % nxc;
-        const int j = (int)(a % npc);
-        const int d = P.slot_species[sl];
-        const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
-        const unsigned xoff = (unsigned)(x * npc);
-        const unsigned slot_stride = (unsigned)(nxc * npc);
-        // warp-uniform masses: lanes 0..4 convert one double each, then broadcast
-        float mv = 0.0f;
-        if (lane < 5) mv = (float)P.m2[x * 4 + (lane < 4 ? lane : 0)];
-        const float mg2 = __shfl_sync(0xffffffffu, mv, 4);
-        float m0 = __shfl_sync(0xffffffffu, mv, 0), m1 = __shfl_sync(0xffffffffu, mv, 1);
-        float m2v = __shfl_sync(0xffffffffu, mv, 2), m3 = __shfl_sync(0xffffffffu, mv, 3);
-        if (P.mass_mode == 1) m0 = m1 = m2v = m3 = 0.0f;
-        const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
+    const int nt = P.nterms[d];
+    if (lane < nt) {
+        const TermDev& T = P.terms[d][lane];
+        S.tm[lane] = make_float4(sel4(T.mslot[0], m0, m1, m2v, m3), sel4(T.mslot[1], m0, m1, m2v, m3),
+                                 sel4(T.mslot[2], m0, m1, m2v, m3), (float)T.sym);
+        S.tinfo[lane] = T.slot[0] | (T.slot[1] << 3) | (T.slot[2] << 6) | (T.quark[0] << 9) | (T.quark[1] << 10)
+                        | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
+    }
+    const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
+    const int smp = chunk * 32 + lane;
+    const bool live = smp < P.nsamples;
+    // ---- sample geometry (one sample per lane) ----
+    {
+        const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
+        const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+        const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+        const float p0 = (-L + ((float)jx + 0.5f) * P.dp[0]) + P.dp[0] * (unif23(r0.x) - 0.5f);
+        const float p1 = (-L + ((float)jy + 0.5f) * P.dp[1]) + P.dp[1] * (unif23(r0.y) - 0.5f);
+        const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
+        const float k1x = -L + twoL * unif23(r0.w);
+        const float k1y = -L + twoL * unif23(r1.x);
+        const float k30 = -L + twoL * unif23(r1.y);
+        const float k31 = -L + twoL * unif23(r1.z);
+        const float k32 = -L + twoL * unif23(r1.w);
+        const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+        const float bx = Px - k1x, by = Py - k1y;
+        S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
+        S.k30[lane] = k30; S.k31[lane] = k31; S.k32[lane] = k32;
+        S.k1x[lane] = k1x; S.k1y[lane] = k1y;
+        S.Pz[lane] = Pz;
+        S.PP[lane] = (Px * Px + Py * Py) + Pz * Pz;
+        S.bx[lane] = bx; S.by[lane] = by;
+        S.a2m[lane] = k1x * k1x + k1y * k1y;
+        S.b2m[lane] = bx * bx + by * by;
+        S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
+        S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+        S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+    }
+    __syncwarp();
+    const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
+    const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY));
+    const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
 
-        const int nt = P.nterms[d];
-        if (lane < nt) {
-            const TermDev& T = P.terms[d][lane];
-            S.tm[lane] = make_float4(sel4(T.mslot[0], m0, m1, m2v, m3), sel4(T.mslot[1], m0, m1, m2v, m3),
-                                     sel4(T.mslot[2], m0, m1, m2v, m3), (float)T.sym);
-            S.tinfo[lane] = T.slot[0] | (T.slot[1] << 3) | (T.slot[2] << 6) | (T.quark[0] << 9) | (T.quark[1] << 10)
-                            | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
-        }
-        const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
-        const int smp = chunk * 32 + lane;
-        const bool live = smp < P.nsamples;
-        // ---- sample geometry (one sample per lane) ----
-        {
-            const uint32_t ctr3 = ((uint32_t)P.step << 3) | (uint32_t)d;
-            const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-            const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-            const float p0 = (-L + ((float)jx + 0.5f) * P.dp[0]) + P.dp[0] * (unif23(r0.x) - 0.5f);
-            const float p1 = (-L + ((float)jy + 0.5f) * P.dp[1]) + P.dp[1] * (unif23(r0.y) - 0.5f);
-            const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
-            const float k1x = -L + twoL * unif23(r0.w);
-            const float k1y = -L + twoL * unif23(r1.x);
-            const float k30 = -L + twoL * unif23(r1.y);
-            const float k31 = -L + twoL * unif23(r1.z);
-            const float k32 = -L + twoL * unif23(r1.w);
-            const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
-            const float bx = Px - k1x, by = Py - k1y;
-            S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
-            S.k30[lane] = k30; S.k31[lane] = k31; S.k32[lane] = k32;
-            S.k1x[lane] = k1x; S.k1y[lane] = k1y;
-            S.Pz[lane] = Pz;
-            S.PP[lane] = (Px * Px + Py * Py) + Pz * Pz;
-            S.bx[lane] = bx; S.by[lane] = by;
-            S.a2m[lane] = k1x * k1x + k1y * k1y;
-            S.b2m[lane] = bx * bx + by * by;
-            S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
-            S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
-            S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
-        }
-        __syncwarp();
-        const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
-        const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY));
-        const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
+    int head = 0, tail = 0;  // ring indices (warp-uniform)
+    long long own = 0;
 
-        int head = 0, tail = 0;  // ring indices (warp-uniform)
-        long long own = 0;
-
-        // phase B on n pending roots starting at head
-        auto process = [&](int n) {
-            if (lane < n) {
-                const int slot_i = (head + lane) & (RING - 1);
-                const int tg = S.tag[slot_i];
-                const int src = tg & 31, ti = tg >> 5;
-                const float z = S.z[slot_i], E3 = S.E3[slot_i], sqH = S.sqH[slot_i];
-                const float4 tmv = S.tm[ti];
-                const int info = S.tinfo[ti];
-                const float ma2 = tmv.x, mc2 = tmv.z;
-                const float Ep = S.Ep[src];
-                const float E = Ep + E3;
-                const float a2 = S.a2m[src] + ma2;
-                const float E1 = sqrtf(a2 + z * z);
-                const float Pz = S.Pz[src];
-                const float dz = Pz - z;
-                const float k1x = S.k1x[src], k1y = S.k1y[src];
-                const float s = E * E - S.PP[src];
-                const float k1k3 = (k1x * S.k30[src] + k1y * S.k31[src]) + z * S.k32[src];
-                const float k1p = (k1x * S.p0[src] + k1y * S.p1[src]) + z * S.p2[src];
-                const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
-                const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
-                if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
-                    red_add(&P.flags[0], 1);
+    // phase B on n pending roots starting at head
+    auto process = [&](int n) {
+        if (lane < n) {
+            const int slot_i = (head + lane) & (RING - 1);
+            const int tg = S.tag[slot_i];
+            const int src = tg & 31, ti = tg >> 5;
+            const float z = S.z[slot_i], E3 = S.E3[slot_i], sqH = S.sqH[slot_i];
+            const float4 tmv = S.tm[ti];
+            const int info = S.tinfo[ti];
+            const float ma2 = tmv.x, mc2 = tmv.z;
+            const float Ep = S.Ep[src];
+            const float E = Ep + E3;
+            const float a2 = S.a2m[src] + ma2;
+            const float E1 = sqrtf(a2 + z * z);
+            const float Pz = S.Pz[src];
+            const float dz = Pz - z;
+            const float k1x = S.k1x[src], k1y = S.k1y[src];
+            const float s = E * E - S.PP[src];
+            const float k1k3 = (k1x * S.k30[src] + k1y * S.k31[src]) + z * S.k32[src];
+            const float k1p = (k1x * S.p0[src] + k1y * S.p1[src]) + z * S.p2[src];
+            const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
+            const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
+            if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
+                red_add(&P.flags[0], 1);
+            } else {
+                const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
+                const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
+                const int lin2 = (binf(S.bx[src], L, inv_dp0, P.np[0]) * P.np[1]
+                                  + binf(S.by[src], L, inv_dp1, P.np[1])) * P.np[2]
+                                 + binf(dz, L, inv_dp2, P.np[2]);
+                const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
+                const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
+                const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
+                float f1, f2, f3, fpp;
+                if (P.analytic) {
+                    const float E2 = E - E1;
+                    f1 = f_equilibrium(P, P.slot_species[info & 7], E1);
+                    f2 = f_equilibrium(P, P.slot_species[(info >> 3) & 7], E2);
+                    f3 = f_equilibrium(P, P.slot_species[(info >> 6) & 7], E3);
+                    fpp = f_equilibrium(P, d, Ep);
                 } else {
-                    const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
-                    const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
-                    const int lin2 = (binf(S.bx[src], L, inv_dp0, P.np[0]) * P.np[1]
-                                      + binf(S.by[src], L, inv_dp1, P.np[1])) * P.np[2]
-                                     + binf(dz, L, inv_dp2, P.np[2]);
-                    const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
-                    const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
-                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
-                    float f1, f2, f3, fpp;
-                    if (P.analytic) {
-                        const float E2 = E - E1;
-                        f1 = f_equilibrium(P, P.slot_species[info & 7], E1);
-                        f2 = f_equilibrium(P, P.slot_species[(info >> 3) & 7], E2);
-                        f3 = f_equilibrium(P, P.slot_species[(info >> 6) & 7], E3);
-                        fpp = f_equilibrium(P, d, Ep);
-                    } else {
-                        const float* F = static_cast<const float*>(P.f);
-                        f1 = __ldg(F + i1);
-                        f2 = __ldg(F + i2);
-                        f3 = __ldg(F + i3);
-                        fpp = fp;
-                    }
-                    const float F1 = (info & (1 << 9)) ? 1.0f - f1 : 1.0f + f1;
-                    const float F2 = (info & (1 << 10)) ? 1.0f - f2 : 1.0f + f2;
-                    const float F3 = (info & (1 << 11)) ? 1.0f - f3 : 1.0f + f3;
-                    const float Fp = (info & (1 << 12)) ? 1.0f - fpp : 1.0f + fpp;
-                    const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
-                    // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
-                    const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
-                    const float wq = tmv.w * W * M2 / den * P.Kown;
-                    if (!(fabsf(wq) < 4611686018427387904.0f)) {
-                        red_add(&P.flags[1], 1);
-                    } else {
-                        const long long q = rint_ll(wq);
-                        if (q != 0) {
-                            own += q;
-                            if (P.sampler == 0) {
-                                red_add(&P.A[i3], q);
-                                red_add(&P.A[i1], -q);
-                                red_add(&P.A[i2], -q);
-                            }
+                    const float* F = static_cast<const float*>(P.f);
+                    f1 = __ldg(F + i1);
+                    f2 = __ldg(F + i2);
+                    f3 = __ldg(F + i3);
+                    fpp = fp;
+                }
+                const float F1 = (info & (1 << 9)) ? 1.0f - f1 : 1.0f + f1;
+                const float F2 = (info & (1 << 10)) ? 1.0f - f2 : 1.0f + f2;
+                const float F3 = (info & (1 << 11)) ? 1.0f - f3 : 1.0f + f3;
+                const float Fp = (info & (1 << 12)) ? 1.0f - fpp : 1.0f + fpp;
+                const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
+                // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
+                const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
+                const float wq = tmv.w * W * M2 / den * P.Kown;
+                if (!(fabsf(wq) < 4611686018427387904.0f)) {
+                    red_add(&P.flags[1], 1);
+                } else {
+                    const long long q = rint_ll(wq);
+                    if (q != 0) {
+                        own += q;
+                        if (P.sampler == 0) {
+                            red_add(&P.A[i3], q);
+                            red_add(&P.A[i1], -q);
+                            red_add(&P.A[i2], -q);
                         }
                     }
                 }
             }
-            head += n;
-            __syncwarp();
-        };
+        }
+        head += n;
+        __syncwarp();
+    };
 
-        for (int ti = 0; ti < nt; ++ti) {
-            // ---- phase A: roots of term ti for this lane's sample ----
-            const float4 tmv = S.tm[ti];
-            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
-            const float Ep = S.Ep[lane];
-            const float E3 = sqrtf(kk3 + mc2);
-            const float E = Ep + E3;
-            const float Pz = S.Pz[lane];
-            const float a2 = S.a2m[lane] + ma2;
-            const float b2 = S.b2m[lane] + mb2;
-            const float D = E * E - Pz * Pz;
-            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
-            const float H = kap * kap - a2 * D;
-            bool v0 = false, v1 = false;
-            float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
-            if ((k2xy_in || marg_xy) && D > 0.0f) {
-                // FP64 re-evaluation of this term when it is ill-conditioned
-                // (|H| < tau kappa^2) or a solved coordinate sits on an edge
-                bool defer = fabsf(H) < P.tau * (kap * kap);
-                bool e0 = false, e1v = false;
-                if (!defer && H > 0.0f) {
+    for (int ti = 0; ti < nt; ++ti) {
+        // ---- phase A: roots of term ti for this lane's sample ----
+        const float4 tmv = S.tm[ti];
+        const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
+        const float Ep = S.Ep[lane];
+        const float E3 = sqrtf(kk3 + mc2);
+        const float E = Ep + E3;
+        const float Pz = S.Pz[lane];
+        const float a2 = S.a2m[lane] + ma2;
+        const float b2 = S.b2m[lane] + mb2;
+        const float D = E * E - Pz * Pz;
+        const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+        const float H = kap * kap - a2 * D;
+        bool v0 = false, v1 = false;
+        float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
+        if ((k2xy_in || marg_xy) && D > 0.0f) {
+            // FP64 re-evaluation of this term when it is ill-conditioned
+            // (|H| < tau kappa^2) or a solved coordinate sits on an edge
+            bool defer = fabsf(H) < P.tau * (kap * kap);
+            bool e0 = false, e1v = false;
+            if (!defer && H > 0.0f) {
+                sqH = sqrtf(H);
+                const float kp = kap * Pz;
+                const float sq = E * sqH;
+                const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                if (Q != 0.0f) {
+                    z0 = Q / D;
+                    z1 = (E * E * a2 - kap * kap) / Q;
+                    const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
+                    e0 = e10 > 0.0f && e10 < E;
+                    e1v = e11 > 0.0f && e11 < E;
+                    const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+                    defer = (marg_xy && (e0 || e1v))
+                            || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
+                            || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
+                }
+            }
+            if (defer) {
+                const int qs = atomicAdd(dq.s_count, 1);
+                if (qs < dq.cap) {
+                    dq.seg[qs] = box_tag | ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
+                } else {
+                    red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
+                    defer = false;
+                }
+            }
+            if (!defer && k2xy_in && H > 0.0f) {
+                if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
                     sqH = sqrtf(H);
                     const float kp = kap * Pz;
                     const float sq = E * sqH;
@@ -292,60 +306,50 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
                         const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
                         e0 = e10 > 0.0f && e10 < E;
                         e1v = e11 > 0.0f && e11 < E;
-                        const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                        defer = (marg_xy && (e0 || e1v))
-                                || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
-                                || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
                     }
                 }
-                if (defer) {
-                    const int qs = atomicAdd(dq.s_count, 1);
-                    if (qs < dq.cap) {
-                        dq.seg[qs] = ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
-                    } else {
-                        red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
-                        defer = false;
-                    }
-                }
-                if (!defer && k2xy_in && H > 0.0f) {
-                    if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
-                        sqH = sqrtf(H);
-                        const float kp = kap * Pz;
-                        const float sq = E * sqH;
-                        const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-                        if (Q != 0.0f) {
-                            z0 = Q / D;
-                            z1 = (E * E * a2 - kap * kap) / Q;
-                            const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
-                            e0 = e10 > 0.0f && e10 < E;
-                            e1v = e11 > 0.0f && e11 < E;
-                        }
-                    }
-                    v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
-                    v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
-                }
+                v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
+                v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
             }
-            // ---- append valid roots to the ring ----
-            const unsigned b0 = __ballot_sync(0xffffffffu, v0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, v1);
-            const int n0 = __popc(b0);
-            if (v0) {
-                const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
-                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
-            }
-            if (v1) {
-                const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
-                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
-            }
-            tail += n0 + __popc(b1);
-            __syncwarp();
-            while (tail - head >= 32) process(32);
         }
-        if (tail > head) process(tail - head);
-        own = warp_sum_ll(own);
-        if (lane == 0 && own != 0) red_add(&P.A[a], own);
+        // ---- append valid roots to the ring ----
+        const unsigned b0 = __ballot_sync(0xffffffffu, v0);
+        const unsigned b1 = __ballot_sync(0xffffffffu, v1);
+        const int n0 = __popc(b0);
+        if (v0) {
+            const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
+            S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
+        }
+        if (v1) {
+            const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
+            S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
+        }
+        tail += n0 + __popc(b1);
         __syncwarp();
+        while (tail - head >= 32) process(32);
     }
+    if (tail > head) process(tail - head);
+    own = warp_sum_ll(own);
+    if (lane == 0 && own != 0) red_add(&P.A[a], own);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__ CollideArgs<float> P)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ int s_qcount[WARPS];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    if (lane == 0) s_qcount[warp] = 0;
+    __syncwarp();
+    DeferCtx dq;
+    dq.s_count = &s_qcount[warp];
+    dq.seg = P.qitems + gw * P.qcap;
+    dq.cap = (int)P.qcap;
+    const int64_t units = P.n_sel * ((P.nsamples + 31) >> 5);
+    for (int64_t unit = gw; unit < units; unit += nwarps) collide_unit(P, unit, P.step, smem[warp], dq, 0ull);
     __syncwarp();
     if (lane == 0) {
         const int c = s_qcount[warp];
@@ -353,9 +357,68 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
     }
 }
 
+// Batch of independent boxes in one persistent launch: warps take chunks of
+// `chunk` units from a global counter over the concatenated unit space
+// (prefix[b] = first unit of box b), so ragged boxes share the GPU evenly.
+// The step index is read from device memory, so a captured graph replays
+// with the same parameters.
+__global__ void __launch_bounds__(256, 3) k_collide_f32_batch(const CollideArgs<float>* __restrict__ boxes,
+                                                              const int64_t* __restrict__ prefix, int nboxes,
+                                                              unsigned long long* counter, const int* step_dev,
+                                                              int chunk, int* qcount, unsigned long long* qitems,
+                                                              long long qcap)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ int s_qcount[WARPS];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
+    if (lane == 0) s_qcount[warp] = 0;
+    __syncwarp();
+    DeferCtx dq;
+    dq.s_count = &s_qcount[warp];
+    dq.seg = qitems + gw * qcap;
+    dq.cap = (int)qcap;
+    const int step = *step_dev;
+    const int64_t total = prefix[nboxes];
+    int b = 0;
+    for (;;) {
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(counter, (unsigned long long)chunk);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if ((int64_t)start >= total) break;
+        const int64_t stop = min((int64_t)start + chunk, total);
+        for (int64_t u = (int64_t)start; u < stop; ++u) {
+            if (u < prefix[b] || u >= prefix[b + 1]) {  // binary search for the box of u
+                int lo = 0, hi = nboxes - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (prefix[mid] <= u) lo = mid; else hi = mid - 1;
+                }
+                b = lo;
+            }
+            collide_unit(boxes[b], u - prefix[b], step, smem[warp], dq, (unsigned long long)b << 48);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const int c = s_qcount[warp];
+        qcount[gw] = c < qcap ? c : (int)qcap;
+    }
+}
+
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
 {
     k_collide_f32w<<<grid, 32 * WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int64_t* prefix, int nboxes,
+                                     unsigned long long* counter, const int* step_dev, int chunk, int grid,
+                                     int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s)
+{
+    k_collide_f32_batch<<<grid, 32 * WARPS, 0, s>>>(boxes, prefix, nboxes, counter, step_dev, chunk, qcount, qitems,
+                                                     qcap);
     return cudaGetLastError();
 }
 

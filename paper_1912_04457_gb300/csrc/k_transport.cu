@@ -41,14 +41,12 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
 // ---------------------------------------------------------------------------
 constexpr int MASS_CHUNK = 2048;
 
-__global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs P)
+// Fixed-point partial sums of one (x cell, chunk of MASS_CHUNK bins) block.
+__device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64_t c0, bool use_prev)
 {
-    const int64_t nchunk = (P.npc + MASS_CHUNK - 1) / MASS_CHUNK;
-    const int64_t x = blockIdx.x / nchunk;
-    const int64_t c0 = (blockIdx.x % nchunk) * MASS_CHUNK;
     const double CA = 3.0, CF = 4.0 / 3.0;
     double m2p[4] = {0.0, 0.0, 0.0, 0.0};
-    if (P.m2_prev)
+    if (use_prev && P.m2_prev)
         for (int i = 0; i < 4; ++i) m2p[i] = P.m2_prev[x * 4 + i];
     long long sg = 0, sq[3] = {0, 0, 0};
     bool ovf = false;
@@ -102,6 +100,41 @@ __global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
         red_add_ll(&P.acc[x * 4 + threadIdx.x], t);
     }
+}
+
+__global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs P)
+{
+    const int64_t nchunk = (P.npc + MASS_CHUNK - 1) / MASS_CHUNK;
+    masses_block(P, blockIdx.x / nchunk, (blockIdx.x % nchunk) * MASS_CHUNK, true);
+}
+
+__device__ __forceinline__ int find_box(const int64_t* prefix, int nboxes, int64_t v)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batch of homogeneous boxes: block -> (box, chunk) through chunk_prefix.
+__global__ void __launch_bounds__(256) k_masses_batch(const MassArgs* __restrict__ boxes,
+                                                      const int64_t* __restrict__ chunk_prefix, int nboxes,
+                                                      const int* have_prev)
+{
+    const int b = find_box(chunk_prefix, nboxes, blockIdx.x);
+    masses_block(boxes[b], 0, (blockIdx.x - chunk_prefix[b]) * MASS_CHUNK, *have_prev != 0);
+}
+
+__global__ void k_masses_finish_batch(const MassArgs* __restrict__ boxes, int nboxes)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nboxes) return;
+    const MassArgs& P = boxes[b];
+    const double inv = 1.0 / (double)(1LL << MASS_SHIFT);
+    P.m2_out[0] = P.pref_g * P.meas * ((double)P.acc[0] * inv);
+    for (int i = 0; i < 3; ++i) P.m2_out[1 + i] = P.pref_q * P.meas * ((double)P.acc[1 + i] * inv);
 }
 
 __global__ void k_masses_finish(const __grid_constant__ MassArgs P)
@@ -255,10 +288,9 @@ __device__ __forceinline__ double i128_to_double(__int128 v)
     return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
 }
 
-__global__ void __launch_bounds__(256) k_moments(const __grid_constant__ MomentArgs P)
+// Exact sums of one (x cell, slot); writes 5 doubles at o.
+__device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, int sl, double* o)
 {
-    const int64_t x = blockIdx.x / P.nslots;
-    const int sl = blockIdx.x % P.nslots;
     const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
     const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
     __int128 v[5] = {0, 0, 0, 0, 0};
@@ -286,16 +318,104 @@ __global__ void __launch_bounds__(256) k_moments(const __grid_constant__ MomentA
         __int128 t[5] = {0, 0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int i = 0; i < 5; ++i) t[i] += red[i][w];
-        double* o = P.out + (x * P.nslots + sl) * 5;
         o[0] = i128_to_double(t[0]) * P.pref;
         o[1] = i128_to_double(t[1]) * P.pref * (1.0 / 16777216.0);
         for (int d = 0; d < 3; ++d) o[2 + d] = i128_to_double(t[2 + d]) * P.pref * P.half_dp[d];
     }
 }
 
+__global__ void __launch_bounds__(256) k_moments(const __grid_constant__ MomentArgs P)
+{
+    const int64_t x = blockIdx.x / P.nslots;
+    const int sl = blockIdx.x % P.nslots;
+    moments_block(P, x, sl, P.out + (x * P.nslots + sl) * 5);
+}
+
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s)
 {
     k_moments<<<(unsigned)(a.nxc * a.nslots), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_zero_ll(long long* p, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0;
+}
+
+cudaError_t launch_masses_batch(const MassArgs* boxes, const int64_t* chunk_prefix, int nboxes, int64_t nchunks,
+                                const int* have_prev, long long* acc_all, cudaStream_t s)
+{
+    k_zero_ll<<<(unsigned)((4 * nboxes + 255) / 256), 256, 0, s>>>(acc_all, 4 * (int64_t)nboxes);
+    k_masses_batch<<<(unsigned)nchunks, 256, 0, s>>>(boxes, chunk_prefix, nboxes, have_prev);
+    k_masses_finish_batch<<<(unsigned)((nboxes + 127) / 128), 128, 0, s>>>(boxes, nboxes);
+    return cudaGetLastError();
+}
+
+// f of the concatenated batch state (FP32): f = n 2^-40 / N_s, block -> (box, chunk of 2048 cells)
+__global__ void __launch_bounds__(256) k_convert_batch(const long long* __restrict__ state, float* __restrict__ f,
+                                                       const int64_t* __restrict__ cell_prefix,
+                                                       const int64_t* __restrict__ chunk_prefix,
+                                                       const float* __restrict__ gluon_first_scale,
+                                                       const int* __restrict__ slot_cells, int nboxes)
+{
+    const int b = find_box(chunk_prefix, nboxes, blockIdx.x);
+    const int64_t base = cell_prefix[b];
+    const int64_t ncell = cell_prefix[b + 1] - base;
+    const int64_t c0 = (blockIdx.x - chunk_prefix[b]) * MASS_CHUNK;
+    const float s0 = gluon_first_scale[2 * b], s1 = gluon_first_scale[2 * b + 1];
+    const int per_slot = slot_cells[b];
+    for (int64_t i = c0 + threadIdx.x; i < c0 + MASS_CHUNK && i < ncell; i += blockDim.x)
+        f[base + i] = __ll2float_rn(state[base + i]) * (i < per_slot ? s0 : s1);
+}
+
+cudaError_t launch_convert_batch(const long long* state, float* f, const int64_t* cell_prefix,
+                                 const int64_t* chunk_prefix, const float* scale, const int* slot_cells, int nboxes,
+                                 int64_t nchunks, cudaStream_t s)
+{
+    k_convert_batch<<<(unsigned)nchunks, 256, 0, s>>>(state, f, cell_prefix, chunk_prefix, scale, slot_cells, nboxes);
+    return cudaGetLastError();
+}
+
+// Moments of every (box, slot): one block each, through slot_prefix; out
+// advances by one step's worth per call index (*kidx).
+__global__ void __launch_bounds__(256) k_moments_batch(const MomentArgs* __restrict__ boxes,
+                                                       const int* __restrict__ slot_prefix, int nboxes,
+                                                       double* out, const int* kidx, int per_step)
+{
+    int lo = 0, hi = nboxes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (slot_prefix[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    moments_block(boxes[lo], 0, (int)blockIdx.x - slot_prefix[lo], out + (int64_t)(*kidx) * per_step + 5 * (int64_t)blockIdx.x);
+}
+
+cudaError_t launch_moments_batch(const MomentArgs* boxes, const int* slot_prefix, int nboxes, int nblocks,
+                                 double* out, const int* kidx, int per_step, cudaStream_t s)
+{
+    k_moments_batch<<<nblocks, 256, 0, s>>>(boxes, slot_prefix, nboxes, out, kidx, per_step);
+    return cudaGetLastError();
+}
+
+// End of a batch step: current masses become the previous ones, step and
+// call-local step index advance.
+__global__ void k_batch_end_step(double* m2_prev, const double* m2_cur, int n, int* have_prev, int* step_dev,
+                                 int* kidx)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) m2_prev[i] = m2_cur[i];
+    if (i == 0) {
+        *have_prev = 1;
+        *step_dev += 1;
+        *kidx += 1;
+    }
+}
+
+cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, int* have_prev, int* step_dev,
+                                  int* kidx, cudaStream_t s)
+{
+    k_batch_end_step<<<(n + 127) / 128, 128, 0, s>>>(m2_prev, m2_cur, n, have_prev, step_dev, kidx);
     return cudaGetLastError();
 }
 

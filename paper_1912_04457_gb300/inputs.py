@@ -141,3 +141,27 @@ def gluon_bump_xp(nxs=16, dx=0.2, n=20, L=2.0, nsamples=256, nsteps=100, dt=0.00
     f = (bump[:, None] * step_f(np_, L, 0.5, 1.0)[None, :]).reshape(1, nxs ** 3, n ** 3)
     return Workload("gluon_bump_x%d^3_p%d^3_N%d" % (nxs, n, nsamples), (nxs,) * 3, dx, np_, L,
                     GLUON_ONLY, 0.3, nsamples, nsteps, dt, seed, f)
+
+
+def batched_boxes(nboxes=64, seed=5, dt=0.01, nsteps=50):
+    """Ensemble of independent homogeneous boxes: grids drawn from {12, 16, 20,
+    24, 32}^3 on [-2, 2) GeV, species sets from {gluons only, 7 species},
+    alpha_s ~ U[0.2, 0.4], Q_s ~ U[0.8, 1.5] GeV, f0 ~ U[0.1, 1.0], samples per
+    cell ~ U{256..1024}.  Gluons start as f0 theta(Q_s - |p|), (anti)quarks
+    empty.  Returns (list of box dicts, list of int64 states, dt, nsteps)."""
+    rng = np.random.default_rng(seed)
+    boxes, states = [], []
+    for i in range(nboxes):
+        n = int(rng.choice([12, 16, 20, 24, 32]))
+        mask = ALL_SPECIES if rng.uniform() < 0.5 else GLUON_ONLY
+        alpha = float(rng.uniform(0.2, 0.4))
+        qs = float(rng.uniform(0.8, 1.5))
+        f0 = float(rng.uniform(0.1, 1.0))
+        N = int(rng.integers(256, 1025))
+        L = 2.0
+        f = np.zeros((bin(mask).count("1"), 1, n ** 3))
+        f[0, 0] = step_f((n, n, n), L, f0, qs)
+        boxes.append({"np_": (n, n, n), "L": L, "species_mask": mask, "nsamples": N, "alpha_s": alpha,
+                      "mass_mode": 0, "box_id": i, "seed": seed, "Qs": qs, "f0": f0})
+        states.append(encode(f, mask))
+    return boxes, states, dt, nsteps
