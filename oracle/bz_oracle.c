@@ -420,13 +420,44 @@ typedef struct {
     int32_t nsamples;        /* N samples per anchor (x-cell, species d, p-cell)     */
     int32_t step;            /* time-step index, part of the Philox counter          */
     double dt;               /* fm/c                                                 */
-    int32_t sampler;         /* 0 symmetrical (4 legs, 1/4 each), 1 plain (own cell) */
+    int32_t sampler;         /* 0 symmetrical (4 legs, 1/4 each), 1 plain (own cell), 2 symmetrical
+                                with samples from a per-anchor proposal density              */
     int32_t ubits;           /* 32: u=(x+1/2)2^-32; 23: u=((x>>9)+1/2)2^-23          */
     int32_t p_center;        /* 1: p at the cell centre (no jitter)                  */
     int64_t anchor_stride;   /* anchors with index % stride == offset are sampled    */
     int64_t anchor_offset;
     const double* u_explicit;/* optional [anchor][sample][8] uniforms replacing Philox */
+    const double* prop;      /* sampler 2: per-anchor proposal (mu3 x3, sigma3, sigma1, alpha, -, -) */
 } bzo_run;
+
+/* Learned-proposal sample: defensive mixture q(y) = alpha/32 + (1 - alpha)
+ * prod_i g_i(y_i) on y = (k1x, k1y, k3)/L in [-1, 1)^5, g_i the logistic
+ * density truncated to [-1, 1) (centre 0 and scale sigma1 for the k1
+ * components, centre mu3 and scale sigma3 for k3); pr = (mu3 x3, sigma3,
+ * sigma1, alpha).  usel < alpha picks the uniform component (y = 2u - 1),
+ * else y_i = mu + sigma logit(Fa + u (Fb - Fa)).  Returns 1/(32 q(y)), the
+ * factor that turns the uniform weight V/N into 1/(N q_x). */
+double bzo_proposal_sample(const double* pr, double usel, const double* u5, double* y)
+{
+    int uni = usel < pr[5];
+    double G = 1.0;
+    for (int i = 0; i < 5; ++i) {
+        double mu = i < 2 ? 0.0 : pr[i - 2];
+        double sg = i < 2 ? pr[4] : pr[3];
+        double Fa = 1.0 / (1.0 + exp((1.0 + mu) / sg)), Fb = 1.0 / (1.0 + exp(-(1.0 - mu) / sg));
+        if (uni) {
+            y[i] = 2.0 * u5[i] - 1.0;
+        } else {
+            double v = Fa + u5[i] * (Fb - Fa);
+            y[i] = mu + sg * log(v / (1.0 - v));
+            if (y[i] < -1.0) y[i] = -1.0;
+            if (y[i] >= 1.0) y[i] = 0.99999994;
+        }
+        double F = 1.0 / (1.0 + exp(-(y[i] - mu) / sg));
+        G *= F * (1.0 - F) / (sg * (Fb - Fa));
+    }
+    return 1.0 / (32.0 * (pr[5] / 32.0 + (1.0 - pr[5]) * G));
+}
 
 static double uniform_of(uint32_t x, int ubits)
 {
@@ -474,9 +505,23 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
             double pc = -L + ((double)jv[i] + 0.5) * dp[i];
             p[i] = r->p_center ? pc : pc + dp[i] * (u[i] - 0.5);
         }
-        double k1x = -L + twoL * u[3];
-        double k1y = -L + twoL * u[4];
-        for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];
+        double k1x, k1y, wfac = 1.0;
+        if (r->sampler == 2) {
+            const double* pr = r->prop + aidx * 8;
+            uint32_t ctr[4] = {0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x,
+                               ((uint32_t)r->step << 3) | (uint32_t)d};
+            uint32_t o[4];
+            bzo_philox4x32_10(ctr, key, o);
+            double y[5];
+            wfac = bzo_proposal_sample(pr, uniform_of(o[0], r->ubits), u + 3, y);
+            k1x = L * y[0];
+            k1y = L * y[1];
+            for (int i = 0; i < 3; ++i) k3[i] = L * y[2 + i];
+        } else {
+            k1x = -L + twoL * u[3];
+            k1y = -L + twoL * u[4];
+            for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];
+        }
         double pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
         double kk3 = (k3[0] * k3[0] + k3[1] * k3[1]) + k3[2] * k3[2];
         int bp[3] = {jv[0], jv[1], jv[2]};
@@ -541,22 +586,22 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
                 double W = gain - F1 * F2 * f3 * fp;
                 double den = fabs(J) * twopi5 * 16.0 * E1 * E2 * E3 * Ep;
                 double ct = T->sym * W * M2 / den;        /* c~ of Eq. (ca), one root */
-                double wq = ct * Kown;                    /* weight in units 2^-40 of N f */
+                double wq = ct * Kown * wfac;             /* weight in units 2^-40 of N f */
                 if (!(fabs(wq) < 4611686018427387904.0)) {
 #pragma omp atomic
                     flags[1] += 1;
                     continue;
                 }
                 int64_t q = llrint(wq);
-                c64 += ct * (Kq * 4.0) * (1.0 / TWO_POW_40);
-                g64 += (T->sym * gain * M2 / den) * (Kq * 4.0) * (1.0 / TWO_POW_40);
+                c64 += ct * (Kq * 4.0) * wfac * (1.0 / TWO_POW_40);
+                g64 += (T->sym * gain * M2 / den) * (Kq * 4.0) * wfac * (1.0 / TWO_POW_40);
                 /* own cell: +q to (d, p) */
                 {
                     int64_t idx = ((int64_t)slot_of(c, sd) * nxc + x) * npc + linp;
 #pragma omp atomic
                     A[idx] += q;
                 }
-                if (r->sampler == 0) {
+                if (r->sampler != 1) {
                     int64_t i3 = ((int64_t)slot_of(c, sc) * nxc + x) * npc + lin3;
                     int64_t i1 = ((int64_t)slot_of(c, sa) * nxc + x) * npc + lin1;
                     int64_t i2 = ((int64_t)slot_of(c, sb) * nxc + x) * npc + lin2;
@@ -569,7 +614,7 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
                 }
                 if (audit) {
                     /* continuous-leg E / P balance of each deposit set */
-                    double w = ct * Kq;
+                    double w = ct * Kq * wfac;
                     audit[0] += w * ((Ep + E3) - (E1 + E2));
                     audit[1] += w * ((p[0] + k3[0]) - (k1[0] + k2[0]));
                     audit[2] += w * ((p[1] + k3[1]) - (k1[1] + k2[1]));

@@ -12,7 +12,7 @@ import numpy as np
 from .build import build_oracle
 
 NSPEC = 7
-SYMMETRIC, PLAIN = 0, 1
+SYMMETRIC, PLAIN, LEARNED = 0, 1, 2
 M_QQP, M_QQ, M_QQB, M_QQB2, M_QQBGG, M_QG, M_GG = range(7)
 
 
@@ -33,6 +33,7 @@ class Run(C.Structure):
         ("sampler", C.c_int32), ("ubits", C.c_int32), ("p_center", C.c_int32),
         ("anchor_stride", C.c_int64), ("anchor_offset", C.c_int64),
         ("u_explicit", C.POINTER(C.c_double)),
+        ("prop", C.POINTER(C.c_double)),
     ]
 
 
@@ -60,6 +61,8 @@ def lib():
         _lib.bzo_moments.argtypes = [P, P, P, P, P]
         _lib.bzo_step.argtypes = [P, P, P, P, C.c_int, P, P]
         _lib.bzo_num_threads.restype = C.c_int
+        _lib.bzo_proposal_sample.argtypes = [P, C.c_double, P, P]
+        _lib.bzo_proposal_sample.restype = C.c_double
         assert _lib.bzo_sizeof_config() == C.sizeof(Config)
         assert _lib.bzo_sizeof_run() == C.sizeof(Run)
     return _lib
@@ -137,7 +140,7 @@ def masses(cfg, state, m2_prev=None):
 
 
 def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=False,
-             anchor_stride=1, anchor_offset=0, u_explicit=None):
+             anchor_stride=1, anchor_offset=0, u_explicit=None, prop=None):
     r = Run()
     r.nsamples = nsamples
     r.step = step
@@ -152,18 +155,25 @@ def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=Fa
         r.u_explicit = r._u_keep.ctypes.data_as(C.POINTER(C.c_double))
     else:
         r.u_explicit = None
+    if prop is not None:
+        r._prop_keep = np.ascontiguousarray(prop, dtype=np.float64)
+        r.prop = r._prop_keep.ctypes.data_as(C.POINTER(C.c_double))
+    else:
+        r.prop = None
     return r
 
 
 def collision(cfg, state, m2, nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32,
               p_center=False, anchor_stride=1, anchor_offset=0, u_explicit=None,
-              want_c64=False, want_audit=False):
+              want_c64=False, want_audit=False, prop=None):
     """Returns dict with A (int64 [slot][x][p]), flags, and optionally C64/G64/audit."""
     ns, nxc, npc = ncells(cfg)
     state = np.ascontiguousarray(state, dtype=np.int64).reshape(-1)
     m2 = np.ascontiguousarray(m2, dtype=np.float64).reshape(nxc, 4)
+    if sampler == LEARNED:
+        assert prop is not None and np.asarray(prop).size == ns * nxc * npc * 8
     run = make_run(nsamples, step, dt, sampler, ubits, p_center, anchor_stride, anchor_offset,
-                   u_explicit)
+                   u_explicit, prop)
     A = np.zeros(ns * nxc * npc, dtype=np.int64)
     C64 = np.zeros(ns * nxc * npc) if want_c64 else None
     G64 = np.zeros(ns * nxc * npc) if want_c64 else None
@@ -225,3 +235,12 @@ def step(cfg, state, m2, first, nsamples, step_index, dt, sampler=SYMMETRIC, ubi
 
 def num_threads():
     return lib().bzo_num_threads()
+
+
+def proposal_sample(prm, usel, u5):
+    """One learned-proposal sample: (y [5], 1/(32 q(y)))."""
+    prm = np.ascontiguousarray(prm, dtype=np.float64)
+    u5 = np.ascontiguousarray(u5, dtype=np.float64)
+    y = np.zeros(5)
+    wf = lib().bzo_proposal_sample(_ptr(prm), float(usel), _ptr(u5), _ptr(y))
+    return y, wf
