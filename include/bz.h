@@ -47,6 +47,7 @@ extern "C" {
 
 #define BZ_SAMPLER_SYMMETRIC 0 /* each root deposits +w/4 to p and k3, -w/4 to k1, k2 (Eq. small c relation) */
 #define BZ_SAMPLER_PLAIN 1     /* usual MC: full weight to the anchor cell only (Fig. 3, 4 "without") */
+#define BZ_SAMPLER_LEARNED 2   /* symmetric deposition, samples from the learned per-anchor proposal (bz_proposal_*) */
 
 #define BZ_MASS_THERMAL 0   /* Eqs. (mg), (mq) every call; E = sqrt(p^2 + m^2) everywhere        */
 #define BZ_MASS_MASSLESS 1  /* thermal m_g^2 as |M|^2 regulator only; E = |p| in kinematics     */
@@ -262,6 +263,57 @@ int bz_collision_term_static(const bz_grid* g, uint32_t species_mask, double alp
                              const int64_t* state, const double* m2_in, double* m2_out, int64_t* A,
                              int32_t nsamples, int32_t step, double dt, void* stream, char* errbuf,
                              int32_t errbuf_len);
+
+/* ------------------------------------------------------------------------
+ * Learned importance-sampling proposal (not in the paper; it changes only
+ * where the samples of Eq. (MC C_gg) fall).  For every anchor a small
+ * network (9 -> 128 -> 128 -> 6, SiLU, BF16 tensor cores with FP32
+ * accumulation) gives the parameters of a density over the normalised box
+ * y = (k1x, k1y, k3)/L in [-1, 1)^5:
+ *   q(y) = alpha/32 + (1 - alpha) prod_i g_i(y_i),  alpha >= 0.1,
+ * g_i logistic densities truncated to [-1, 1) (k1 components centred at 0
+ * with scale sigma1, k3 components centred at mu3 with scale sigma3).  A
+ * sample drawn from q carries the weight c~ L^5 / q(y) instead of c~ (2L)^5,
+ * and its four legs still receive +-w/4, so the estimator stays unbiased
+ * for any q > 0 and Sum A = 0 exactly.  Training maximises the |c~|-weighted
+ * log-likelihood of samples recorded with the uniform sampler
+ * (optimum q ~ |c~|).  Records: struct { int64 anchor; float w; float y[5]; }
+ * (32 bytes), w = sum over the sample's terms and roots of |c~|.
+ * ------------------------------------------------------------------------ */
+/* Number of FP32 parameters of the network (flat: W1[16][128], b1[128],
+ * W2[128][128], b2[128], W3[128][8], b3[8]; W[in][out], unused input rows
+ * 9..15 and output columns 6, 7 are zero). */
+int bz_proposal_nparams(void);
+/* Allocates the network on h and draws Glorot-uniform weights from seed. */
+int bz_proposal_init(bz_handle h, uint64_t seed);
+int bz_proposal_get_params(bz_handle h, float* host);
+int bz_proposal_set_params(bz_handle h, const float* host);
+/* Uniform FP32 sampling of state in record mode: no deposits, no FP64
+ * re-evaluation; for every unit (anchor, 32 samples) whose index is a
+ * multiple of unit_stride one record is appended to records (device,
+ * max_records) for each sample with w > 0 (samples whose roots were all
+ * rejected or fell outside the box carry no information and are skipped).
+ * Record order is not deterministic.  *n_written (host) receives the count,
+ * at most max_records; synchronises.  Errors: BZ_EINVAL for a NULL pointer,
+ * max_records <= 0, unit_stride <= 0 or 2^31 cells or more. */
+int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, int32_t step, double dt, int32_t unit_stride,
+              void* records, int64_t max_records, int64_t* n_written, void* stream);
+/* Loss L = -sum w log q / sum w over records [0, n) and its gradient (device
+ * float [nparams], device float loss), forward and backward on the tensor
+ * cores.  Synchronises (to read sum w). */
+int bz_proposal_grad(bz_handle h, const void* records, int64_t n, float* grad, float* loss, void* stream);
+/* steps Adam steps (lr, beta 0.9/0.999) on consecutive batches of `batch`
+ * records (wrapping); losses_host (may be NULL) receives each step's loss. */
+int bz_proposal_train(bz_handle h, const void* records, int64_t n, int32_t steps, int32_t batch, double lr,
+                      float* losses_host, void* stream);
+/* Runs the network for every anchor of h (8 floats each: mu3 x3, sigma3,
+ * sigma1, alpha, 0, 0); required before BZ_SAMPLER_LEARNED. */
+int bz_proposal_infer(bz_handle h, void* stream);
+/* Reads (out_host) and/or replaces (in_host) the per-anchor parameters,
+ * host float [nslots nx np][8]; synchronises. */
+int bz_proposal_anchor_params(bz_handle h, float* out_host, const float* in_host);
+/* Sampler used by bz_step: BZ_SAMPLER_SYMMETRIC (default) or BZ_SAMPLER_LEARNED. */
+int bz_set_step_sampler(bz_handle h, int32_t sampler);
 
 /* Library version string. */
 const char* bz_version(void);

@@ -21,6 +21,7 @@ UNITS = [
     ("k_collide_f64.cu", ["-fmad=false"]),
     ("k_collide_f32.cu", ["-use_fast_math"]),
     ("k_transport.cu", ["-fmad=false"]),
+    ("k_mlp.cu", []),
     ("bz_api.cu", ["-fmad=false"]),
     ("bz_static.cu", ["-fmad=false"]),
 ]

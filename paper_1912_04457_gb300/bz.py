@@ -16,7 +16,9 @@ LIB_PATH = os.path.join(HERE, "_build", "libbz.so")
 BZ_OK, BZ_EINVAL, BZ_ENOMEM, BZ_ECUDA, BZ_EOVERFLOW, BZ_ENODEV = 0, -1, -2, -3, -4, -5
 PREC_F64, PREC_F32 = 0, 1
 SAMPLER_SYMMETRIC, SAMPLER_PLAIN = 0, 1
+SAMPLER_LEARNED = 2
 MASS_THERMAL, MASS_MASSLESS, MASS_FIXED = 0, 1, 2
+RECORD_BYTES = 32  # struct { int64 anchor; float w; float y[5]; }
 KERNELS = ("masses", "drift", "collide", "fixup", "moments", "convert")
 
 
@@ -70,6 +72,16 @@ SIGNATURES = {
     "bz_batch_tuning": (C.c_int, [_P, _P, _P, _P]),
     "bz_batch_get_masses": (C.c_int, [_P, _P]),
     "bz_batch_get_flags": (C.c_int, [_P, _P]),
+    "bz_proposal_nparams": (C.c_int, []),
+    "bz_proposal_init": (C.c_int, [_P, C.c_uint64]),
+    "bz_proposal_get_params": (C.c_int, [_P, _P]),
+    "bz_proposal_set_params": (C.c_int, [_P, _P]),
+    "bz_record": (C.c_int, [_P, _P, _I32, _I32, _D, _I32, _P, _I64, _P, _P]),
+    "bz_proposal_grad": (C.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "bz_proposal_train": (C.c_int, [_P, _P, _I64, _I32, _I32, _D, _P, _P]),
+    "bz_proposal_infer": (C.c_int, [_P, _P]),
+    "bz_proposal_anchor_params": (C.c_int, [_P, _P, _P]),
+    "bz_set_step_sampler": (C.c_int, [_P, _I32]),
     "bz_version": (C.c_char_p, []),
 }
 
@@ -197,6 +209,61 @@ class Handle:
         self._check(self.lib.bz_profile_read(self.h, ms.ctypes.data_as(C.c_void_p),
                                              cnt.ctypes.data_as(C.c_void_p), n))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+    # -- learned proposal ----------------------------------------------------
+    def proposal_init(self, seed=1):
+        self._check(self.lib.bz_proposal_init(self.h, seed))
+
+    def proposal_params(self):
+        out = np.zeros(self.lib.bz_proposal_nparams(), dtype=np.float32)
+        self._check(self.lib.bz_proposal_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def set_proposal_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.lib.bz_proposal_nparams()
+        self._check(self.lib.bz_proposal_set_params(self.h, p.ctypes.data_as(C.c_void_p)))
+
+    def record(self, state, nsamples, step=0, dt=0.01, unit_stride=1, max_records=1 << 20, stream=None):
+        """Uniform-sampler records (uint8 CUDA tensor of max_records x 32 bytes), count."""
+        import torch
+        rec = torch.empty(max_records * RECORD_BYTES, dtype=torch.uint8, device="cuda")
+        n = C.c_int64()
+        self._check(self.lib.bz_record(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), nsamples,
+                                       step, dt, unit_stride, C.c_void_p(rec.data_ptr()), max_records,
+                                       C.byref(n), _stream_ptr(stream)))
+        return rec, n.value
+
+    def proposal_grad(self, records, n, stream=None):
+        import torch
+        npar = self.lib.bz_proposal_nparams()
+        grad = torch.empty(npar, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        self._check(self.lib.bz_proposal_grad(self.h, C.c_void_p(records.data_ptr()), n,
+                                              C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr()),
+                                              _stream_ptr(stream)))
+        return grad, loss
+
+    def proposal_train(self, records, n, steps, batch=16384, lr=1e-3, stream=None):
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(self.lib.bz_proposal_train(self.h, C.c_void_p(records.data_ptr()), n, steps, batch, lr,
+                                               losses.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return losses[:steps]
+
+    def proposal_infer(self, stream=None):
+        self._check(self.lib.bz_proposal_infer(self.h, _stream_ptr(stream)))
+
+    def anchor_params(self):
+        out = np.zeros((self.ncell, 8), dtype=np.float32)
+        self._check(self.lib.bz_proposal_anchor_params(self.h, out.ctypes.data_as(C.c_void_p), None))
+        return out
+
+    def set_anchor_params(self, prm):
+        prm = np.ascontiguousarray(prm, dtype=np.float32).reshape(self.ncell, 8)
+        self._check(self.lib.bz_proposal_anchor_params(self.h, None, prm.ctypes.data_as(C.c_void_p)))
+
+    def set_step_sampler(self, sampler):
+        self._check(self.lib.bz_set_step_sampler(self.h, sampler))
 
     # -- the hot path -------------------------------------------------------
     def collision_term(self, state, A, nsamples, step=0, dt=0.01, prec=PREC_F64,

@@ -38,6 +38,15 @@ struct bz_handle_s {
     int* d_qcount = nullptr;       // FP32 deferral queue: per-warp counts
     unsigned long long* d_qitems = nullptr;
     int64_t q_warps = 0, q_items = 0;
+    // learned proposal: FP32 master parameters, Adam moments, gradient, per-anchor parameters
+    float *d_prop = nullptr, *d_prop_g = nullptr, *d_prop_m = nullptr, *d_prop_v = nullptr;
+    float* d_anchor_prm = nullptr;
+    float* d_loss = nullptr;
+    double* d_wsum = nullptr;
+    int adam_step = 0;
+    bool anchor_prm_ready = false;
+    int step_sampler = BZ_SAMPLER_SYMMETRIC;
+    unsigned long long* d_rec_count = nullptr;
     // opt-in per-kernel timing: event pairs recorded around each launch
     bool prof = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
@@ -130,6 +139,17 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_state2);
     cudaFree(h->d_qcount);
     cudaFree(h->d_qitems);
+    cudaFree(h->d_prop);
+    cudaFree(h->d_prop_g);
+    cudaFree(h->d_prop_m);
+    cudaFree(h->d_prop_v);
+    cudaFree(h->d_anchor_prm);
+    cudaFree(h->d_loss);
+    cudaFree(h->d_wsum);
+    cudaFree(h->d_rec_count);
+    h->d_rec_count = nullptr;
+    h->d_prop = h->d_prop_g = h->d_prop_m = h->d_prop_v = h->d_anchor_prm = h->d_loss = nullptr;
+    h->d_wsum = nullptr;
     h->d_qcount = nullptr;
     h->d_qitems = nullptr;
     h->q_warps = h->q_items = 0;
@@ -271,7 +291,12 @@ extern "C" int bz_set_species(bz_handle h, uint32_t species_mask, double alpha_s
     h->mass_mode = mass_mode;
     set_slots(h);
     h->have_masses = false;
-    if (h->nslots != old) return alloc_scratch(h);
+    h->anchor_prm_ready = false;
+    if (h->nslots != old) {
+        cudaFree(h->d_anchor_prm);
+        h->d_anchor_prm = nullptr;
+        return alloc_scratch(h);
+    }
     return BZ_OK;
 }
 
@@ -472,6 +497,11 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.f_is_float = sizeof(R) == 4 ? 1 : 0;
     a.ubits = sizeof(R) == 4 ? 23 : 32;
     a.tau = 0;
+    a.prop = h->d_anchor_prm;
+    a.rec = nullptr;
+    a.rec_count = nullptr;
+    a.rec_cap = 0;
+    a.rec_stride = 0;
     a.qcount = nullptr;
     a.qitems = nullptr;
     a.qcap = 0;
@@ -641,8 +671,10 @@ static int check_common(bz_handle h, int nsamples, int step, double dt, int prec
     if (step < 0 || step >= (1 << 29)) return fail(h, BZ_EINVAL, "step must be in [0, 2^29)");
     if (!(dt > 0)) return fail(h, BZ_EINVAL, "dt must be positive");
     if (prec != BZ_PREC_F64 && prec != BZ_PREC_F32) return fail(h, BZ_EINVAL, "bad precision %d", prec);
-    if (sampler != BZ_SAMPLER_SYMMETRIC && sampler != BZ_SAMPLER_PLAIN)
+    if (sampler != BZ_SAMPLER_SYMMETRIC && sampler != BZ_SAMPLER_PLAIN && sampler != BZ_SAMPLER_LEARNED)
         return fail(h, BZ_EINVAL, "bad sampler %d", sampler);
+    if (sampler == BZ_SAMPLER_LEARNED && !h->anchor_prm_ready)
+        return fail(h, BZ_EINVAL, "the learned sampler needs per-anchor proposal parameters (bz_proposal_infer)");
     return BZ_OK;
 }
 
@@ -707,7 +739,7 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
 {
     if (!h || !state) return BZ_EINVAL;
     if (nsteps < 0) return fail(h, BZ_EINVAL, "nsteps must be >= 0");
-    int rc = check_common(h, nsamples, step0, dt, prec, BZ_SAMPLER_SYMMETRIC);
+    int rc = check_common(h, nsamples, step0, dt, prec, h->step_sampler);
     if (rc) return rc;
     if ((int64_t)step0 + nsteps > (1 << 29)) return fail(h, BZ_EINVAL, "step index overflows 2^29");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -723,7 +755,7 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
             ProfScope ps(h, BZ_K_DRIFT, s);
             CK(h, launch_drift(d, s));
         }
-        if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, BZ_SAMPLER_SYMMETRIC, s))) return rc;
+        if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, h->step_sampler, s))) return rc;
         if (moments_out) {
             MomentArgs m{};
             fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5);
@@ -1144,5 +1176,233 @@ extern "C" int bz_batch_step(bz_batch b, int64_t* state, double dt, int32_t nste
     CKB(b, cudaMemcpyAsync(b->d_step, &step0, sizeof(int), cudaMemcpyHostToDevice, s));
     CKB(b, cudaMemcpyAsync(b->d_kidx, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
     for (int k = 0; k < nsteps; ++k) CKB(b, cudaGraphLaunch(b->exec, s));
+    return BZ_OK;
+}
+
+
+// --------------------------------------------------------------------------
+// Learned proposal (network, training, inference)
+// --------------------------------------------------------------------------
+static int prop_alloc(bz_handle h)
+{
+    const int n = mlp_nparam();
+    if (h->d_prop) return BZ_OK;
+    if (!dalloc(&h->d_prop, n) || !dalloc(&h->d_prop_g, n) || !dalloc(&h->d_prop_m, n) ||
+        !dalloc(&h->d_prop_v, n) || !dalloc(&h->d_loss, 1) || !dalloc(&h->d_wsum, 1))
+        return fail(h, BZ_ENOMEM, "cannot allocate the proposal network");
+    CK(h, cudaMemset(h->d_prop_g, 0, sizeof(float) * n));
+    CK(h, cudaMemset(h->d_prop_m, 0, sizeof(float) * n));
+    CK(h, cudaMemset(h->d_prop_v, 0, sizeof(float) * n));
+    return BZ_OK;
+}
+
+static ProposalArgs prop_args(bz_handle h)
+{
+    ProposalArgs A{};
+    A.nxc = h->nxc;
+    A.npc = h->npc;
+    for (int d = 0; d < 3; ++d) A.np[d] = h->g.np[d];
+    A.L = (float)h->g.L;
+    for (int q = 0; q < NSPEC; ++q) A.slot_species[q] = q < h->nslots ? h->slot_species[q] : 0;
+    return A;
+}
+
+extern "C" int bz_proposal_nparams(void) { return mlp_nparam(); }
+
+extern "C" int bz_proposal_init(bz_handle h, uint64_t seed)
+{
+    if (!h) return BZ_EINVAL;
+    int rc = prop_alloc(h);
+    if (rc) return rc;
+    const int H = 128, NIN = 16, NOUT = 8;
+    std::vector<float> p(mlp_nparam(), 0.0f);
+    // uniform(-a, a) with a = sqrt(6 / (fan_in + fan_out)), from a splitmix64 stream
+    uint64_t st = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto uni = [&]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    };
+    float* W1 = p.data();
+    float* W2 = W1 + NIN * H + H;
+    float* W3 = W2 + H * H + H;
+    const double a1 = std::sqrt(6.0 / (9 + H)), a2 = std::sqrt(6.0 / (2 * H)), a3 = 0.1 * std::sqrt(6.0 / (H + 6));
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < H; ++j) W1[i * H + j] = (float)((2 * uni() - 1) * a1);
+    for (int i = 0; i < H * H; ++i) W2[i] = (float)((2 * uni() - 1) * a2);
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < 6; ++j) W3[i * NOUT + j] = (float)((2 * uni() - 1) * a3);
+    CK(h, cudaMemcpy(h->d_prop, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->d_prop_m, 0, sizeof(float) * p.size()));
+    CK(h, cudaMemset(h->d_prop_v, 0, sizeof(float) * p.size()));
+    h->adam_step = 0;
+    h->anchor_prm_ready = false;
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_get_params(bz_handle h, float* host)
+{
+    if (!h || !host || !h->d_prop) return h ? fail(h, BZ_EINVAL, "no proposal network (bz_proposal_init)") : BZ_EINVAL;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(host, h->d_prop, sizeof(float) * mlp_nparam(), cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_set_params(bz_handle h, const float* host)
+{
+    if (!h || !host) return BZ_EINVAL;
+    int rc = prop_alloc(h);
+    if (rc) return rc;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(h->d_prop, host, sizeof(float) * mlp_nparam(), cudaMemcpyHostToDevice));
+    h->anchor_prm_ready = false;
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_grad(bz_handle h, const void* records, int64_t n, float* grad, float* loss, void* stream)
+{
+    if (!h || !records || !grad || !loss || n <= 0) return BZ_EINVAL;
+    if (!h->d_prop) return fail(h, BZ_EINVAL, "no proposal network (bz_proposal_init)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ProposalRecord* rec = static_cast<const ProposalRecord*>(records);
+    CK(h, launch_sum_weights(rec, n, h->d_wsum, s));
+    double wsum = 0;
+    CK(h, cudaMemcpyAsync(&wsum, h->d_wsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (!(wsum > 0)) return fail(h, BZ_EINVAL, "records carry no weight");
+    CK(h, cudaMemsetAsync(grad, 0, sizeof(float) * mlp_nparam(), s));
+    CK(h, cudaMemsetAsync(loss, 0, sizeof(float), s));
+    const int64_t nch = (n + 63) / 64;
+    const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
+    CK(h, launch_mlp_grad(h->d_prop, prop_args(h), rec, n, (float)(1.0 / wsum), grad, loss, grid, s));
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_train(bz_handle h, const void* records, int64_t n, int32_t steps, int32_t batch,
+                                 double lr, float* losses_host, void* stream)
+{
+    if (!h || !records || n <= 0 || steps < 0 || batch <= 0 || !(lr > 0)) return BZ_EINVAL;
+    if (!h->d_prop) return fail(h, BZ_EINVAL, "no proposal network (bz_proposal_init)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const ProposalRecord* rec = static_cast<const ProposalRecord*>(records);
+    CK(h, launch_sum_weights(rec, n, h->d_wsum, s));
+    double wsum = 0;
+    CK(h, cudaMemcpyAsync(&wsum, h->d_wsum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (!(wsum > 0)) return fail(h, BZ_EINVAL, "records carry no weight");
+    const double wbar = wsum / (double)n;
+    const ProposalArgs A = prop_args(h);
+    const int np = mlp_nparam();
+    CK(h, cudaMemsetAsync(h->d_prop_g, 0, sizeof(float) * np, s));
+    int64_t off = 0;
+    for (int k = 0; k < steps; ++k) {
+        int64_t b = std::min<int64_t>(batch, n);
+        if (off + b > n) off = 0;
+        CK(h, cudaMemsetAsync(h->d_loss, 0, sizeof(float), s));
+        const int64_t nch = (b + 63) / 64;
+        const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
+        CK(h, launch_mlp_grad(h->d_prop, A, rec + off, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss,
+                              grid, s));
+        CK(h, launch_adam(h->d_prop, h->d_prop_g, h->d_prop_m, h->d_prop_v, np, (float)lr, ++h->adam_step, s));
+        if (losses_host) CK(h, cudaMemcpyAsync(&losses_host[k], h->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        off += b;
+    }
+    if (losses_host) CK(h, cudaStreamSynchronize(s));
+    h->anchor_prm_ready = false;
+    return BZ_OK;
+}
+
+static int anchor_prm_alloc(bz_handle h)
+{
+    if (!h->d_anchor_prm && !dalloc(&h->d_anchor_prm, 8 * h->ncell))
+        return fail(h, BZ_ENOMEM, "cannot allocate the per-anchor proposal parameters");
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_infer(bz_handle h, void* stream)
+{
+    if (!h) return BZ_EINVAL;
+    if (!h->d_prop) return fail(h, BZ_EINVAL, "no proposal network (bz_proposal_init)");
+    int rc = anchor_prm_alloc(h);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(h, launch_mlp_infer(h->d_prop, prop_args(h), h->ncell, h->d_anchor_prm, h->nsm * 2, s));
+    h->anchor_prm_ready = true;
+    return BZ_OK;
+}
+
+extern "C" int bz_proposal_anchor_params(bz_handle h, float* out_host, const float* in_host)
+{
+    if (!h || (!out_host && !in_host)) return BZ_EINVAL;
+    int rc = anchor_prm_alloc(h);
+    if (rc) return rc;
+    CK(h, cudaDeviceSynchronize());
+    if (in_host) {
+        CK(h, cudaMemcpy(h->d_anchor_prm, in_host, sizeof(float) * 8 * h->ncell, cudaMemcpyHostToDevice));
+        h->anchor_prm_ready = true;
+    }
+    if (out_host) {
+        if (!h->anchor_prm_ready) return fail(h, BZ_EINVAL, "no per-anchor proposal parameters yet");
+        CK(h, cudaMemcpy(out_host, h->d_anchor_prm, sizeof(float) * 8 * h->ncell, cudaMemcpyDeviceToHost));
+    }
+    return BZ_OK;
+}
+
+extern "C" int bz_set_step_sampler(bz_handle h, int32_t sampler)
+{
+    if (!h) return BZ_EINVAL;
+    if (sampler != BZ_SAMPLER_SYMMETRIC && sampler != BZ_SAMPLER_LEARNED)
+        return fail(h, BZ_EINVAL, "bz_step supports the symmetric and learned samplers");
+    h->step_sampler = sampler;
+    return BZ_OK;
+}
+
+extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, int32_t step, double dt,
+                         int32_t unit_stride, void* records, int64_t max_records, int64_t* n_written, void* stream)
+{
+    if (!h || !state || !records || max_records <= 0 || unit_stride <= 0) return BZ_EINVAL;
+    int rc = check_common(h, nsamples, step, dt, BZ_PREC_F32, BZ_SAMPLER_SYMMETRIC);
+    if (rc) return rc;
+    if (h->ncell >= (int64_t)1 << 31) return fail(h, BZ_EINVAL, "record mode needs fewer than 2^31 cells");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long* st = reinterpret_cast<const long long*>(state);
+    if ((rc = compute_masses(h, st, s))) return rc;
+    double deg[NSPEC];
+    for (int sl = 0; sl < NSPEC; ++sl) deg[sl] = kDeg[sl < h->nslots ? h->slot_species[sl] : 0];
+    CK(h, launch_convert(st, h->d_freal, 0, h->nxc, h->npc, h->nslots, deg, s));
+    if (!h->d_qcount && !dalloc(&h->d_qcount, 1)) return fail(h, BZ_ENOMEM, "scratch");
+    if (!h->d_rec_count && !dalloc(&h->d_rec_count, 1)) return fail(h, BZ_ENOMEM, "scratch");
+    unsigned long long* cnt = h->d_rec_count;
+    CK(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    const int64_t n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
+    const int64_t units = n_sel * (int64_t)((nsamples + 31) / 32);
+    int64_t blocks = (units + 7) / 8;
+    if (blocks > (int64_t)h->nsm * 24) blocks = (int64_t)h->nsm * 24;
+    if (blocks < 1) blocks = 1;
+    CollideArgs<float> a{};
+    fill_collide(h, a, nullptr, nsamples, step, dt, BZ_SAMPLER_SYMMETRIC);
+    a.tau = 0.0f;
+    a.rec = static_cast<ProposalRecord*>(records);
+    a.rec_count = cnt;
+    a.rec_cap = max_records;
+    a.rec_stride = unit_stride;
+    // the kernel writes its per-warp queue counts even with no deferral: give it room
+    if ((int64_t)blocks * 8 > h->q_warps) {
+        cudaFree(h->d_qcount);
+        h->d_qcount = nullptr;
+        if (!dalloc(&h->d_qcount, blocks * 8)) return fail(h, BZ_ENOMEM, "scratch");
+        h->q_warps = blocks * 8;
+        if (!h->d_qitems && !dalloc(&h->d_qitems, 1)) return fail(h, BZ_ENOMEM, "scratch");
+    }
+    a.qcount = h->d_qcount;
+    a.qitems = h->d_qitems;
+    a.qcap = 0;
+    CK(h, launch_collide_f32(a, (int)blocks, s));
+    unsigned long long n = 0;
+    CK(h, cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (n_written) *n_written = (int64_t)(n < (unsigned long long)max_records ? n : (unsigned long long)max_records);
     return BZ_OK;
 }

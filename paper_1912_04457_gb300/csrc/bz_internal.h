@@ -30,6 +30,21 @@ struct TermDev {
     double sym;       // 1/2 for identical initial particles
 };
 
+// Learned proposal: anchor description for the network's features, and one
+// training record (anchor, weight sum |c~|, normalised sample y = (k1x, k1y, k3)/L).
+struct ProposalArgs {
+    int64_t nxc, npc;
+    int np[3];
+    float L;
+    int slot_species[NSPEC];
+};
+struct ProposalRecord {
+    int64_t a;
+    float w;
+    float y[5];
+};
+constexpr int SAMPLER_LEARNED = 2;
+
 template <typename R>
 struct CollideArgs {
     const void* f;          // f per cell [slot][x][p] (unused in equilibrium mode)
@@ -51,6 +66,13 @@ struct CollideArgs {
     int slot_species[NSPEC];
     int nterms[NSPEC];
     TermDev terms[NSPEC][MAX_TERMS];
+    // learned sampler: per-anchor proposal (mu3 x3, sigma3, sigma1, alpha, -, -)
+    const float* prop;
+    // record mode (FP32 uniform sampler): per-sample sum of |c~| written to rec
+    ProposalRecord* rec;
+    unsigned long long* rec_count;
+    long long rec_cap;
+    int rec_stride;  // 0: off; else units with index % rec_stride == 0 are recorded
     // FP32 path: terms with |H| < tau kappa^2 are queued per warp for FP64
     R tau;                          // 0: never defer
     int* qcount;                    // [warps] items queued by each warp
@@ -129,6 +151,13 @@ constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2
 #endif
 constexpr int DEFER_CAP_DIV = BZ_DEFER_CAP_DIV;  // queue room: 1/DIV of a warp's term evaluations
 constexpr int MAX_SAMPLES = 1 << 20;
+int mlp_nparam();
+cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
+                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s);
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
+cudaError_t launch_mlp_infer(const float* params, const ProposalArgs& A, int64_t nanchor, float* out, int grid,
+                             cudaStream_t s);
+cudaError_t launch_sum_weights(const ProposalRecord* rec, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_masses(const MassArgs& a, cudaStream_t s);
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);

@@ -134,6 +134,7 @@ struct Geom {
     R p[3], k3[3], k1x, k1y, pp, kk3, Pz, PP, bx, by, a2m, b2m;
     bool k2xy_in;
     R mdisp[4], mg2;
+R wfac;  // learned sampler: 1/(32 q(y)), else 1
 };
 
 template <typename R>
@@ -159,10 +160,39 @@ __device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, in
         const R pc = -L + ((R)jv[i] + R(0.5)) * P.dp[i];
         G.p[i] = P.p_center ? pc : pc + P.dp[i] * (u[i] - R(0.5));
     }
-    G.k1x = -L + twoL * u[3];
-    G.k1y = -L + twoL * u[4];
+    G.wfac = R(1);
+    if (P.sampler == SAMPLER_LEARNED) {
+        // defensive mixture of the uniform density and truncated logistics (per-anchor parameters)
+        const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0,
+                                       P.key1);
+        R prm[6];
+        for (int i = 0; i < 6; ++i) prm[i] = (R)P.prop[a * 8 + i];
+        const bool uni = O::unif(r2.x, P.ubits) < prm[5];
+        R y[5], Gd = R(1);
+        for (int i = 0; i < 5; ++i) {
+            const R mu = i < 2 ? R(0) : prm[i - 2];
+            const R sg = i < 2 ? prm[4] : prm[3];
+            const R Fa = R(1) / (R(1) + O::exp_((R(1) + mu) / sg)), Fb = R(1) / (R(1) + O::exp_(-(R(1) - mu) / sg));
+            if (uni) {
+                y[i] = R(2) * u[3 + i] - R(1);
+            } else {
+                const R v = Fa + u[3 + i] * (Fb - Fa);
+                y[i] = mu + sg * log(v / (R(1) - v));
+                y[i] = y[i] < R(-1) ? R(-1) : (y[i] >= R(1) ? R(0.99999994) : y[i]);
+            }
+            const R F = R(1) / (R(1) + O::exp_(-(y[i] - mu) / sg));
+            Gd *= F * (R(1) - F) / (sg * (Fb - Fa));
+        }
+        G.wfac = R(1) / (R(32) * (prm[5] * (R(1) / R(32)) + (R(1) - prm[5]) * Gd));
+        G.k1x = L * y[0];
+        G.k1y = L * y[1];
+        for (int i = 0; i < 3; ++i) G.k3[i] = L * y[2 + i];
+    } else {
+        G.k1x = -L + twoL * u[3];
+        G.k1y = -L + twoL * u[4];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) G.k3[i] = -L + twoL * u[5 + i];
+        for (int i = 0; i < 3; ++i) G.k3[i] = -L + twoL * u[5 + i];
+    }
     G.pp = (G.p[0] * G.p[0] + G.p[1] * G.p[1]) + G.p[2] * G.p[2];
     G.kk3 = (G.k3[0] * G.k3[0] + G.k3[1] * G.k3[1]) + G.k3[2] * G.k3[2];
     G.lin3 = ((int64_t)bin_of(G.k3[0], L, P.dp[0], P.np[0]) * P.np[1] + bin_of(G.k3[1], L, P.dp[1], P.np[1])) * P.np[2]
@@ -281,7 +311,7 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
         const R W = gain - F1 * F2 * f3 * fp;
         const R den = O::fabs_(J) * P.twopi5 * R(16) * E1 * E2 * E3 * Ep;
         const R ct = (R)T.sym * W * M2 / den;
-        const R wq = ct * P.Kown;
+        const R wq = P.sampler == SAMPLER_LEARNED ? ct * P.Kown * G.wfac : ct * P.Kown;
         if (!(O::fabs_(wq) < O::LIM)) {
             red_add(&P.flags[1], 1);
             continue;
@@ -289,7 +319,7 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
         const long long q = O::rint_(wq);
         if (q == 0) continue;
         own += q;
-        if (P.sampler == 0) {
+        if (P.sampler != 1) {
             red_add(&P.A[i3], q);
             red_add(&P.A[i1], -q);
             red_add(&P.A[i2], -q);

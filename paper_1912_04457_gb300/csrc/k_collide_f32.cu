@@ -30,6 +30,9 @@ struct WarpSmem {
     float p0[32], p1[32], p2[32], k30[32], k31[32], k32[32], k1x[32], k1y[32];
     float Pz[32], PP[32], bx[32], by[32], a2m[32], b2m[32], Ep[32];
     int lin3[32], b1xy[32];       // exact bins of k3 and of (k1x, k1y)
+float wfac[32];               // learned sampler: 1/(32 q(y)); 1 for uniform samples
+float recw[32];               // record mode: sum of |c~| of the lane's sample
+unsigned char marg[32];       // learned sampler: a sampled coordinate sits on a bin edge
     // pending roots
     float z[RING], E3[RING], sqH[RING];
     int tag[RING];                // lane | term << 5
@@ -96,6 +99,21 @@ __device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float 
     return r < nu || r > 1.0f - nu;
 }
 
+// Truncated logistic on [-1, 1): inverse CDF of u and density at y.
+__device__ __forceinline__ float tlog_sample(float u, float mu, float s)
+{
+    const float Fa = 1.0f / (1.0f + __expf((1.0f + mu) / s)), Fb = 1.0f / (1.0f + __expf(-(1.0f - mu) / s));
+    const float v = Fa + u * (Fb - Fa);
+    const float y = mu + s * __logf(v / (1.0f - v));
+    return fminf(fmaxf(y, -1.0f), 0.99999994f);
+}
+__device__ __forceinline__ float tlog_density(float y, float mu, float s)
+{
+    const float Fa = 1.0f / (1.0f + __expf((1.0f + mu) / s)), Fb = 1.0f / (1.0f + __expf(-(1.0f - mu) / s));
+    const float F = 1.0f / (1.0f + __expf(-(y - mu) / s));
+    return F * (1.0f - F) / (s * (Fb - Fa));
+}
+
 }  // namespace
 
 // One unit: the anchor of unit / nchunk and its samples [32 chunk, 32 chunk + 32).
@@ -137,6 +155,16 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                         | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
     }
     const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
+float pm0 = 0.0f, pm1 = 0.0f, pm2 = 0.0f, ps3 = 1.0f, ps1 = 1.0f, pa = 1.0f;
+if (P.sampler == SAMPLER_LEARNED) {
+    const float v = lane < 6 ? __ldg(&P.prop[a * 8 + lane]) : 0.0f;
+    pm0 = __shfl_sync(0xffffffffu, v, 0);
+    pm1 = __shfl_sync(0xffffffffu, v, 1);
+    pm2 = __shfl_sync(0xffffffffu, v, 2);
+    ps3 = __shfl_sync(0xffffffffu, v, 3);
+    ps1 = __shfl_sync(0xffffffffu, v, 4);
+    pa = __shfl_sync(0xffffffffu, v, 5);
+}
     const int smp = chunk * 32 + lane;
     const bool live = smp < P.nsamples;
     // ---- sample geometry (one sample per lane) ----
@@ -147,11 +175,39 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         const float p0 = (-L + ((float)jx + 0.5f) * P.dp[0]) + P.dp[0] * (unif23(r0.x) - 0.5f);
         const float p1 = (-L + ((float)jy + 0.5f) * P.dp[1]) + P.dp[1] * (unif23(r0.y) - 0.5f);
         const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
-        const float k1x = -L + twoL * unif23(r0.w);
-        const float k1y = -L + twoL * unif23(r1.x);
-        const float k30 = -L + twoL * unif23(r1.y);
-        const float k31 = -L + twoL * unif23(r1.z);
-        const float k32 = -L + twoL * unif23(r1.w);
+        float k1x, k1y, k30, k31, k32, wfac = 1.0f;
+        bool margk = false;
+        if (P.sampler == SAMPLER_LEARNED) {
+            // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
+            const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
+                                           P.key0, P.key1);
+            const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
+            float y[5];
+            const bool uni = unif23(r2.x) < pa;
+            float G = 1.0f;
+        #pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
+                const float sg = i < 2 ? ps1 : ps3;
+                y[i] = uni ? 2.0f * uv[i] - 1.0f : tlog_sample(uv[i], mu, sg);
+                G *= tlog_density(y[i], mu, sg);
+            }
+            wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
+            k1x = L * y[0];
+            k1y = L * y[1];
+            k30 = L * y[2];
+            k31 = L * y[3];
+            k32 = L * y[4];
+            margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
+                    near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
+                    near_edge(k32, L, inv_dp2, EDGE_XY);
+        } else {
+            k1x = -L + twoL * unif23(r0.w);
+            k1y = -L + twoL * unif23(r1.x);
+            k30 = -L + twoL * unif23(r1.y);
+            k31 = -L + twoL * unif23(r1.z);
+            k32 = -L + twoL * unif23(r1.w);
+        }
         const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
         const float bx = Px - k1x, by = Py - k1y;
         S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
@@ -163,12 +219,24 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         S.a2m[lane] = k1x * k1x + k1y * k1y;
         S.b2m[lane] = bx * bx + by * by;
         S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
-        S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
-        S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+        if (P.sampler == SAMPLER_LEARNED) {
+            S.lin3[lane] = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                           + binf(k32, L, inv_dp2, P.np[2]);
+            S.b1xy[lane] = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+        } else {
+            S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                           + bin_word(r1.w, P.np[2]);
+            S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+        }
+        S.wfac[lane] = wfac;
+        S.recw[lane] = 0.0f;
+        S.marg[lane] = margk ? 1 : 0;
     }
     __syncwarp();
     const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
-    const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY));
+    const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY)
+                              || S.marg[lane]);
+const bool may_defer = P.tau > 0.0f;
     const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
 
     int head = 0, tail = 0;  // ring indices (warp-uniform)
@@ -228,14 +296,17 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
                 // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                 const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
-                const float wq = tmv.w * W * M2 / den * P.Kown;
-                if (!(fabsf(wq) < 4611686018427387904.0f)) {
+                const float ct = tmv.w * W * M2 / den;
+                const float wq = ct * P.Kown * S.wfac[src];
+                if (P.rec_stride) {  // record mode: sum |c~| per sample, no deposits
+                    atomicAdd(&S.recw[src], fabsf(ct));
+                } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
                     red_add(&P.flags[1], 1);
                 } else {
                     const long long q = rint_ll(wq);
                     if (q != 0) {
                         own += q;
-                        if (P.sampler == 0) {
+                        if (P.sampler != 1) {
                             red_add(&P.A[i3], q);
                             red_add(&P.A[i1], -q);
                             red_add(&P.A[i2], -q);
@@ -266,7 +337,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         if ((k2xy_in || marg_xy) && D > 0.0f) {
             // FP64 re-evaluation of this term when it is ill-conditioned
             // (|H| < tau kappa^2) or a solved coordinate sits on an edge
-            bool defer = fabsf(H) < P.tau * (kap * kap);
+            bool defer = may_defer && fabsf(H) < P.tau * (kap * kap);
             bool e0 = false, e1v = false;
             if (!defer && H > 0.0f) {
                 sqH = sqrtf(H);
@@ -280,9 +351,9 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     e0 = e10 > 0.0f && e10 < E;
                     e1v = e11 > 0.0f && e11 < E;
                     const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                    defer = (marg_xy && (e0 || e1v))
+                    defer = may_defer && ((marg_xy && (e0 || e1v))
                             || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
-                            || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
+                            || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu))));
                 }
             }
             if (defer) {
@@ -329,6 +400,31 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         while (tail - head >= 32) process(32);
     }
     if (tail > head) process(tail - head);
+    if (P.rec_stride) {
+        // samples with at least one accepted root only: a zero weight teaches nothing
+        __syncwarp();
+        if (unit % P.rec_stride == 0) {
+            const bool keep = live && S.recw[lane] > 0.0f;
+            const unsigned keep_mask = __ballot_sync(0xffffffffu, keep);
+            unsigned long long base = 0;
+            if (lane == 0 && keep_mask) base = atomicAdd(P.rec_count, (unsigned long long)__popc(keep_mask));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const unsigned slot = __popc(keep_mask & lt_mask);
+            if (keep && (long long)(base + slot) < P.rec_cap) {
+                ProposalRecord R;
+                R.a = a;
+                R.w = S.recw[lane];
+                R.y[0] = S.k1x[lane] / L;
+                R.y[1] = S.k1y[lane] / L;
+                R.y[2] = S.k30[lane] / L;
+                R.y[3] = S.k31[lane] / L;
+                R.y[4] = S.k32[lane] / L;
+                P.rec[base + slot] = R;
+            }
+        }
+        __syncwarp();
+        return;
+    }
     own = warp_sum_ll(own);
     if (lane == 0 && own != 0) red_add(&P.A[a], own);
     __syncwarp();
