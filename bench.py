@@ -478,22 +478,171 @@ def run_batch(args):
     return 0
 
 
+def run_tts(args):
+    """Time to solution of the collision term at equal MC error on the 7-species
+    32^3 box: FP64 uniform (symmetric and plain deposition) against FP32
+    uniform and FP32 with the learned proposal, trained on records of the
+    uniform sampler at t = 0, 0.25 and 0.5 fm/c.
+
+    The MC error of an unbiased estimator A_N is its spread: eps(N)^2 =
+    E|A_a - A_b|^2 / (2 |C|^2) over independent sample streams a, b, with |C|
+    from the mean of 64 uniform estimates at N = 4096.  eps sqrt(N) is constant, so the
+    samples needed for a target eps are N(eps) = (eps(N) sqrt(N) / eps)^2 and
+    the time to solution is N(eps) times the measured time per sample.  The
+    FP64 and FP32 kernels evaluate the same samples (deviation <= 2e-5 relative
+    L2), so the FP64 paths take the FP32 error curves of the same sampler,
+    checked at one N."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1912_04457_gb300 import build as B
+    B.build()
+    from paper_1912_04457_gb300 import bz
+    from paper_1912_04457_gb300 import inputs as I
+
+    w = I.qgp_box()
+    anchors = w.nslots * w.nxc * w.npc
+    h = bz.Handle(np_=w.np_, L=w.L, seed=w.seed, species_mask=w.species_mask, alpha_s=w.alpha_s)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    st0 = torch.from_numpy(w.state().reshape(-1)).cuda()
+    # states at t = 0, 0.25, 0.5 fm/c (50 steps of 0.005 fm/c each, FP32 symmetric)
+    states, s = [st0.clone()], st0.clone()
+    for k in range(2):
+        h.step(s, w.dt, 50, w.nsamples, bz.PREC_F32, step0=50 * k)
+        states.append(s.clone())
+    torch.cuda.synchronize()
+
+    # training records: 16 uniform samples per anchor at each time, w > 0 kept
+    t0 = time.perf_counter()
+    recs = []
+    for i, st in enumerate(states):
+        h.reset_masses()
+        rec, n = h.record(st, args.rec_samples, step=1 << 20 | i, dt=w.dt, max_records=1 << 23)
+        recs.append(rec[: n * bz.RECORD_BYTES].view(n, bz.RECORD_BYTES))
+    rec = torch.cat(recs)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    rec = rec[torch.randperm(rec.shape[0], device="cuda", generator=gen)].contiguous().view(-1)
+    nrec = rec.numel() // bz.RECORD_BYTES
+    torch.cuda.synchronize()
+    t_rec = time.perf_counter() - t0
+    h.proposal_init(1)
+    t0 = time.perf_counter()
+    losses = h.proposal_train(rec, nrec, args.train_steps, batch=16384, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        return statistics.median(ts)
+
+    t_infer = timed(h.proposal_infer)
+    A = torch.empty_like(st0)
+
+    def call(st, N, step, prec, sampler):
+        h.reset_masses()
+        h.collision_term(st, A, N, step=step, dt=w.dt, prec=prec, sampler=sampler)
+
+    def estimates(st, N, prec, sampler, seeds, base):
+        out = []
+        for sd in range(seeds):
+            call(st, N, base + sd, prec, sampler)
+            out.append(A.to(torch.float64))
+        return out
+
+    def spread(outs):
+        d2 = [float(((outs[i] - outs[j]) ** 2).sum()) for i in range(len(outs)) for j in range(i + 1, len(outs))]
+        return (sum(d2) / len(d2) / 2.0) ** 0.5
+
+    result = {"metric": "time to solution of the collision term at equal MC error (relative L2)",
+              "workload": describe(w), "targets": [1e-2, 3e-3],
+              "training": {"records": nrec, "record_samples_per_anchor": args.rec_samples,
+                           "record_times_fm": [0.0, 0.25, 0.5], "record_s": t_rec,
+                           "train_steps": args.train_steps, "batch": 16384, "train_s": t_train,
+                           "loss_first": float(losses[:50].mean()), "loss_last": float(losses[-50:].mean()),
+                           "infer_ms": 1e3 * t_infer}, "times": {}}
+    Ns = [64, 128, 256, 512, 1024, 2048, 4096]
+    seeds = 8
+    for ti, st in ((0, states[0]), (2, states[2])):
+        ref = torch.zeros_like(st0, dtype=torch.float64)
+        for r in range(64):   # 64 independent N = 4096 estimates = one at N = 262144
+            call(st, 4096, 1 << 16 | r, bz.PREC_F32, bz.SAMPLER_SYMMETRIC)
+            ref += A.to(torch.float64)
+        ref /= 64.0
+        cnorm = float(ref.norm())
+        paths, means = {}, {}
+        samplers = (("f32_symmetric", bz.SAMPLER_SYMMETRIC), ("f32_learned", bz.SAMPLER_LEARNED),
+                    ("f32_plain", bz.SAMPLER_PLAIN))
+        for name, smp in samplers:
+            eps = {}
+            for N in (Ns if ti == 0 else [1024]):
+                outs = estimates(st, N, bz.PREC_F32, smp, seeds, 100 + 10 * N)
+                eps[N] = spread(outs) / cnorm
+                if N == max(eps):
+                    means[name] = sum(outs) / len(outs)
+            tN = timed(lambda: call(st, 1024, 3, bz.PREC_F32, smp))
+            if smp == bz.SAMPLER_LEARNED:
+                tN += t_infer
+            paths[name] = {"eps": eps, "eps_sqrtN": statistics.median(e * N ** 0.5 for N, e in eps.items()),
+                           "s_per_sample": tN / (anchors * 1024)}
+        for name, smp, src in (("f64_symmetric", bz.SAMPLER_SYMMETRIC, "f32_symmetric"),
+                               ("f64_plain", bz.SAMPLER_PLAIN, "f32_plain")):
+            e64 = spread(estimates(st, 64, bz.PREC_F64, smp, 4, 5000)) / cnorm
+            t64 = timed(lambda: call(st, 64, 3, bz.PREC_F64, smp), reps=2)
+            paths[name] = {"eps_check_N64": e64, "eps": paths[src]["eps"], "eps_sqrtN": paths[src]["eps_sqrtN"],
+                           "s_per_sample": t64 / (anchors * 64)}
+        for p in paths.values():
+            p["tts_s"] = {str(e): p["s_per_sample"] * anchors * (p["eps_sqrtN"] / e) ** 2
+                          for e in result["targets"]}
+        # speedup at equal error, N by N: (eps_base / eps_path)^2 x (t_base / t_path)
+        base = paths["f64_symmetric"]
+        for p in paths.values():
+            r = [(base["eps"][N] / p["eps"][N]) ** 2 * base["s_per_sample"] / p["s_per_sample"] for N in p["eps"]]
+            p["speedup_vs_f64_symmetric"] = {"min_over_N": min(r), "median_over_N": statistics.median(r)}
+        # unbiasedness of the learned estimator against the reference
+        nl = max(paths["f32_learned"]["eps"])
+        dev = float((means["f32_learned"] - ref).norm()) / cnorm
+        expect = (paths["f32_learned"]["eps"][nl] ** 2 / seeds
+                  + paths["f32_symmetric"]["eps"][max(paths["f32_symmetric"]["eps"])] ** 2
+                  * max(paths["f32_symmetric"]["eps"]) / (64 * 4096)) ** 0.5
+        result["times"]["t=%.2f fm" % (0.25 * ti)] = {
+            "C_norm": cnorm, "paths": paths,
+            "learned_mean_vs_reference": {"rel_l2": dev, "expected_from_spread": expect, "N": nl, "seeds": seeds}}
+    print(json.dumps(result), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bz", choices=["bz", "reference"])
-    ap.add_argument("--workload", default="qgp", choices=["qgp", "gluon_step", "gluon_bump", "batch"])
+    ap.add_argument("--workload", default="qgp", choices=["qgp", "gluon_step", "gluon_bump", "batch", "tts"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--nsamples", type=int, default=0, help="override samples per cell (small profiling cases)")
+    ap.add_argument("--rec-samples", type=int, default=16, help="tts: uniform samples per anchor recorded")
+    ap.add_argument("--train-steps", type=int, default=3000, help="tts: Adam steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "tts":
+        return run_tts(args)
     return run_bz(args)
 
 

@@ -925,9 +925,10 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
         delete b;
         return bfail(nullptr, BZ_EINVAL, "the batch needs fewer than 2^31 cells");
     }
-    // persistent grid of up to 3 blocks per SM; per-warp queue room for 4% of an even share
-    b->qwarps = (int64_t)b->nsm * 3 * 8;
-    b->qcap = (b->nunits * 32 * MAX_TERMS) / b->qwarps / 25 + 64;
+    // persistent grid of up to 4 blocks per SM; per-warp queue room for 4% of an
+    // even share at 3 blocks per SM (2.7% at 2, 5.3% at 4)
+    b->qwarps = (int64_t)b->nsm * 4 * 8;
+    b->qcap = (b->nunits * 32 * MAX_TERMS) / ((int64_t)b->nsm * 3 * 8) / 25 + 64;
     bool ok = dalloc(&b->d_f, b->ncell) && dalloc(&b->d_m2_cur, 4 * nboxes) && dalloc(&b->d_m2_prev, 4 * nboxes) &&
               dalloc(&b->d_acc, 4 * nboxes) && dalloc(&b->d_flags, 4) && dalloc(&b->d_have_prev, 1) &&
               dalloc(&b->d_step, 1) && dalloc(&b->d_kidx, 1) && dalloc(&b->d_counter, 1) &&
@@ -1083,7 +1084,7 @@ static int batch_autotune(bz_batch b, long long* state, double dt, cudaStream_t 
     if (!dalloc(&scratch, b->ncell)) return bfail(b, BZ_ENOMEM, "cannot allocate the tuning copy");
     int rc = BZ_OK;
     const int chunks[] = {1, 2, 4, 8, 16};
-    const int bpss[] = {2, 3};
+    const int bpss[] = {2, 3, 4};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

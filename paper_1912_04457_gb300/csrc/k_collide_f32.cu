@@ -116,8 +116,13 @@ __device__ __forceinline__ float tlog_density(float y, float mu, float s)
 
 }  // namespace
 
+// Sampling modes, resolved at compile time so that the uniform kernel carries
+// none of the learned-proposal or record-mode state (registers set occupancy).
+enum { M_UNIFORM = 0, M_LEARNED = 1, M_RECORD = 2 };
+
 // One unit: the anchor of unit / nchunk and its samples [32 chunk, 32 chunk + 32).
 // box_tag is or-ed into queued items (the box index << 48 in a batch).
+template <int MODE>
 __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
                                              DeferCtx& dq, unsigned long long box_tag)
 {
@@ -155,16 +160,16 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                         | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
     }
     const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
-float pm0 = 0.0f, pm1 = 0.0f, pm2 = 0.0f, ps3 = 1.0f, ps1 = 1.0f, pa = 1.0f;
-if (P.sampler == SAMPLER_LEARNED) {
-    const float v = lane < 6 ? __ldg(&P.prop[a * 8 + lane]) : 0.0f;
-    pm0 = __shfl_sync(0xffffffffu, v, 0);
-    pm1 = __shfl_sync(0xffffffffu, v, 1);
-    pm2 = __shfl_sync(0xffffffffu, v, 2);
-    ps3 = __shfl_sync(0xffffffffu, v, 3);
-    ps1 = __shfl_sync(0xffffffffu, v, 4);
-    pa = __shfl_sync(0xffffffffu, v, 5);
-}
+    float pm0 = 0.0f, pm1 = 0.0f, pm2 = 0.0f, ps3 = 1.0f, ps1 = 1.0f, pa = 1.0f;
+    if (MODE == M_LEARNED) {  // this anchor's proposal parameters (mu3, sigma3, sigma1, alpha)
+        const float v = lane < 6 ? __ldg(&P.prop[a * 8 + lane]) : 0.0f;
+        pm0 = __shfl_sync(0xffffffffu, v, 0);
+        pm1 = __shfl_sync(0xffffffffu, v, 1);
+        pm2 = __shfl_sync(0xffffffffu, v, 2);
+        ps3 = __shfl_sync(0xffffffffu, v, 3);
+        ps1 = __shfl_sync(0xffffffffu, v, 4);
+        pa = __shfl_sync(0xffffffffu, v, 5);
+    }
     const int smp = chunk * 32 + lane;
     const bool live = smp < P.nsamples;
     // ---- sample geometry (one sample per lane) ----
@@ -177,7 +182,7 @@ if (P.sampler == SAMPLER_LEARNED) {
         const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
         float k1x, k1y, k30, k31, k32, wfac = 1.0f;
         bool margk = false;
-        if (P.sampler == SAMPLER_LEARNED) {
+        if (MODE == M_LEARNED) {
             // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
             const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
                                            P.key0, P.key1);
@@ -219,7 +224,7 @@ if (P.sampler == SAMPLER_LEARNED) {
         S.a2m[lane] = k1x * k1x + k1y * k1y;
         S.b2m[lane] = bx * bx + by * by;
         S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
-        if (P.sampler == SAMPLER_LEARNED) {
+        if (MODE == M_LEARNED) {
             S.lin3[lane] = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
                            + binf(k32, L, inv_dp2, P.np[2]);
             S.b1xy[lane] = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
@@ -228,14 +233,16 @@ if (P.sampler == SAMPLER_LEARNED) {
                            + bin_word(r1.w, P.np[2]);
             S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
         }
-        S.wfac[lane] = wfac;
-        S.recw[lane] = 0.0f;
-        S.marg[lane] = margk ? 1 : 0;
+        if (MODE == M_LEARNED) {
+            S.wfac[lane] = wfac;
+            S.marg[lane] = margk ? 1 : 0;
+        }
+        if (MODE == M_RECORD) S.recw[lane] = 0.0f;
     }
     __syncwarp();
     const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
     const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY)
-                              || S.marg[lane]);
+                              || (MODE == M_LEARNED && S.marg[lane]));
 const bool may_defer = P.tau > 0.0f;
     const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
 
@@ -297,8 +304,8 @@ const bool may_defer = P.tau > 0.0f;
                 // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                 const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
                 const float ct = tmv.w * W * M2 / den;
-                const float wq = ct * P.Kown * S.wfac[src];
-                if (P.rec_stride) {  // record mode: sum |c~| per sample, no deposits
+                const float wq = ct * P.Kown * (MODE == M_LEARNED ? S.wfac[src] : 1.0f);
+                if (MODE == M_RECORD) {  // record mode: sum |c~| per sample, no deposits
                     atomicAdd(&S.recw[src], fabsf(ct));
                 } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
                     red_add(&P.flags[1], 1);
@@ -400,7 +407,7 @@ const bool may_defer = P.tau > 0.0f;
         while (tail - head >= 32) process(32);
     }
     if (tail > head) process(tail - head);
-    if (P.rec_stride) {
+    if (MODE == M_RECORD) {
         // samples with at least one accepted root only: a zero weight teaches nothing
         __syncwarp();
         if (unit % P.rec_stride == 0) {
@@ -430,7 +437,20 @@ const bool may_defer = P.tau > 0.0f;
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__ CollideArgs<float> P)
+// FP32 collision, one warp per unit (an anchor and 32 of its samples).
+// Single box (boxes == nullptr): warps stride over the units of `one`.
+// Batch of independent boxes: warps take chunks of `chunk` units from a
+// global counter over the concatenated unit space (prefix[b] = first unit of
+// box b), so ragged boxes share the GPU evenly; the step index is read from
+// device memory, so a captured graph replays with the same parameters.
+// Both walk through the one call site of collide_unit: a box gives the same
+// bits alone or inside a batch.
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) k_collide_f32(const __grid_constant__ CollideArgs<float> one,
+                                                        const CollideArgs<float>* __restrict__ boxes,
+                                                        const int64_t* __restrict__ prefix, int nboxes,
+                                                        unsigned long long* counter, const int* step_dev, int chunk,
+                                                        int* qcount, unsigned long long* qitems, long long qcap)
 {
     __shared__ WarpSmem smem[WARPS];
     __shared__ int s_qcount[WARPS];
@@ -442,49 +462,23 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32w(const __grid_constant__
     __syncwarp();
     DeferCtx dq;
     dq.s_count = &s_qcount[warp];
-    dq.seg = P.qitems + gw * P.qcap;
-    dq.cap = (int)P.qcap;
-    const int64_t units = P.n_sel * ((P.nsamples + 31) >> 5);
-    for (int64_t unit = gw; unit < units; unit += nwarps) collide_unit(P, unit, P.step, smem[warp], dq, 0ull);
-    __syncwarp();
-    if (lane == 0) {
-        const int c = s_qcount[warp];
-        P.qcount[gw] = c < P.qcap ? c : (int)P.qcap;
-    }
-}
-
-// Batch of independent boxes in one persistent launch: warps take chunks of
-// `chunk` units from a global counter over the concatenated unit space
-// (prefix[b] = first unit of box b), so ragged boxes share the GPU evenly.
-// The step index is read from device memory, so a captured graph replays
-// with the same parameters.
-__global__ void __launch_bounds__(256, 3) k_collide_f32_batch(const CollideArgs<float>* __restrict__ boxes,
-                                                              const int64_t* __restrict__ prefix, int nboxes,
-                                                              unsigned long long* counter, const int* step_dev,
-                                                              int chunk, int* qcount, unsigned long long* qitems,
-                                                              long long qcap)
-{
-    __shared__ WarpSmem smem[WARPS];
-    __shared__ int s_qcount[WARPS];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + warp;
-    if (lane == 0) s_qcount[warp] = 0;
-    __syncwarp();
-    DeferCtx dq;
-    dq.s_count = &s_qcount[warp];
     dq.seg = qitems + gw * qcap;
     dq.cap = (int)qcap;
-    const int step = *step_dev;
-    const int64_t total = prefix[nboxes];
+    const bool batch = boxes != nullptr;
+    const int64_t total = batch ? prefix[nboxes] : one.n_sel * ((one.nsamples + 31) >> 5);
+    const int step = batch ? *step_dev : one.step;
     int b = 0;
+    int64_t u = batch ? 0 : gw, stop = 0;  // next unit; end of the current chunk (batch)
     for (;;) {
-        unsigned long long start = 0;
-        if (lane == 0) start = atomicAdd(counter, (unsigned long long)chunk);
-        start = __shfl_sync(0xffffffffu, start, 0);
-        if ((int64_t)start >= total) break;
-        const int64_t stop = min((int64_t)start + chunk, total);
-        for (int64_t u = (int64_t)start; u < stop; ++u) {
+        if (batch) {
+            if (u >= stop) {
+                unsigned long long start = 0;
+                if (lane == 0) start = atomicAdd(counter, (unsigned long long)chunk);
+                start = __shfl_sync(0xffffffffu, start, 0);
+                if ((int64_t)start >= total) break;
+                u = (int64_t)start;
+                stop = min(u + chunk, total);
+            }
             if (u < prefix[b] || u >= prefix[b + 1]) {  // binary search for the box of u
                 int lo = 0, hi = nboxes - 1;
                 while (lo < hi) {
@@ -493,8 +487,12 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32_batch(const CollideArgs<
                 }
                 b = lo;
             }
-            collide_unit(boxes[b], u - prefix[b], step, smem[warp], dq, (unsigned long long)b << 48);
+        } else if (u >= total) {
+            break;
         }
+        const CollideArgs<float>& P = batch ? boxes[b] : one;
+        collide_unit<MODE>(P, batch ? u - prefix[b] : u, step, smem[warp], dq, (unsigned long long)b << 48);
+        u += batch ? 1 : nwarps;
     }
     __syncwarp();
     if (lane == 0) {
@@ -505,7 +503,15 @@ __global__ void __launch_bounds__(256, 3) k_collide_f32_batch(const CollideArgs<
 
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
 {
-    k_collide_f32w<<<grid, 32 * WARPS, 0, s>>>(a);
+    if (a.rec_stride)
+        k_collide_f32<M_RECORD><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                             a.qitems, a.qcap);
+    else if (a.sampler == SAMPLER_LEARNED)
+        k_collide_f32<M_LEARNED><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                              a.qitems, a.qcap);
+    else
+        k_collide_f32<M_UNIFORM><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                              a.qitems, a.qcap);
     return cudaGetLastError();
 }
 
@@ -513,8 +519,9 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
                                      unsigned long long* counter, const int* step_dev, int chunk, int grid,
                                      int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s)
 {
-    k_collide_f32_batch<<<grid, 32 * WARPS, 0, s>>>(boxes, prefix, nboxes, counter, step_dev, chunk, qcount, qitems,
-                                                     qcap);
+    const CollideArgs<float> none{};
+    k_collide_f32<M_UNIFORM><<<grid, 32 * WARPS, 0, s>>>(none, boxes, prefix, nboxes, counter, step_dev, chunk, qcount,
+                                                          qitems, qcap);
     return cudaGetLastError();
 }
 
