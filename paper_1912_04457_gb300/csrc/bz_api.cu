@@ -567,12 +567,12 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
     // terms queued per warp for FP64.  Cell indices are 32-bit there.
     if (h->ncell >= (int64_t)1 << 31)
         return fail(h, BZ_EINVAL, "the FP32 path needs fewer than 2^31 cells (has %lld)", (long long)h->ncell);
-    const int64_t units = n_sel * (int64_t)((nsamples + 31) / 32);
-    blocks = (units + 7) / 8;
-    if (blocks > (int64_t)h->nsm * 24) blocks = (int64_t)h->nsm * 24;
+    const int64_t units = f32_units(n_sel, nsamples);
+    blocks = (units + F32_WARPS - 1) / F32_WARPS;
+    if (blocks > (int64_t)h->nsm * 48) blocks = (int64_t)h->nsm * 48;
     if (blocks < 1) blocks = 1;
-    const int64_t warps = blocks * 8;
-    const int64_t samples_per_warp = ((units + warps - 1) / warps) * 32;
+    const int64_t warps = blocks * F32_WARPS;
+    const int64_t samples_per_warp = ((units + warps - 1) / warps) * 32 * F32_GROUP;
     const int64_t qcap = samples_per_warp * MAX_TERMS / DEFER_CAP_DIV + 64;
     if (warps > h->q_warps || warps * qcap > h->q_items) {
         cudaFree(h->d_qcount);
@@ -817,7 +817,7 @@ struct bz_batch_s {
     const double* g_mom = nullptr;
     double g_dt = 0;
     bool tuned = false;
-    int chunk = 4, bps = 3;
+    int chunk = 4, bps = 24 / F32_WARPS;
     double tuned_ms = 0;
     std::string err;
 };
@@ -911,7 +911,7 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
         h.ncell = h.nslots * h.npc;
         h.nsm = b->nsm;
         b->cell_prefix[i + 1] = b->cell_prefix[i] + h.ncell;
-        b->unit_prefix[i + 1] = b->unit_prefix[i] + h.ncell * ((d.nsamples + 31) / 32);
+        b->unit_prefix[i + 1] = b->unit_prefix[i] + f32_units(h.ncell, d.nsamples);
         b->mchunk_prefix[i + 1] = b->mchunk_prefix[i] + (h.npc + 2047) / 2048;
         b->cchunk_prefix[i + 1] = b->cchunk_prefix[i] + (h.ncell + 2047) / 2048;
         b->slot_prefix[i + 1] = b->slot_prefix[i] + h.nslots;
@@ -925,10 +925,10 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
         delete b;
         return bfail(nullptr, BZ_EINVAL, "the batch needs fewer than 2^31 cells");
     }
-    // persistent grid of up to 4 blocks per SM; per-warp queue room for 4% of an
-    // even share at 3 blocks per SM (2.7% at 2, 5.3% at 4)
-    b->qwarps = (int64_t)b->nsm * 4 * 8;
-    b->qcap = (b->nunits * 32 * MAX_TERMS) / ((int64_t)b->nsm * 3 * 8) / 25 + 64;
+    // persistent grid of up to 32 warps per SM; per-warp queue room for 4% of an
+    // even share at 24 warps per SM (2.7% at 16, 5.3% at 32)
+    b->qwarps = (int64_t)b->nsm * 32;
+    b->qcap = (b->nunits * 32 * F32_GROUP * MAX_TERMS) / ((int64_t)b->nsm * 24) / 25 + 64;
     bool ok = dalloc(&b->d_f, b->ncell) && dalloc(&b->d_m2_cur, 4 * nboxes) && dalloc(&b->d_m2_prev, 4 * nboxes) &&
               dalloc(&b->d_acc, 4 * nboxes) && dalloc(&b->d_flags, 4) && dalloc(&b->d_have_prev, 1) &&
               dalloc(&b->d_step, 1) && dalloc(&b->d_kidx, 1) && dalloc(&b->d_counter, 1) &&
@@ -1058,7 +1058,7 @@ static int batch_collide(bz_batch b, int chunk, int bps, cudaStream_t s)
     CKB(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
     CKB(b, launch_collide_f32_batch(b->d_a32, b->d_unit_prefix, b->nboxes, b->d_counter, b->d_step, chunk, grid,
                                     b->d_qcount, b->d_qitems, b->qcap, s));
-    CKB(b, launch_fixup_batch(b->d_a64, b->d_qcount, b->d_qitems, b->qcap, b->d_step, grid * 8, s));
+    CKB(b, launch_fixup_batch(b->d_a64, b->d_qcount, b->d_qitems, b->qcap, b->d_step, grid * F32_WARPS, s));
     return BZ_OK;
 }
 
@@ -1084,7 +1084,7 @@ static int batch_autotune(bz_batch b, long long* state, double dt, cudaStream_t 
     if (!dalloc(&scratch, b->ncell)) return bfail(b, BZ_ENOMEM, "cannot allocate the tuning copy");
     int rc = BZ_OK;
     const int chunks[] = {1, 2, 4, 8, 16};
-    const int bpss[] = {2, 3, 4};
+    const int bpss[] = {16 / F32_WARPS, 24 / F32_WARPS, 32 / F32_WARPS};  // 16, 24, 32 warps per SM
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1378,9 +1378,9 @@ extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, in
     unsigned long long* cnt = h->d_rec_count;
     CK(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     const int64_t n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
-    const int64_t units = n_sel * (int64_t)((nsamples + 31) / 32);
-    int64_t blocks = (units + 7) / 8;
-    if (blocks > (int64_t)h->nsm * 24) blocks = (int64_t)h->nsm * 24;
+    const int64_t units = f32_units(n_sel, nsamples);
+    int64_t blocks = (units + F32_WARPS - 1) / F32_WARPS;
+    if (blocks > (int64_t)h->nsm * 48) blocks = (int64_t)h->nsm * 48;
     if (blocks < 1) blocks = 1;
     CollideArgs<float> a{};
     fill_collide(h, a, nullptr, nsamples, step, dt, BZ_SAMPLER_SYMMETRIC);
@@ -1390,11 +1390,11 @@ extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, in
     a.rec_cap = max_records;
     a.rec_stride = unit_stride;
     // the kernel writes its per-warp queue counts even with no deferral: give it room
-    if ((int64_t)blocks * 8 > h->q_warps) {
+    if ((int64_t)blocks * F32_WARPS > h->q_warps) {
         cudaFree(h->d_qcount);
         h->d_qcount = nullptr;
-        if (!dalloc(&h->d_qcount, blocks * 8)) return fail(h, BZ_ENOMEM, "scratch");
-        h->q_warps = blocks * 8;
+        if (!dalloc(&h->d_qcount, blocks * F32_WARPS)) return fail(h, BZ_ENOMEM, "scratch");
+        h->q_warps = blocks * F32_WARPS;
         if (!h->d_qitems && !dalloc(&h->d_qitems, 1)) return fail(h, BZ_ENOMEM, "scratch");
     }
     a.qcount = h->d_qcount;

@@ -143,7 +143,7 @@ cudaError_t launch_moments_batch(const MomentArgs* boxes, const int* slot_prefix
 cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, int* have_prev, int* step_dev,
                                   int* kidx, cudaStream_t s);
 #ifndef BZ_DEFER_TAU
-#define BZ_DEFER_TAU 1e-3
+#define BZ_DEFER_TAU 2e-3
 #endif
 constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2 are re-evaluated in FP64
 #ifndef BZ_DEFER_CAP_DIV
@@ -151,6 +151,15 @@ constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2
 #endif
 constexpr int DEFER_CAP_DIV = BZ_DEFER_CAP_DIV;  // queue room: 1/DIV of a warp's term evaluations
 constexpr int MAX_SAMPLES = 1 << 20;
+// FP32 collision kernel: warps per block, and 32-sample chunks per work unit
+// (an anchor and up to 256 of its samples; the live ones are compacted).
+constexpr int F32_WARPS = 4;
+constexpr int F32_GROUP = 8;
+__host__ __device__ inline int64_t f32_units(int64_t n_sel, int nsamples)
+{
+    const int64_t nchunk = (nsamples + 31) / 32;
+    return n_sel * ((nchunk + F32_GROUP - 1) / F32_GROUP);
+}
 int mlp_nparam();
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
                             float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s);

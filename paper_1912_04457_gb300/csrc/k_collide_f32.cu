@@ -23,19 +23,23 @@ namespace bz {
 namespace {
 
 constexpr int RING = 128;         // pending roots per warp (power of 2)
-constexpr int WARPS = 8;          // warps per block
+constexpr int SBUF = 64;          // buffered live samples per warp (power of 2)
+constexpr int WARPS = F32_WARPS;  // warps per block
+#ifndef BZ_F32_MIN_BLOCKS
+#define BZ_F32_MIN_BLOCKS (24 / WARPS)  // resident blocks per SM the register budget is cut for
+#endif
 
 struct WarpSmem {
-    // sample geometry, [field][lane]
-    float p0[32], p1[32], p2[32], k30[32], k31[32], k32[32], k1x[32], k1y[32];
-    float Pz[32], PP[32], bx[32], by[32], a2m[32], b2m[32], Ep[32];
-    int lin3[32], b1xy[32];       // exact bins of k3 and of (k1x, k1y)
-float wfac[32];               // learned sampler: 1/(32 q(y)); 1 for uniform samples
-float recw[32];               // record mode: sum of |c~| of the lane's sample
-unsigned char marg[32];       // learned sampler: a sampled coordinate sits on a bin edge
+    // live samples (k2 inside the box in x and y, or on its edge), [field][slot]
+    float Ep[SBUF], Pz[SBUF], PP[SBUF], a2m[SBUF], b2m[SBUF], kk3[SBUF];
+    float k13[SBUF], k3z[SBUF], k1p[SBUF], pz[SBUF];  // k1perp.k3perp, k3z, k1perp.pperp, pz
+    int b1xy[SBUF], b2xy[SBUF], lin3[SBUF];           // bins of k1perp, k2perp and k3
+    int meta[SBUF];               // sample index | k2perp inside << 24 | on an edge << 25
+    float wfac[SBUF];             // learned: 1/(32 q(y)); record mode: sum of |c~| of the sample
+    float3 tlc[4];                // learned: tlog_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
     // pending roots
     float z[RING], E3[RING], sqH[RING];
-    int tag[RING];                // lane | term << 5
+    int tag[RING];                // live-sample sequence number | term << 24
     // this unit's terms: masses of the legs and sym, packed leg slots / flags / row
     float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
     int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
@@ -99,19 +103,27 @@ __device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float 
     return r < nu || r > 1.0f - nu;
 }
 
-// Truncated logistic on [-1, 1): inverse CDF of u and density at y.
-__device__ __forceinline__ float tlog_sample(float u, float mu, float s)
+// e^x accurate to a few ulp for any |x|: x log2(e) is split exactly into
+// t + r (t = fl(x log2e_hi), r from the FMA residual of that product plus
+// x log2e_lo, i.e. Dekker's exact product), so the rounding of the argument
+// no longer grows with |x|; then e^x = 2^t (1 + r ln 2) to second order in r.
+__device__ __forceinline__ float exp_split(float x)
 {
-    const float Fa = 1.0f / (1.0f + __expf((1.0f + mu) / s)), Fb = 1.0f / (1.0f + __expf(-(1.0f - mu) / s));
-    const float v = Fa + u * (Fb - Fa);
-    const float y = mu + s * __logf(v / (1.0f - v));
-    return fminf(fmaxf(y, -1.0f), 0.99999994f);
+    const float L2E_HI = 1.44269502162933349609375f;  // log2(e) rounded to FP32
+    const float L2E_LO = 1.92596299e-08f;             // log2(e) - L2E_HI
+    const float t = x * L2E_HI;
+    const float r = fmaf(x, L2E_HI, -t) + x * L2E_LO;
+    return exp2f(t) * fmaf(r, 0.6931471805599453f, 1.0f);
 }
-__device__ __forceinline__ float tlog_density(float y, float mu, float s)
+
+// Truncated logistic on [-1, 1) with centre mu and scale s: Fa = F(-1),
+// cFb = 1 - F(1) and D = F(1) - F(-1), each without cancellation.
+__device__ __forceinline__ float3 tlog_consts(float mu, float s)
 {
-    const float Fa = 1.0f / (1.0f + __expf((1.0f + mu) / s)), Fb = 1.0f / (1.0f + __expf(-(1.0f - mu) / s));
-    const float F = 1.0f / (1.0f + __expf(-(y - mu) / s));
-    return F * (1.0f - F) / (s * (Fb - Fa));
+    const float Fa = 1.0f / (1.0f + exp_split((1.0f + mu) / s));
+    const float cFb = 1.0f / (1.0f + exp_split((1.0f - mu) / s));
+    const float Fb = 1.0f / (1.0f + exp_split(-(1.0f - mu) / s));
+    return make_float3(Fa, cFb, Fb - Fa);
 }
 
 }  // namespace
@@ -120,8 +132,12 @@ __device__ __forceinline__ float tlog_density(float y, float mu, float s)
 // none of the learned-proposal or record-mode state (registers set occupancy).
 enum { M_UNIFORM = 0, M_LEARNED = 1, M_RECORD = 2 };
 
-// One unit: the anchor of unit / nchunk and its samples [32 chunk, 32 chunk + 32).
-// box_tag is or-ed into queued items (the box index << 48 in a batch).
+// One unit: the anchor of unit / ngroup and its samples of the chunks
+// [F32_GROUP g, F32_GROUP (g + 1)) of 32.  Samples whose k2perp falls outside
+// the box (they contribute nothing to any term) are dropped, the others are
+// compacted into the live-sample buffer, and the roots are solved on full
+// warps of live samples.  box_tag is or-ed into queued items (the box index
+// << 48 in a batch).
 template <int MODE>
 __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
                                              DeferCtx& dq, unsigned long long box_tag)
@@ -132,8 +148,10 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     const float inv_dp0 = 1.0f / P.dp[0], inv_dp1 = 1.0f / P.dp[1], inv_dp2 = 1.0f / P.dp[2];
     const int64_t nxc = P.nxc, npc = P.npc;
     const int nchunk = (P.nsamples + 31) >> 5;
-    const int64_t al = unit / nchunk;
-    const int chunk = (int)(unit - al * nchunk);
+    const int ngroup = (nchunk + F32_GROUP - 1) / F32_GROUP;
+    const int64_t al = unit / ngroup;
+    const int grp = (int)(unit - al * ngroup);
+    const int c0 = grp * F32_GROUP, c1 = min(c0 + F32_GROUP, nchunk);
     const int64_t a = P.a_offset + al * P.a_stride;
     const int sl = (int)(a / (nxc * npc));
     const int64_t x = (a / npc) % nxc;
@@ -169,93 +187,28 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         ps3 = __shfl_sync(0xffffffffu, v, 3);
         ps1 = __shfl_sync(0xffffffffu, v, 4);
         pa = __shfl_sync(0xffffffffu, v, 5);
+        if (lane < 4) S.tlc[lane] = tlog_consts(lane == 0 ? 0.0f : (lane == 1 ? pm0 : (lane == 2 ? pm1 : pm2)),
+                                               lane == 0 ? ps1 : ps3);
     }
-    const int smp = chunk * 32 + lane;
-    const bool live = smp < P.nsamples;
-    // ---- sample geometry (one sample per lane) ----
-    {
-        const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
-        const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-        const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-        const float p0 = (-L + ((float)jx + 0.5f) * P.dp[0]) + P.dp[0] * (unif23(r0.x) - 0.5f);
-        const float p1 = (-L + ((float)jy + 0.5f) * P.dp[1]) + P.dp[1] * (unif23(r0.y) - 0.5f);
-        const float p2 = (-L + ((float)jz + 0.5f) * P.dp[2]) + P.dp[2] * (unif23(r0.z) - 0.5f);
-        float k1x, k1y, k30, k31, k32, wfac = 1.0f;
-        bool margk = false;
-        if (MODE == M_LEARNED) {
-            // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
-            const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
-                                           P.key0, P.key1);
-            const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
-            float y[5];
-            const bool uni = unif23(r2.x) < pa;
-            float G = 1.0f;
-        #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
-                const float sg = i < 2 ? ps1 : ps3;
-                y[i] = uni ? 2.0f * uv[i] - 1.0f : tlog_sample(uv[i], mu, sg);
-                G *= tlog_density(y[i], mu, sg);
-            }
-            wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
-            k1x = L * y[0];
-            k1y = L * y[1];
-            k30 = L * y[2];
-            k31 = L * y[3];
-            k32 = L * y[4];
-            margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
-                    near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
-                    near_edge(k32, L, inv_dp2, EDGE_XY);
-        } else {
-            k1x = -L + twoL * unif23(r0.w);
-            k1y = -L + twoL * unif23(r1.x);
-            k30 = -L + twoL * unif23(r1.y);
-            k31 = -L + twoL * unif23(r1.z);
-            k32 = -L + twoL * unif23(r1.w);
-        }
-        const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
-        const float bx = Px - k1x, by = Py - k1y;
-        S.p0[lane] = p0; S.p1[lane] = p1; S.p2[lane] = p2;
-        S.k30[lane] = k30; S.k31[lane] = k31; S.k32[lane] = k32;
-        S.k1x[lane] = k1x; S.k1y[lane] = k1y;
-        S.Pz[lane] = Pz;
-        S.PP[lane] = (Px * Px + Py * Py) + Pz * Pz;
-        S.bx[lane] = bx; S.by[lane] = by;
-        S.a2m[lane] = k1x * k1x + k1y * k1y;
-        S.b2m[lane] = bx * bx + by * by;
-        S.Ep[lane] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
-        if (MODE == M_LEARNED) {
-            S.lin3[lane] = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
-                           + binf(k32, L, inv_dp2, P.np[2]);
-            S.b1xy[lane] = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
-        } else {
-            S.lin3[lane] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
-                           + bin_word(r1.w, P.np[2]);
-            S.b1xy[lane] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
-        }
-        if (MODE == M_LEARNED) {
-            S.wfac[lane] = wfac;
-            S.marg[lane] = margk ? 1 : 0;
-        }
-        if (MODE == M_RECORD) S.recw[lane] = 0.0f;
-    }
+    const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
+    const float pc0 = -L + ((float)jx + 0.5f) * P.dp[0];
+    const float pc1 = -L + ((float)jy + 0.5f) * P.dp[1];
+    const float pc2 = -L + ((float)jz + 0.5f) * P.dp[2];
+    const bool may_defer = P.tau > 0.0f;
     __syncwarp();
-    const bool k2xy_in = live && in_box(S.bx[lane], L) && in_box(S.by[lane], L);
-    const bool marg_xy = live && (near_edge(S.bx[lane], L, inv_dp0, EDGE_XY) || near_edge(S.by[lane], L, inv_dp1, EDGE_XY)
-                              || (MODE == M_LEARNED && S.marg[lane]));
-const bool may_defer = P.tau > 0.0f;
-    const float kk3 = (S.k30[lane] * S.k30[lane] + S.k31[lane] * S.k31[lane]) + S.k32[lane] * S.k32[lane];
 
-    int head = 0, tail = 0;  // ring indices (warp-uniform)
+    int c = c0;               // next chunk of 32 samples to draw
+    int nlive = 0, cons = 0;  // live samples buffered / taken by phase A (sequence numbers)
+    int head = 0, tail = 0;   // ring indices (warp-uniform)
     long long own = 0;
 
     // phase B on n pending roots starting at head
     auto process = [&](int n) {
         if (lane < n) {
-            const int slot_i = (head + lane) & (RING - 1);
-            const int tg = S.tag[slot_i];
-            const int src = tg & 31, ti = tg >> 5;
-            const float z = S.z[slot_i], E3 = S.E3[slot_i], sqH = S.sqH[slot_i];
+            const int ri = (head + lane) & (RING - 1);
+            const int tg = S.tag[ri];
+            const int src = tg & (SBUF - 1), ti = tg >> 24;
+            const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
             const float4 tmv = S.tm[ti];
             const int info = S.tinfo[ti];
             const float ma2 = tmv.x, mc2 = tmv.z;
@@ -263,12 +216,10 @@ const bool may_defer = P.tau > 0.0f;
             const float E = Ep + E3;
             const float a2 = S.a2m[src] + ma2;
             const float E1 = sqrtf(a2 + z * z);
-            const float Pz = S.Pz[src];
-            const float dz = Pz - z;
-            const float k1x = S.k1x[src], k1y = S.k1y[src];
+            const float dz = S.Pz[src] - z;
             const float s = E * E - S.PP[src];
-            const float k1k3 = (k1x * S.k30[src] + k1y * S.k31[src]) + z * S.k32[src];
-            const float k1p = (k1x * S.p0[src] + k1y * S.p1[src]) + z * S.p2[src];
+            const float k1k3 = S.k13[src] + z * S.k3z[src];
+            const float k1p = S.k1p[src] + z * S.pz[src];
             const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
             const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
             if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
@@ -276,9 +227,7 @@ const bool may_defer = P.tau > 0.0f;
             } else {
                 const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
                 const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
-                const int lin2 = (binf(S.bx[src], L, inv_dp0, P.np[0]) * P.np[1]
-                                  + binf(S.by[src], L, inv_dp1, P.np[1])) * P.np[2]
-                                 + binf(dz, L, inv_dp2, P.np[2]);
+                const int lin2 = S.b2xy[src] * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
                 const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
                 const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
                 const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
@@ -306,7 +255,7 @@ const bool may_defer = P.tau > 0.0f;
                 const float ct = tmv.w * W * M2 / den;
                 const float wq = ct * P.Kown * (MODE == M_LEARNED ? S.wfac[src] : 1.0f);
                 if (MODE == M_RECORD) {  // record mode: sum |c~| per sample, no deposits
-                    atomicAdd(&S.recw[src], fabsf(ct));
+                    atomicAdd(&S.wfac[src], fabsf(ct));
                 } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
                     red_add(&P.flags[1], 1);
                 } else {
@@ -326,54 +275,45 @@ const bool may_defer = P.tau > 0.0f;
         __syncwarp();
     };
 
-    for (int ti = 0; ti < nt; ++ti) {
-        // ---- phase A: roots of term ti for this lane's sample ----
-        const float4 tmv = S.tm[ti];
-        const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
-        const float Ep = S.Ep[lane];
-        const float E3 = sqrtf(kk3 + mc2);
-        const float E = Ep + E3;
-        const float Pz = S.Pz[lane];
-        const float a2 = S.a2m[lane] + ma2;
-        const float b2 = S.b2m[lane] + mb2;
-        const float D = E * E - Pz * Pz;
-        const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
-        const float H = kap * kap - a2 * D;
-        bool v0 = false, v1 = false;
-        float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
-        if ((k2xy_in || marg_xy) && D > 0.0f) {
-            // FP64 re-evaluation of this term when it is ill-conditioned
-            // (|H| < tau kappa^2) or a solved coordinate sits on an edge
-            bool defer = may_defer && fabsf(H) < P.tau * (kap * kap);
-            bool e0 = false, e1v = false;
-            if (!defer && H > 0.0f) {
-                sqH = sqrtf(H);
-                const float kp = kap * Pz;
-                const float sq = E * sqH;
-                const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-                if (Q != 0.0f) {
-                    z0 = Q / D;
-                    z1 = (E * E * a2 - kap * kap) / Q;
-                    const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
-                    e0 = e10 > 0.0f && e10 < E;
-                    e1v = e11 > 0.0f && e11 < E;
-                    const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                    defer = may_defer && ((marg_xy && (e0 || e1v))
-                            || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
-                            || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu))));
-                }
-            }
-            if (defer) {
-                const int qs = atomicAdd(dq.s_count, 1);
-                if (qs < dq.cap) {
-                    dq.seg[qs] = box_tag | ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
-                } else {
-                    red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
-                    defer = false;
-                }
-            }
-            if (!defer && k2xy_in && H > 0.0f) {
-                if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
+    // One loop with a single site per phase, so the code stays small enough
+    // for the instruction cache.  In order of priority: evaluate 32 pending
+    // roots (or all of them during a flush); solve the next term of the
+    // running batch of <= 32 live samples; start a batch; draw the next chunk
+    // of 32 samples into the live-sample buffer.
+    int bstart = 0, bcnt = 0, ti = -1;  // running batch: first sequence number, size, next term (-1: none)
+    bool flush = false, rec_due = false;
+    float bEp = 0.0f, bPz = 0.0f, ba2m = 0.0f, bb2m = 0.0f, bkk3 = 0.0f;
+    int bmeta = 0;
+    for (;;) {
+        const int pend = tail - head;
+        if (pend >= 32 || (flush && pend > 0)) {
+            process(min(pend, 32));
+            continue;
+        }
+        flush = false;
+        if (ti >= 0 && ti < nt) {
+            // ---- phase A: roots of term ti for this lane's live sample ----
+            const bool act = lane < bcnt;
+            const int seq = bstart + lane;
+            const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
+            const float4 tmv = S.tm[ti];
+            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
+            const float E3 = sqrtf(bkk3 + mc2);
+            const float E = bEp + E3;
+            const float Pz = bPz;
+            const float a2 = ba2m + ma2;
+            const float b2 = bb2m + mb2;
+            const float D = E * E - Pz * Pz;
+            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+            const float H = kap * kap - a2 * D;
+            bool v0 = false, v1 = false;
+            float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
+            if (act && D > 0.0f) {
+                // FP64 re-evaluation of this term when it is ill-conditioned
+                // (|H| < tau kappa^2) or a solved coordinate sits on an edge
+                bool defer = may_defer && fabsf(H) < P.tau * (kap * kap);
+                bool e0 = false, e1v = false;
+                if (!defer && H > 0.0f) {
                     sqH = sqrtf(H);
                     const float kp = kap * Pz;
                     const float sq = E * sqH;
@@ -384,60 +324,227 @@ const bool may_defer = P.tau > 0.0f;
                         const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
                         e0 = e10 > 0.0f && e10 < E;
                         e1v = e11 > 0.0f && e11 < E;
+                        const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+                        defer = may_defer && ((marg_xy && (e0 || e1v))
+                                || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
+                                || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu))));
                     }
                 }
-                v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
-                v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
+                if (defer) {
+                    const int qs = atomicAdd(dq.s_count, 1);
+                    if (qs < dq.cap) {
+                        dq.seg[qs] = box_tag | ((unsigned long long)a << 24)
+                                     | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)ti;
+                    } else {
+                        red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
+                        defer = false;
+                    }
+                }
+                if (!defer && k2xy_in && H > 0.0f) {
+                    if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
+                        sqH = sqrtf(H);
+                        const float kp = kap * Pz;
+                        const float sq = E * sqH;
+                        const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                        if (Q != 0.0f) {
+                            z0 = Q / D;
+                            z1 = (E * E * a2 - kap * kap) / Q;
+                            const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
+                            e0 = e10 > 0.0f && e10 < E;
+                            e1v = e11 > 0.0f && e11 < E;
+                        }
+                    }
+                    v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
+                    v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
+                }
             }
-        }
-        // ---- append valid roots to the ring ----
-        const unsigned b0 = __ballot_sync(0xffffffffu, v0);
-        const unsigned b1 = __ballot_sync(0xffffffffu, v1);
-        const int n0 = __popc(b0);
-        if (v0) {
-            const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
-            S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
-        }
-        if (v1) {
-            const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
-            S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = lane | (ti << 5);
-        }
-        tail += n0 + __popc(b1);
-        __syncwarp();
-        while (tail - head >= 32) process(32);
-    }
-    if (tail > head) process(tail - head);
-    if (MODE == M_RECORD) {
-        // samples with at least one accepted root only: a zero weight teaches nothing
-        __syncwarp();
-        if (unit % P.rec_stride == 0) {
-            const bool keep = live && S.recw[lane] > 0.0f;
-            const unsigned keep_mask = __ballot_sync(0xffffffffu, keep);
-            unsigned long long base = 0;
-            if (lane == 0 && keep_mask) base = atomicAdd(P.rec_count, (unsigned long long)__popc(keep_mask));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const unsigned slot = __popc(keep_mask & lt_mask);
-            if (keep && (long long)(base + slot) < P.rec_cap) {
-                ProposalRecord R;
-                R.a = a;
-                R.w = S.recw[lane];
-                R.y[0] = S.k1x[lane] / L;
-                R.y[1] = S.k1y[lane] / L;
-                R.y[2] = S.k30[lane] / L;
-                R.y[3] = S.k31[lane] / L;
-                R.y[4] = S.k32[lane] / L;
-                P.rec[base + slot] = R;
+            // append the valid roots to the ring
+            const unsigned b0 = __ballot_sync(0xffffffffu, v0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, v1);
+            const int n0 = __popc(b0);
+            if (v0) {
+                const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
+                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = seq | (ti << 24);
             }
+            if (v1) {
+                const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
+                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = seq | (ti << 24);
+            }
+            tail += n0 + __popc(b1);
+            ++ti;
+            __syncwarp();
+            continue;
         }
-        __syncwarp();
-        return;
+        if (ti == nt) {  // batch done; record mode first finishes its roots, then writes records
+            cons = bstart + bcnt;
+            ti = -1;
+            if (MODE == M_RECORD) {
+                flush = true;
+                rec_due = true;
+            }
+            continue;
+        }
+        if (MODE == M_RECORD && rec_due) {
+            // one record per sample with at least one accepted root (a zero
+            // weight teaches nothing); the sample's coordinates are drawn again
+            rec_due = false;
+            if (unit % P.rec_stride == 0) {
+                const int sb = (bstart + lane) & (SBUF - 1);
+                const bool keep = lane < bcnt && S.wfac[sb] > 0.0f;
+                const unsigned keep_mask = __ballot_sync(0xffffffffu, keep);
+                unsigned long long base = 0;
+                if (lane == 0 && keep_mask) base = atomicAdd(P.rec_count, (unsigned long long)__popc(keep_mask));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const unsigned pos = __popc(keep_mask & lt_mask);
+                if (keep && (long long)(base + pos) < P.rec_cap) {
+                    const int smp = bmeta & 0xFFFFFF;
+                    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+                    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0,
+                                                   P.key1);
+                    ProposalRecord R;
+                    R.a = a;
+                    R.w = S.wfac[sb];
+                    R.y[0] = (-L + twoL * unif23(r0.w)) / L;
+                    R.y[1] = (-L + twoL * unif23(r1.x)) / L;
+                    R.y[2] = (-L + twoL * unif23(r1.y)) / L;
+                    R.y[3] = (-L + twoL * unif23(r1.z)) / L;
+                    R.y[4] = (-L + twoL * unif23(r1.w)) / L;
+                    P.rec[base + pos] = R;
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        if (nlive - cons >= 32 || (c >= c1 && nlive > cons)) {  // start a batch
+            bstart = cons;
+            bcnt = min(nlive - cons, 32);
+            const int sb = (bstart + lane) & (SBUF - 1);
+            if (lane < bcnt) {
+                bEp = S.Ep[sb]; bPz = S.Pz[sb]; ba2m = S.a2m[sb]; bb2m = S.b2m[sb]; bkk3 = S.kk3[sb];
+                bmeta = S.meta[sb];
+            } else {
+                bmeta = 0;
+            }
+            ti = 0;
+            continue;
+        }
+        if (c < c1) {
+            // ---- sample geometry (one sample per lane) ----
+            const int smp = c * 32 + lane;
+            const bool live = smp < P.nsamples;
+            const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+            const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+            const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
+            const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
+            const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
+            float k1x, k1y, k30, k31, k32, wfac = 1.0f;
+            bool margk = false;
+            if (MODE == M_LEARNED) {
+                // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
+                const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
+                                               P.key0, P.key1);
+                // Component i: y = mu + s logit(v), v = Fa + u D, so F(y) = v and
+                // 1 - F(y) = cFb + (1 - u) D: the density v (1 - v)/(s D) needs no
+                // exponential.  A uniform draw y = 2u - 1 takes F(y) from exp_split.
+                const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
+                float y[5];
+                const bool uni = unif23(r2.x) < pa;
+                float G = 1.0f;
+    #pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
+                    const float sg = i < 2 ? ps1 : ps3;
+                    const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
+                    float F, cF;
+                    if (uni) {
+                        y[i] = 2.0f * uv[i] - 1.0f;
+                        const float zz = (y[i] - mu) / sg;
+                        const float e = exp_split(-fabsf(zz));
+                        const float inv = 1.0f / (1.0f + e);
+                        F = zz >= 0.0f ? inv : e * inv;
+                        cF = zz >= 0.0f ? e * inv : inv;
+                    } else {
+                        F = tc.x + uv[i] * tc.z;
+                        cF = tc.y + (1.0f - uv[i]) * tc.z;
+                        y[i] = fminf(fmaxf(mu + sg * __logf(F / cF), -1.0f), 0.99999994f);
+                    }
+                    G *= F * cF / (sg * tc.z);
+                }
+                wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
+                k1x = L * y[0];
+                k1y = L * y[1];
+                k30 = L * y[2];
+                k31 = L * y[3];
+                k32 = L * y[4];
+                margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
+                        near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
+                        near_edge(k32, L, inv_dp2, EDGE_XY);
+            } else {
+                k1x = -L + twoL * unif23(r0.w);
+                k1y = -L + twoL * unif23(r1.x);
+                k30 = -L + twoL * unif23(r1.y);
+                k31 = -L + twoL * unif23(r1.z);
+                k32 = -L + twoL * unif23(r1.w);
+            }
+            const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+            const float bx = Px - k1x, by = Py - k1y;
+            const bool k2xy_in = in_box(bx, L) && in_box(by, L);
+            const bool marg_xy = near_edge(bx, L, inv_dp0, EDGE_XY) || near_edge(by, L, inv_dp1, EDGE_XY) || margk;
+            const bool keep = live && (k2xy_in || marg_xy);
+            const unsigned kb = __ballot_sync(0xffffffffu, keep);
+            const int cnt = __popc(kb);
+            // the new samples take the slots of sequence numbers nlive - SBUF ..:
+            // finish the pending roots that may still refer to those first.  The
+            // oldest pending root belongs to the batch of the head root, which
+            // starts at a multiple of 32 (only the last batch of a unit is short).
+            if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
+                flush = true;  // draw this chunk again after the flush
+                continue;
+            }
+            if (keep) {
+                const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
+                S.Ep[sb] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
+                S.Pz[sb] = Pz;
+                S.PP[sb] = (Px * Px + Py * Py) + Pz * Pz;
+                S.a2m[sb] = k1x * k1x + k1y * k1y;
+                S.b2m[sb] = bx * bx + by * by;
+                S.kk3[sb] = (k30 * k30 + k31 * k31) + k32 * k32;
+                S.k13[sb] = k1x * k30 + k1y * k31;
+                S.k3z[sb] = k32;
+                S.k1p[sb] = k1x * p0 + k1y * p1;
+                S.pz[sb] = p2;
+                if (MODE == M_LEARNED) {
+                    S.lin3[sb] = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                                 + binf(k32, L, inv_dp2, P.np[2]);
+                    S.b1xy[sb] = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                } else {
+                    S.lin3[sb] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                                 + bin_word(r1.w, P.np[2]);
+                    S.b1xy[sb] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                }
+                S.b2xy[sb] = binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]);
+                S.meta[sb] = smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25);
+                S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
+            }
+            nlive += cnt;
+            ++c;
+            __syncwarp();
+            continue;
+        }
+        if (tail > head) {
+            flush = true;
+            continue;
+        }
+        break;
     }
-    own = warp_sum_ll(own);
-    if (lane == 0 && own != 0) red_add(&P.A[a], own);
+    if (MODE != M_RECORD) {
+        own = warp_sum_ll(own);
+        if (lane == 0 && own != 0) red_add(&P.A[a], own);
+    }
     __syncwarp();
 }
 
-// FP32 collision, one warp per unit (an anchor and 32 of its samples).
+// FP32 collision, one warp per unit (an anchor and up to 32 F32_GROUP of its samples).
 // Single box (boxes == nullptr): warps stride over the units of `one`.
 // Batch of independent boxes: warps take chunks of `chunk` units from a
 // global counter over the concatenated unit space (prefix[b] = first unit of
@@ -446,7 +553,7 @@ const bool may_defer = P.tau > 0.0f;
 // Both walk through the one call site of collide_unit: a box gives the same
 // bits alone or inside a batch.
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_collide_f32(const __grid_constant__ CollideArgs<float> one,
+__global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(const __grid_constant__ CollideArgs<float> one,
                                                         const CollideArgs<float>* __restrict__ boxes,
                                                         const int64_t* __restrict__ prefix, int nboxes,
                                                         unsigned long long* counter, const int* step_dev, int chunk,
@@ -465,7 +572,7 @@ __global__ void __launch_bounds__(256, 4) k_collide_f32(const __grid_constant__ 
     dq.seg = qitems + gw * qcap;
     dq.cap = (int)qcap;
     const bool batch = boxes != nullptr;
-    const int64_t total = batch ? prefix[nboxes] : one.n_sel * ((one.nsamples + 31) >> 5);
+    const int64_t total = batch ? prefix[nboxes] : f32_units(one.n_sel, one.nsamples);
     const int step = batch ? *step_dev : one.step;
     int b = 0;
     int64_t u = batch ? 0 : gw, stop = 0;  // next unit; end of the current chunk (batch)
