@@ -58,7 +58,7 @@ typedef struct bz_handle_s* bz_handle;
 typedef struct bz_grid {
     int32_t nx[3];   /* spatial cells per axis (1 = homogeneous along that axis)          */
     double dx;       /* spatial cell size, fm                                              */
-    int32_t np[3];   /* momentum cells per axis; even n keeps cell centres off p = 0       */
+    int32_t np[3];   /* momentum cells per axis; not odd along all three (a cell at p = 0) */
     double L;        /* momentum box [-L, L)^3, GeV; also the integration box of (k1_perp, k3) */
     uint64_t seed;   /* Philox4x32-10 key (low word xor box id, high word)                  */
     uint32_t box;    /* box id, xored into the key's low word                               */
@@ -70,7 +70,8 @@ typedef struct bz_grid {
  * one f-sized work array).  Defaults: gluons only, alpha_s = 0.3, mass mode
  * BZ_MASS_THERMAL, all anchors sampled, no equilibrium override.
  * Grid and seed follow the statement of the problem in Sec. II / III.
- * Errors: BZ_EINVAL (sizes <= 0, L <= 0, dx <= 0), BZ_ENODEV, BZ_ENOMEM. */
+ * Errors: BZ_EINVAL (sizes <= 0, np > BZ max, all np odd, L <= 0, dx <= 0), BZ_ENODEV,
+ * BZ_ENOMEM. */
 int bz_init_grid(bz_handle* out, const bz_grid* g);
 
 /* Releases the handle and its scratch (synchronises the device first). */

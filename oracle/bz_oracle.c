@@ -53,6 +53,7 @@
 #define TWO_POW_40 1099511627776.0
 #define TWO_POW_M40 (1.0 / 1099511627776.0)
 #define MASS_SHIFT 30 /* fixed-point scale of the mass integrals: 2^30 */
+#define MASS_FX (1.0 / 1024.0) /* state units (2^-40 of N f) to 2^-30 of f: 2^(MASS_SHIFT - 40) */
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random   */
@@ -353,14 +354,14 @@ static double f_equilibrium(const bzo_config* c, int s, double E)
 /* Thermal masses, Eqs. (mg), (mq).  Each species integral uses its    */
 /* own dispersion E^a = sqrt(p^2 + m_a^2) with the previous masses      */
 /* (E = |p| when m2_prev is NULL, the first step, and always in mass    */
-/* mode 1, the massless dispersion).  The bin sums are                  */
-/* taken exactly in 2^-30 fixed point; out[x][0] = m_g^2, out[x][1+i] = */
+/* mode 1, the massless dispersion).  The bin sums (3x the Eq. (mg)    */
+/* integrand, 24x the Eq. (mq) one) are taken exactly in 2^-30 fixed    */
+/* point of f; out[x][0] = m_g^2, out[x][1+i] =                         */
 /* m_{q_i}^2.  Returns 0, or 1 if a fixed-point sum would overflow.     */
 /* ------------------------------------------------------------------ */
 int bzo_masses(const bzo_config* c, const int64_t* state, const double* m2_prev, double* out)
 {
-    const double dF = 3.0, CA = 3.0, CF = 4.0 / 3.0, dA = 8.0;
-    (void)dF;
+    const double CF = 4.0 / 3.0, dA = 8.0;  /* C_A = 3 and C_F enter the integrand coefficients */
     double g2 = 4.0 * PI * c->alpha_s;
     double dpx = 2.0 * c->L / c->np[0], dpy = 2.0 * c->L / c->np[1], dpz = 2.0 * c->L / c->np[2];
     double twopi = 2.0 * PI;
@@ -381,34 +382,39 @@ int bzo_masses(const bzo_config* c, const int64_t* state, const double* m2_prev,
             double py = -c->L + ((double)jy + 0.5) * dpy;
             double pz = -c->L + ((double)jz + 0.5) * dpz;
             double pp = (px * px + py * py) + pz * pz;
-            double fs[NSPEC];
+            /* N_s f_s = n_s 2^-40, so with r_a = 1/(2 E_a) the bin integrands are
+             *   Eq. (mg): N_g C_A f_g r_g + sum_i N_q C_F (f_qi + f_qbi) r_qi
+             *             = 2^-40 (3 n_g r_g + (4/3) sum_i q_i r_qi),
+             *   Eq. (mq): 2 f_g r_g + (f_qi + f_qbi) r_qi = 2^-40 (n_g r_g / 8 + q_i r_qi / 6),
+             * q_i = n_qi + n_qbi.  They are summed as 3x and 24x these (integer
+             * coefficients), rounded to 2^-30 of f. */
+            int64_t nsp[NSPEC];
             for (int s = 0; s < NSPEC; ++s) {
                 int sl = slot_of(c, s);
-                fs[s] = sl < 0 ? 0.0 : f_of_state(state[((int64_t)sl * nxc + x) * npc + j], s);
+                nsp[s] = sl < 0 ? 0 : state[((int64_t)sl * nxc + x) * npc + j];
             }
-            double Eg = sqrt(pp + m2p[0]);
-            /* Eq. (mg): N_g C_A f_g / (2E_g) + sum_i N_q C_F (f_qi + f_qbi) / (2E_qi) */
-            double tg = 16.0 * CA * fs[0] / (2.0 * Eg);
+            double ng = (double)nsp[0];
+            double rg = 0.5 / sqrt(pp + m2p[0]);
+            double q[3], rq[3];
             for (int i = 0; i < 3; ++i) {
-                double Eq = sqrt(pp + m2p[1 + i]);
-                tg = tg + 6.0 * CF * (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
+                q[i] = (double)(nsp[1 + i] + nsp[4 + i]);
+                rq[i] = 0.5 / sqrt(pp + m2p[1 + i]);
             }
-            int64_t qg = llrint(tg * (double)(1LL << MASS_SHIFT));
+            double g3 = 9.0 * ng * rg + 4.0 * ((q[0] * rq[0] + q[1] * rq[1]) + q[2] * rq[2]);
+            int64_t qg = llrint(g3 * MASS_FX);
             if (qg > limit || qg < -limit) ovf = 1;
             sum_g += qg;
-            /* Eq. (mq): 2 f_g / (2E_g) + (f_qi + f_qbi) / (2E_qi) */
             for (int i = 0; i < 3; ++i) {
-                double Eq = sqrt(pp + m2p[1 + i]);
-                double tq = 2.0 * fs[0] / (2.0 * Eg) + (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
-                int64_t qq = llrint(tq * (double)(1LL << MASS_SHIFT));
+                double q24 = 3.0 * ng * rg + 4.0 * q[i] * rq[i];
+                int64_t qq = llrint(q24 * MASS_FX);
                 if (qq > limit || qq < -limit) ovf = 1;
                 sum_q[i] += qq;
             }
         }
         double inv = 1.0 / (double)(1LL << MASS_SHIFT);
-        out[x * 4 + 0] = (2.0 * g2 / dA) * meas * ((double)sum_g * inv);
+        out[x * 4 + 0] = (2.0 * g2 / dA) * meas * ((double)sum_g * inv) / 3.0;
         for (int i = 0; i < 3; ++i)
-            out[x * 4 + 1 + i] = (2.0 * CF * g2) * meas * ((double)sum_q[i] * inv);
+            out[x * 4 + 1 + i] = (2.0 * CF * g2) * meas * ((double)sum_q[i] * inv) / 24.0;
     }
     return ovf;
 }

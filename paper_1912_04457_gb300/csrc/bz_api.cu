@@ -198,6 +198,7 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
         if (g->np[d] > MAX_NP) return fail(nullptr, BZ_EINVAL, "np[%d] = %d exceeds %d", d, g->np[d], MAX_NP);
     }
     if (!(g->L > 0) || !(g->dx > 0)) return fail(nullptr, BZ_EINVAL, "L and dx must be positive");
+    if (np_has_zero_cell(g->np)) return fail(nullptr, BZ_EINVAL, "np odd along all axes puts a cell at p = 0 (E = 0)");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
         return fail(nullptr, BZ_ENODEV, "no CUDA device");
@@ -516,6 +517,8 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     }
     a.L = (R)h->g.L;
     a.twoL = (R)twoL;
+    a.L64 = h->g.L;
+    for (int d = 0; d < 3; ++d) a.dp64[d] = twoL / h->g.np[d];
     a.key0 = (uint32_t)(h->g.seed & 0xffffffffu) ^ h->g.box;
     a.key1 = (uint32_t)(h->g.seed >> 32);
     a.nsamples = nsamples;
@@ -597,6 +600,12 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         ProfScope ps(h, BZ_K_COLLIDE, s);
         CK(h, launch_collide_f32(a, (int)blocks, s));
     }
+    if (sampler != BZ_SAMPLER_LEARNED) {  // FP64 root solve, FP32 integrand
+        ProfScope ps(h, BZ_K_FIXUP, s);
+        CK(h, launch_fixup_f32(a, (int)warps, s));
+        return BZ_OK;
+    }
+    // learned sampler: the whole term in FP64 (its inverse-CDF coordinates need FP64 logarithms)
     CollideArgs<double> b{};
     fill_collide(h, b, A, nsamples, step, dt, sampler);
     b.f_is_float = 1;
@@ -801,11 +810,9 @@ struct bz_batch_s {
     float* d_scale = nullptr;
     int* d_slot_cells = nullptr;
     CollideArgs<float>* d_a32 = nullptr;
-    CollideArgs<double>* d_a64 = nullptr;
     MassArgs* d_mass = nullptr;
     MomentArgs* d_mom = nullptr;
     std::vector<CollideArgs<float>> a32;
-    std::vector<CollideArgs<double>> a64;
     std::vector<MassArgs> mass;
     std::vector<MomentArgs> mom;
     int* d_qcount = nullptr;
@@ -848,7 +855,7 @@ static void batch_free(bz_batch b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* ptrs[] = {b->d_f, b->d_m2_cur, b->d_m2_prev, b->d_acc, b->d_flags, b->d_have_prev, b->d_step, b->d_kidx,
                     b->d_counter, b->d_cell_prefix, b->d_unit_prefix, b->d_mchunk_prefix, b->d_cchunk_prefix,
-                    b->d_slot_prefix, b->d_scale, b->d_slot_cells, b->d_a32, b->d_a64, b->d_mass, b->d_mom,
+                    b->d_slot_prefix, b->d_scale, b->d_slot_cells, b->d_a32, b->d_mass, b->d_mom,
                     b->d_qcount, b->d_qitems};
     for (void* p : ptrs) cudaFree(p);
     for (auto& h : b->hb) {
@@ -889,6 +896,10 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
                 delete b;
                 return bfail(nullptr, BZ_EINVAL, "box %d: np out of range", i);
             }
+        if (np_has_zero_cell(d.np)) {
+            delete b;
+            return bfail(nullptr, BZ_EINVAL, "box %d: np odd along all axes puts a cell at p = 0", i);
+        }
         if (!(d.L > 0) || !(d.alpha_s > 0) || (d.species_mask & 0x7Fu) == 0 || (d.species_mask & ~0x7Fu) ||
             d.nsamples <= 0 || d.nsamples > MAX_SAMPLES ||
             (d.mass_mode != BZ_MASS_THERMAL && d.mass_mode != BZ_MASS_MASSLESS)) {
@@ -935,7 +946,7 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
               dalloc(&b->d_cell_prefix, nboxes + 1) && dalloc(&b->d_unit_prefix, nboxes + 1) &&
               dalloc(&b->d_mchunk_prefix, nboxes + 1) && dalloc(&b->d_cchunk_prefix, nboxes + 1) &&
               dalloc(&b->d_slot_prefix, nboxes + 1) && dalloc(&b->d_scale, 2 * nboxes) &&
-              dalloc(&b->d_slot_cells, nboxes) && dalloc(&b->d_a32, nboxes) && dalloc(&b->d_a64, nboxes) &&
+              dalloc(&b->d_slot_cells, nboxes) && dalloc(&b->d_a32, nboxes) &&
               dalloc(&b->d_mass, nboxes) && dalloc(&b->d_mom, nboxes) && dalloc(&b->d_qcount, b->qwarps) &&
               dalloc(&b->d_qitems, b->qwarps * b->qcap);
     if (!ok) {
@@ -1030,23 +1041,18 @@ static int batch_fill_args(bz_batch b, long long* state, double dt, cudaStream_t
 {
     const int n = b->nboxes;
     b->a32.assign(n, CollideArgs<float>{});
-    b->a64.assign(n, CollideArgs<double>{});
     b->mass.assign(n, MassArgs{});
     b->mom.assign(n, MomentArgs{});
     for (int i = 0; i < n; ++i) {
         bz_handle_s* h = &b->hb[i];
         long long* st = state + b->cell_prefix[i];
         fill_collide(h, b->a32[i], st, b->desc[i].nsamples, 0, dt, BZ_SAMPLER_SYMMETRIC);
-        fill_collide(h, b->a64[i], st, b->desc[i].nsamples, 0, dt, BZ_SAMPLER_SYMMETRIC);
-        b->a64[i].f_is_float = 1;
-        b->a64[i].ubits = 23;
         b->a32[i].tau = (float)DEFER_TAU;
         fill_masses(h, b->mass[i], st, b->d_acc + 4 * i, b->d_m2_cur + 4 * i,
                     h->mass_mode == BZ_MASS_MASSLESS ? nullptr : b->d_m2_prev + 4 * i);
         fill_moments(h, b->mom[i], st, nullptr);
     }
     CKB(b, cudaMemcpyAsync(b->d_a32, b->a32.data(), sizeof(CollideArgs<float>) * n, cudaMemcpyHostToDevice, s));
-    CKB(b, cudaMemcpyAsync(b->d_a64, b->a64.data(), sizeof(CollideArgs<double>) * n, cudaMemcpyHostToDevice, s));
     CKB(b, cudaMemcpyAsync(b->d_mass, b->mass.data(), sizeof(MassArgs) * n, cudaMemcpyHostToDevice, s));
     CKB(b, cudaMemcpyAsync(b->d_mom, b->mom.data(), sizeof(MomentArgs) * n, cudaMemcpyHostToDevice, s));
     return BZ_OK;
@@ -1058,7 +1064,7 @@ static int batch_collide(bz_batch b, int chunk, int bps, cudaStream_t s)
     CKB(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), s));
     CKB(b, launch_collide_f32_batch(b->d_a32, b->d_unit_prefix, b->nboxes, b->d_counter, b->d_step, chunk, grid,
                                     b->d_qcount, b->d_qitems, b->qcap, s));
-    CKB(b, launch_fixup_batch(b->d_a64, b->d_qcount, b->d_qitems, b->qcap, b->d_step, grid * F32_WARPS, s));
+    CKB(b, launch_fixup_f32_batch(b->d_a32, b->d_qcount, b->d_qitems, b->qcap, b->d_step, grid * F32_WARPS, s));
     return BZ_OK;
 }
 

@@ -14,6 +14,11 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double TWO_POW_40 = 1099511627776.0;
 constexpr double TWO_POW_M40 = 1.0 / 1099511627776.0;
 constexpr int MASS_SHIFT = 30;
+// A grid odd along all three axes has a cell centred at p = 0, where the
+// massless dispersion E = |p| (first mass evaluation, mass mode MASSLESS)
+// is zero and 1/(2E) in Eqs. (mg), (mq) diverges; such grids are rejected.
+inline bool np_has_zero_cell(const int* np) { return (np[0] & 1) && (np[1] & 1) && (np[2] & 1); }
+constexpr double MASS_FX = 1.0 / 1024.0;  // state units (2^-40 of N f) to 2^-30 of f: 2^(MASS_SHIFT - 40)
 
 enum { M_QQP = 0, M_QQ, M_QQB, M_QQB2, M_QQBGG, M_QG, M_GG };
 
@@ -56,6 +61,7 @@ struct CollideArgs {
     int64_t nxc, npc;
     int np[3];
     R L, twoL, dp[3];
+    double L64, dp64[3];    // L and 2L/n in FP64 (the FP32 path's fixup works in FP64 geometry)
     uint32_t key0, key1;
     int nsamples, step;
     int64_t n_sel, a_stride, a_offset;
@@ -126,12 +132,15 @@ struct MomentArgs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
+// FP32 path, uniform sampler: re-evaluation of the queued terms with an FP64
+// root solve (one warp per queue segment)
+cudaError_t launch_fixup_f32(const CollideArgs<float>& a, int nseg, cudaStream_t s);
+cudaError_t launch_fixup_f32_batch(const CollideArgs<float>* boxes, const int* qcount, const unsigned long long* qitems,
+                                   int64_t qcap, const int* step_dev, int nseg, cudaStream_t s);
 cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
 cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int64_t* prefix, int nboxes,
                                      unsigned long long* counter, const int* step_dev, int chunk, int grid,
                                      int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s);
-cudaError_t launch_fixup_batch(const CollideArgs<double>* boxes, const int* qcount, const unsigned long long* qitems,
-                               int64_t qcap, const int* step_dev, int nseg, cudaStream_t s);
 // batched transport kernels over independent homogeneous boxes
 cudaError_t launch_masses_batch(const MassArgs* boxes, const int64_t* chunk_prefix, int nboxes, int64_t nchunks,
                                 const int* have_prev, long long* acc_all, cudaStream_t s);

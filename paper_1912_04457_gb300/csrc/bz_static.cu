@@ -140,6 +140,8 @@ extern "C" int bz_collision_term_static(const bz_grid* g, uint32_t species_mask,
         if (g->np[d] > MAX_NP) return err(errbuf, errbuf_len, BZ_EINVAL, "np[%d] = %d exceeds %d", d, g->np[d], MAX_NP);
     }
     if (!(g->L > 0) || !(g->dx > 0)) return err(errbuf, errbuf_len, BZ_EINVAL, "L and dx must be positive");
+    if (np_has_zero_cell(g->np))
+        return err(errbuf, errbuf_len, BZ_EINVAL, "np odd along all axes puts a cell at p = 0 (E = 0)");
     if ((species_mask & 0x7Fu) == 0 || (species_mask & ~0x7Fu))
         return err(errbuf, errbuf_len, BZ_EINVAL, "bad species mask 0x%x", species_mask);
     if (!(alpha_s > 0)) return err(errbuf, errbuf_len, BZ_EINVAL, "alpha_s must be positive");

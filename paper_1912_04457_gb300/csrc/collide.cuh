@@ -397,27 +397,5 @@ __global__ void __launch_bounds__(256) k_fixup(const __grid_constant__ CollideAr
     }
 }
 
-// Batch form: the item carries its box (bits 48..63); the step is read from
-// device memory.
-template <typename R>
-__global__ void __launch_bounds__(256) k_fixup_batch(const CollideArgs<R>* __restrict__ boxes, const int* qcount,
-                                                     const unsigned long long* qitems, int64_t qcap, const int* step_dev)
-{
-    const int64_t seg = blockIdx.x;
-    const int n = qcount[seg];
-    const int step = *step_dev;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long it = qitems[seg * qcap + i];
-        const int b = (int)(it >> 48);
-        const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
-        const int smp = (int)((it >> 4) & 0xFFFFFu);
-        const int ti = (int)(it & 0xFu);
-        const CollideArgs<R>& P = boxes[b];
-        Geom<R> G;
-        make_geom(P, a, smp, G, step);
-        const long long own = eval_term<R, false>(P, G, a, smp, ti, nullptr);
-        if (own != 0) red_add(&P.A[a], own);
-    }
-}
 
 }  // namespace bz

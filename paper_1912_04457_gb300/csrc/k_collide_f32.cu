@@ -632,4 +632,174 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Re-evaluation of a queued (anchor, sample, term) of the uniform sampler.
+// What made the term ill-conditioned, or put a solved coordinate on a bin
+// edge, is redone in FP64: the sample point from the same Philox words, E,
+// D, kappa, H, the roots and their validity, box and bin decisions (the
+// sampled legs' bins are the exact integer ones).  From the accepted roots
+// on (s, t, u in FP64; |M|^2, W and c~ in FP32) it is an ordinary term of
+// the FP32 path.  Returns the anchor's +q.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bin64(double k, double L, double dp, int n)
+{
+    int j = (int)floor((k + L) / dp);
+    j = j < 0 ? 0 : j;
+    return j >= n ? n - 1 : j;
+}
+
+__device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step)
+{
+    const int64_t nxc = P.nxc, npc = P.npc;
+    const int sl = (int)(a / (nxc * npc));
+    const int64_t x = (a / npc) % nxc;
+    const int j = (int)(a % npc);
+    const int d = P.slot_species[sl];
+    const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
+    const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
+    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    auto u23 = [](uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); };
+    const double L = P.L64, twoL = 2.0 * P.L64;
+    const double p0 = (-L + ((double)jx + 0.5) * P.dp64[0]) + P.dp64[0] * (u23(r0.x) - 0.5);
+    const double p1 = (-L + ((double)jy + 0.5) * P.dp64[1]) + P.dp64[1] * (u23(r0.y) - 0.5);
+    const double p2 = (-L + ((double)jz + 0.5) * P.dp64[2]) + P.dp64[2] * (u23(r0.z) - 0.5);
+    const double k1x = -L + twoL * u23(r0.w), k1y = -L + twoL * u23(r1.x);
+    const double k30 = -L + twoL * u23(r1.y), k31 = -L + twoL * u23(r1.z), k32 = -L + twoL * u23(r1.w);
+    const double Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+    const double bx = Px - k1x, by = Py - k1y;
+    if (!(bx >= -L && bx < L && by >= -L && by < L)) return 0;
+    const TermDev& T = P.terms[d][ti];
+    double mv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mv[i] = P.mass_mode == 1 ? 0.0 : P.m2[x * 4 + i];
+    const double mg2 = P.m2[x * 4];
+    const double ma2 = mv[T.mslot[0]], mb2 = mv[T.mslot[1]], mc2 = mv[T.mslot[2]], md2 = mv[T.mslot[3]];
+    const double Ep = sqrt(((p0 * p0 + p1 * p1) + p2 * p2) + md2);
+    const double E3 = sqrt(((k30 * k30 + k31 * k31) + k32 * k32) + mc2);
+    const double E = Ep + E3;
+    const double a2 = (k1x * k1x + k1y * k1y) + ma2;
+    const double b2 = (bx * bx + by * by) + mb2;
+    const double D = E * E - Pz * Pz;
+    const double kap = (E * E + a2 - b2 - Pz * Pz) * 0.5;
+    const double H = kap * kap - a2 * D;
+    if (!(D > 0.0) || !(H > 0.0)) return 0;
+    const double sqH = sqrt(H);
+    const double kp = kap * Pz, sq = E * sqH;
+    const double Q = kp >= 0.0 ? kp + sq : kp - sq;
+    if (Q == 0.0) return 0;
+    const double zr[2] = {Q / D, (E * E * a2 - kap * kap) / Q};
+    const double s = E * E - ((Px * Px + Py * Py) + Pz * Pz);
+    const double k13 = k1x * k30 + k1y * k31, k1p = k1x * p0 + k1y * p1;
+    const unsigned slot_stride = (unsigned)(nxc * npc), xoff = (unsigned)(x * npc);
+    const int b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+    const int b2xy = bin64(bx, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(by, L, P.dp64[1], P.np[1]);
+    const int lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+    const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
+    long long own = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const double z = zr[r], dz = Pz - z;
+        const double e2E = kap + Pz * z;  // E2 E at a root: valid iff 0 < E2 < E
+        if (!(e2E > 0.0 && e2E < E * E)) continue;
+        if (!(z >= -L && z < L && dz >= -L && dz < L)) continue;
+        const double E1 = sqrt(a2 + z * z);
+        const double t = (ma2 + mc2) - 2.0 * (E1 * E3 - (k13 + z * k32));
+        const double uu = (ma2 + md2) - 2.0 * (E1 * Ep - (k1p + z * p2));
+        if (s <= 0.0 || t - mg2 >= 0.0 || uu - mg2 >= 0.0) {
+            red_add(&P.flags[0], 1);
+            continue;
+        }
+        const float M2 = msq<float>(T.cls, P, (float)s, (float)t, (float)uu, (float)mg2);
+        const int lin1 = b1xy * P.np[2] + bin64(z, L, P.dp64[2], P.np[2]);
+        const int lin2 = b2xy * P.np[2] + bin64(dz, L, P.dp64[2], P.np[2]);
+        const unsigned i1 = (unsigned)T.slot[0] * slot_stride + xoff + lin1;
+        const unsigned i2 = (unsigned)T.slot[1] * slot_stride + xoff + lin2;
+        const unsigned i3 = (unsigned)T.slot[2] * slot_stride + xoff + lin3;
+        float f1, f2, f3, fpp;
+        if (P.analytic) {
+            f1 = f_equilibrium(P, P.slot_species[T.slot[0]], (float)E1);
+            f2 = f_equilibrium(P, P.slot_species[T.slot[1]], (float)(E - E1));
+            f3 = f_equilibrium(P, P.slot_species[T.slot[2]], (float)E3);
+            fpp = f_equilibrium(P, d, (float)Ep);
+        } else {
+            const float* F = static_cast<const float*>(P.f);
+            f1 = __ldg(F + i1);
+            f2 = __ldg(F + i2);
+            f3 = __ldg(F + i3);
+            fpp = fp;
+        }
+        const float F1 = T.quark[0] ? 1.0f - f1 : 1.0f + f1;
+        const float F2 = T.quark[1] ? 1.0f - f2 : 1.0f + f2;
+        const float F3 = T.quark[2] ? 1.0f - f3 : 1.0f + f3;
+        const float Fp = T.quark[3] ? 1.0f - fpp : 1.0f + fpp;
+        const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
+        // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
+        const float den = (float)((double)P.twopi5 * 16.0 * sqH * E3 * Ep);
+        const float ct = (float)T.sym * W * M2 / den;
+        const float wq = ct * P.Kown;
+        if (!(fabsf(wq) < 4611686018427387904.0f)) {
+            red_add(&P.flags[1], 1);
+            continue;
+        }
+        const long long q = rint_ll(wq);
+        if (q == 0) continue;
+        own += q;
+        if (P.sampler != 1) {
+            red_add(&P.A[i3], q);
+            red_add(&P.A[i1], -q);
+            red_add(&P.A[i2], -q);
+        }
+    }
+    return own;
+}
+
+// One warp per queue segment (segments hold about a hundred items).
+__global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ CollideArgs<float> P, const int* qcount,
+                                                   const unsigned long long* qitems, int64_t qcap, int nseg)
+{
+    const int64_t seg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (seg >= nseg) return;
+    const int n = qcount[seg];
+    for (int i = threadIdx.x & 31; i < n; i += 32) {
+        const unsigned long long it = qitems[seg * qcap + i];
+        const int64_t a = (int64_t)(it >> 24);
+        const long long own = fixup_term(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), P.step);
+        if (own != 0) red_add(&P.A[a], own);
+    }
+}
+
+// Batch form: the item carries its box (bits 48..63); the step is read from
+// device memory.
+__global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float>* __restrict__ boxes,
+                                                         const int* qcount, const unsigned long long* qitems,
+                                                         int64_t qcap, const int* step_dev, int nseg)
+{
+    const int64_t seg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (seg >= nseg) return;
+    const int n = qcount[seg];
+    const int step = *step_dev;
+    for (int i = threadIdx.x & 31; i < n; i += 32) {
+        const unsigned long long it = qitems[seg * qcap + i];
+        const CollideArgs<float>& P = boxes[(int)(it >> 48)];
+        const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
+        const long long own = fixup_term(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step);
+        if (own != 0) red_add(&P.A[a], own);
+    }
+}
+
+cudaError_t launch_fixup_f32(const CollideArgs<float>& a, int nseg, cudaStream_t s)
+{
+    k_fixup_f32<<<(nseg + 7) / 8, 256, 0, s>>>(a, a.qcount, a.qitems, a.qcap, nseg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixup_f32_batch(const CollideArgs<float>* boxes, const int* qcount, const unsigned long long* qitems,
+                                   int64_t qcap, const int* step_dev, int nseg, cudaStream_t s)
+{
+    k_fixup_f32_batch<<<(nseg + 7) / 8, 256, 0, s>>>(boxes, qcount, qitems, qcap, step_dev, nseg);
+    return cudaGetLastError();
+}
+
+
 }  // namespace bz

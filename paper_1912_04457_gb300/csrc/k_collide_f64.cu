@@ -19,11 +19,5 @@ cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixup_batch(const CollideArgs<double>* boxes, const int* qcount, const unsigned long long* qitems,
-                               int64_t qcap, const int* step_dev, int nseg, cudaStream_t s)
-{
-    k_fixup_batch<double><<<nseg, 256, 0, s>>>(boxes, qcount, qitems, qcap, step_dev);
-    return cudaGetLastError();
-}
 
 }  // namespace bz

@@ -33,24 +33,50 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
     return v;
 }
 
+// Conversions between FP32 and int64 without the FP64 pipe (the hardware
+// int64 conversions issue there, at 1/64 of the FP32 rate on this part).
+// f2ll_rn: round to nearest even; inside int32 range the 32-bit conversion
+// gives the same integer.
+__device__ __forceinline__ long long f2ll_rn(float v)
+{
+    return fabsf(v) < 2147483648.0f ? (long long)__float2int_rn(v) : __float2ll_rn(v);
+}
+
+// ll2float_rn: int64 to the nearest float (ties to even) with integer
+// instructions: keep the leading 24 bits, round on the rest, scale by 2^sh.
+__device__ __forceinline__ float ll2float_rn(long long v)
+{
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    float f;
+    if (a < (1ull << 24)) {
+        f = (float)(unsigned)a;
+    } else {
+        const int sh = 40 - __clzll((long long)a);
+        unsigned long long m = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
+        f = (float)(unsigned)m * __int_as_float((127 + sh) << 23);
+    }
+    return v < 0 ? -f : f;
+}
+
 // ---------------------------------------------------------------------------
-// Thermal masses, Eqs. (mg), (mq).  Per bin, in FP64 (same order as the
-// definition):  N_g C_A f_g/(2E_g) + sum_i N_q C_F (f_qi + f_qbi)/(2E_qi) and
-// 2 f_g/(2E_g) + (f_qi + f_qbi)/(2E_qi), each rounded to 2^-30 fixed point
-// and summed exactly.  Grid: one block per (x cell, chunk of 2048 bins).
+// Thermal masses, Eqs. (mg), (mq).  Per bin, in FP64 with r_a = 1/(2E_a):
+// 3x the Eq. (mg) integrand N_g C_A f_g r_g + sum_i N_q C_F (f_qi + f_qbi) r_qi
+// and 24x the Eq. (mq) integrand 2 f_g r_g + (f_qi + f_qbi) r_qi, written in
+// the state n = N_s f 2^40 (integer coefficients), each rounded to 2^-30 of
+// f and summed exactly.  Grid: one block per (x cell, chunk of 2048 bins).
 // ---------------------------------------------------------------------------
 constexpr int MASS_CHUNK = 2048;
 
 // Fixed-point partial sums of one (x cell, chunk of MASS_CHUNK bins) block.
 __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64_t c0, bool use_prev)
 {
-    const double CA = 3.0, CF = 4.0 / 3.0;
     double m2p[4] = {0.0, 0.0, 0.0, 0.0};
     if (use_prev && P.m2_prev)
         for (int i = 0; i < 4; ++i) m2p[i] = P.m2_prev[x * 4 + i];
     long long sg = 0, sq[3] = {0, 0, 0};
     bool ovf = false;
-    const double scale = (double)(1LL << MASS_SHIFT);
     for (int64_t j = c0 + threadIdx.x; j < c0 + MASS_CHUNK && j < P.npc; j += blockDim.x) {
         const int jx = (int)(j / ((int64_t)P.np[1] * P.np[2]));
         const int jy = (int)((j / P.np[2]) % P.np[1]);
@@ -59,28 +85,31 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
         const double py = -P.L + ((double)jy + 0.5) * P.dp[1];
         const double pz = -P.L + ((double)jz + 0.5) * P.dp[2];
         const double pp = (px * px + py * py) + pz * pz;
-        double fs[NSPEC];
+        // N_s f_s = n_s 2^-40 and r_a = 1/(2 E_a): 3x the Eq. (mg) bin integrand
+        // is 2^-40 (9 n_g r_g + 4 sum_i q_i r_qi), 24x the Eq. (mq) one is
+        // 2^-40 (3 n_g r_g + 4 q_i r_qi), q_i = n_qi + n_qbi
+        long long nsp[NSPEC];
 #pragma unroll
         for (int s = 0; s < NSPEC; ++s) {
             const int sl = P.slot_of[s];
-            const double deg = s == 0 ? 16.0 : 6.0;
-            fs[s] = sl < 0 ? 0.0 : (double)P.state[((int64_t)sl * P.nxc + x) * P.npc + j] * TWO_POW_M40 / deg;
+            nsp[s] = sl < 0 ? 0 : P.state[((int64_t)sl * P.nxc + x) * P.npc + j];
         }
-        const double Eg = sqrt(pp + m2p[0]);
-        double tg = 16.0 * CA * fs[0] / (2.0 * Eg);
+        const double ng = (double)nsp[0];
+        const double rg = 0.5 / sqrt(pp + m2p[0]);
+        double q[3], rq[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double Eq = sqrt(pp + m2p[1 + i]);
-            tg = tg + 6.0 * CF * (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
+            q[i] = (double)(nsp[1 + i] + nsp[4 + i]);
+            rq[i] = 0.5 / sqrt(pp + m2p[1 + i]);
         }
-        const long long qg = __double2ll_rn(tg * scale);
+        const double g3 = 9.0 * ng * rg + 4.0 * ((q[0] * rq[0] + q[1] * rq[1]) + q[2] * rq[2]);
+        const long long qg = __double2ll_rn(g3 * MASS_FX);
         ovf |= qg > P.limit || qg < -P.limit;
         sg += qg;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double Eq = sqrt(pp + m2p[1 + i]);
-            const double tq = 2.0 * fs[0] / (2.0 * Eg) + (fs[1 + i] + fs[4 + i]) / (2.0 * Eq);
-            const long long qq = __double2ll_rn(tq * scale);
+            const double q24 = 3.0 * ng * rg + 4.0 * q[i] * rq[i];
+            const long long qq = __double2ll_rn(q24 * MASS_FX);
             ovf |= qq > P.limit || qq < -P.limit;
             sq[i] += qq;
         }
@@ -133,8 +162,8 @@ __global__ void k_masses_finish_batch(const MassArgs* __restrict__ boxes, int nb
     if (b >= nboxes) return;
     const MassArgs& P = boxes[b];
     const double inv = 1.0 / (double)(1LL << MASS_SHIFT);
-    P.m2_out[0] = P.pref_g * P.meas * ((double)P.acc[0] * inv);
-    for (int i = 0; i < 3; ++i) P.m2_out[1 + i] = P.pref_q * P.meas * ((double)P.acc[1 + i] * inv);
+    P.m2_out[0] = P.pref_g * P.meas * ((double)P.acc[0] * inv) / 3.0;
+    for (int i = 0; i < 3; ++i) P.m2_out[1 + i] = P.pref_q * P.meas * ((double)P.acc[1 + i] * inv) / 24.0;
 }
 
 __global__ void k_masses_finish(const __grid_constant__ MassArgs P)
@@ -142,9 +171,9 @@ __global__ void k_masses_finish(const __grid_constant__ MassArgs P)
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= P.nxc) return;
     const double inv = 1.0 / (double)(1LL << MASS_SHIFT);
-    P.m2_out[x * 4 + 0] = P.pref_g * P.meas * ((double)P.acc[x * 4 + 0] * inv);
+    P.m2_out[x * 4 + 0] = P.pref_g * P.meas * ((double)P.acc[x * 4 + 0] * inv) / 3.0;
     for (int i = 0; i < 3; ++i)
-        P.m2_out[x * 4 + 1 + i] = P.pref_q * P.meas * ((double)P.acc[x * 4 + 1 + i] * inv);
+        P.m2_out[x * 4 + 1 + i] = P.pref_q * P.meas * ((double)P.acc[x * 4 + 1 + i] * inv) / 24.0;
 }
 
 cudaError_t launch_masses(const MassArgs& a, cudaStream_t s)
@@ -160,40 +189,83 @@ cudaError_t launch_masses(const MassArgs& a, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // Drift, Eq. (left handside) in flux form: first-order upwind, periodic in
 // x.  Courant number c_d = (p_d (1/sqrt(p^2 + m^2(x)))) dt/dx in IEEE FP32,
-// held as C = rint(c 2^30); face flux = floor((n C + 2^29) / 2^30) exactly
-// (128-bit product), taken at the upwind cell and shared by both cells.
-// One thread per cell, p fastest, so every load and store is coalesced.
+// held as C = rint(c 2^30); face flux = floor((n C + 2^29) / 2^30) exactly,
+// taken at the upwind cell with the upwind cell's mass, so both cells of a
+// face apply the same integer.
+// Grid: block (row, tile), row = (slot, x cell), tile = DRIFT_TILE p cells;
+// rows vary fastest, so the upwind neighbour rows (x +- 1 along each axis)
+// of a tile are read while they are still in L2.  Per-row masses and
+// neighbour offsets are set up once per block; per-cell index arithmetic is
+// 32-bit.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ long long courant_fx(const DriftArgs& P, int64_t x, int ms, float pdf, float ppf)
+constexpr int DRIFT_THREADS = 256;
+constexpr int DRIFT_PER_THREAD = 4;
+constexpr int DRIFT_TILE = DRIFT_THREADS * DRIFT_PER_THREAD;
+
+__device__ __forceinline__ long long courant_fx(float m, float pdf, float ppf, float dtdxf)
 {
-    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + ms];
     const float inv = 1.0f / sqrtf(ppf + m);
-    const float cf = (pdf * inv) * P.dtdxf;
-    return __float2ll_rn(cf * 1073741824.0f);
+    const float cf = (pdf * inv) * dtdxf;
+    return f2ll_rn(cf * 1073741824.0f);
 }
 
+// floor((n C + 2^29) / 2^30) as an int64 (two's complement, like the exact
+// 128-bit product truncated to 64 bits).  For |C| < 2^31 the product splits
+// exactly: n = nh 2^32 + nl with 0 <= nl < 2^32, so the result is
+// 4 nh C + floor((nl C + 2^29) / 2^30) with both products inside int64.
 __device__ __forceinline__ long long flux_fx(long long n, long long C)
 {
+    if (C > -2147483648LL && C < 2147483648LL) {
+        const long long nh = n >> 32;
+        const long long nl = (long long)((unsigned long long)n & 0xffffffffull);
+        const long long lo = (nl * C + (1LL << 29)) >> 30;
+        return (long long)((unsigned long long)(nh * C) * 4ull + (unsigned long long)lo);
+    }
     const __int128 prod = (__int128)n * (__int128)C + ((__int128)1 << 29);
     return (long long)(prod >> 30);
 }
 
-__global__ void __launch_bounds__(256) k_drift(const __grid_constant__ DriftArgs P)
+__global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__ DriftArgs P)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < P.ncell; cell += stride) {
-        const int sl = (int)(cell / (P.nxc * P.npc));
-        const int64_t x = (cell / P.npc) % P.nxc;
-        const int64_t j = cell % P.npc;
-        const int ms = P.slot_mslot[sl];
-        const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]),
-                           (int)(j % P.np[2])};
-        const float pf[3] = {P.pf[0][jv[0]], P.pf[1][jv[1]], P.pf[2][jv[2]]};
+    __shared__ float s_m[7];          // mass of this row's x cell, then (lower, upper) neighbour per axis
+    __shared__ long long s_off[6];    // cell offsets of the (lower, upper) neighbour rows per axis
+    const int64_t row = blockIdx.x;
+    const int sl = (int)(row / P.nxc);
+    const int64_t x = row - (int64_t)sl * P.nxc;
+    const int ms = P.slot_mslot[sl];
+    if (threadIdx.x < 7) {
+        int64_t xn = x;
+        if (threadIdx.x > 0) {
+            const int d = (threadIdx.x - 1) >> 1, up = (threadIdx.x - 1) & 1;
+            const int64_t xs = d == 0 ? (int64_t)P.nx[1] * P.nx[2] : (d == 1 ? (int64_t)P.nx[2] : 1);
+            const int xi = (int)((x / xs) % P.nx[d]);
+            const int64_t step = up ? (xi == P.nx[d] - 1 ? 1 - P.nx[d] : 1) : (xi == 0 ? P.nx[d] - 1 : -1);
+            xn = x + step * xs;
+            s_off[threadIdx.x - 1] = (xn - x) * P.npc;
+        }
+        s_m[threadIdx.x] = P.mass_mode == 1 ? 0.0f : (float)P.m2[xn * 4 + ms];
+    }
+    __syncthreads();
+    const float m_own = s_m[0];
+    const long long* in_row = P.in + row * P.npc;
+    long long* out_row = P.out + row * P.npc;
+    const int np1 = P.np[1], np2 = P.np[2];
+    const int npc = (int)P.npc;
+    const int j0 = blockIdx.y * DRIFT_TILE + threadIdx.x;
+    long long nc[DRIFT_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < DRIFT_PER_THREAD; ++k) {
+        const int j = j0 + k * DRIFT_THREADS;
+        nc[k] = j < npc ? __ldg(in_row + j) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < DRIFT_PER_THREAD; ++k) {
+        const int j = j0 + k * DRIFT_THREADS;
+        if (j >= npc) break;
+        const int jz = j % np2, jxy = j / np2;
+        const int jy = jxy % np1, jx = jxy / np1;
+        const float pf[3] = {P.pf[0][jx], P.pf[1][jy], P.pf[2][jz]};
         const float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
-        const long long nc = __ldg(&P.in[cell]);
-        const int xi[3] = {(int)(x / ((int64_t)P.nx[1] * P.nx[2])), (int)((x / P.nx[2]) % P.nx[1]),
-                           (int)(x % P.nx[2])};
-        const int64_t xs[3] = {(int64_t)P.nx[1] * P.nx[2], (int64_t)P.nx[2], 1};
         long long acc = 0;
         bool own_done = false;
         long long own_C[3] = {0, 0, 0};
@@ -201,45 +273,36 @@ __global__ void __launch_bounds__(256) k_drift(const __grid_constant__ DriftArgs
         for (int d = 0; d < 3; ++d) {
             if (P.nx[d] == 1) continue;
             if (!own_done) {
-                const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + ms];
-                const float inv = 1.0f / sqrtf(ppf + m);
+                const float inv = 1.0f / sqrtf(ppf + m_own);
 #pragma unroll
-                for (int e = 0; e < 3; ++e)
-                    own_C[e] = __float2ll_rn(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
+                for (int e = 0; e < 3; ++e) own_C[e] = f2ll_rn(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
                 own_done = true;
             }
-            long long fplus, fminus;
-            if (pf[d] > 0.0f) {
-                const int64_t xl = x + (int64_t)((xi[d] == 0 ? P.nx[d] - 1 : -1)) * xs[d];
-                fplus = flux_fx(nc, own_C[d]);
-                fminus = flux_fx(__ldg(&P.in[cell + (xl - x) * P.npc]), courant_fx(P, xl, ms, pf[d], ppf));
-            } else {
-                const int64_t xh = x + (int64_t)((xi[d] == P.nx[d] - 1 ? 1 - P.nx[d] : 1)) * xs[d];
-                fplus = flux_fx(__ldg(&P.in[cell + (xh - x) * P.npc]), courant_fx(P, xh, ms, pf[d], ppf));
-                fminus = flux_fx(nc, own_C[d]);
+            if (pf[d] > 0.0f) {  // inflow through the lower face from the lower neighbour
+                const long long nn = __ldg(in_row + s_off[2 * d] + j);
+                acc += flux_fx(nc[k], own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
+            } else {             // inflow through the upper face from the upper neighbour
+                const long long nn = __ldg(in_row + s_off[2 * d + 1] + j);
+                acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(nc[k], own_C[d]);
             }
-            acc += fplus - fminus;
         }
-        P.out[cell] = nc - acc;
+        out_row[j] = nc[k] - acc;
         if (P.freal) {
+            const int64_t cell = row * P.npc + j;
             if (P.freal_double)
-                static_cast<double*>(P.freal)[cell] = (double)nc * TWO_POW_M40 / P.deg[sl];
+                static_cast<double*>(P.freal)[cell] = (double)nc[k] * TWO_POW_M40 / P.deg[sl];
             else
-                static_cast<float*>(P.freal)[cell] = __ll2float_rn(nc) * (float)(TWO_POW_M40 * P.inv_deg[sl]);
+                static_cast<float*>(P.freal)[cell] = ll2float_rn(nc[k]) * (float)(TWO_POW_M40 * P.inv_deg[sl]);
         }
     }
 }
 
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
 {
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int64_t blocks = (a.ncell + 255) / 256;
-    const int64_t cap = (int64_t)nsm * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_drift<<<(unsigned)blocks, 256, 0, s>>>(a);
+    const int64_t rows = a.ncell / a.npc;
+    const int64_t tiles = (a.npc + DRIFT_TILE - 1) / DRIFT_TILE;
+    if (rows < 1 || rows > 2147483647LL || tiles > 65535) return cudaErrorInvalidConfiguration;
+    k_drift<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -260,7 +323,7 @@ __global__ void k_convert(const long long* state, void* freal, int as_double, in
         if (as_double)
             static_cast<double*>(freal)[i] = (double)v * TWO_POW_M40 / degs[sl];
         else
-            static_cast<float*>(freal)[i] = __ll2float_rn(v) * (float)(TWO_POW_M40 / degs[sl]);
+            static_cast<float*>(freal)[i] = ll2float_rn(v) * (float)(TWO_POW_M40 / degs[sl]);
     }
 }
 
@@ -299,7 +362,7 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
                            (int)(j % P.np[2])};
         const float pf0 = P.pf[0][jv[0]], pf1 = P.pf[1][jv[1]], pf2 = P.pf[2][jv[2]];
         const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
-        const long long Efx = __float2ll_rn(sqrtf(ppf + m) * 16777216.0f);
+        const long long Efx = f2ll_rn(sqrtf(ppf + m) * 16777216.0f);
         const long long n = __ldg(&st[j]);
         v[0] += n;
         v[1] += (__int128)Efx * n;
@@ -366,7 +429,7 @@ __global__ void __launch_bounds__(256) k_convert_batch(const long long* __restri
     const float s0 = gluon_first_scale[2 * b], s1 = gluon_first_scale[2 * b + 1];
     const int per_slot = slot_cells[b];
     for (int64_t i = c0 + threadIdx.x; i < c0 + MASS_CHUNK && i < ncell; i += blockDim.x)
-        f[base + i] = __ll2float_rn(state[base + i]) * (i < per_slot ? s0 : s1);
+        f[base + i] = ll2float_rn(state[base + i]) * (i < per_slot ? s0 : s1);
 }
 
 cudaError_t launch_convert_batch(const long long* state, float* f, const int64_t* cell_prefix,
