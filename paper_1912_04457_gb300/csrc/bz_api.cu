@@ -34,6 +34,7 @@ struct bz_handle_s {
     long long* d_acc = nullptr;
     long long* d_flags = nullptr;
     void* d_freal = nullptr;       // f of the state, double-sized
+    int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     long long* d_state2 = nullptr; // second state buffer for bz_step
     int* d_qcount = nullptr;       // FP32 deferral queue: per-warp counts
     unsigned long long* d_qitems = nullptr;
@@ -136,6 +137,8 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_acc);
     cudaFree(h->d_flags);
     cudaFree(h->d_freal);
+    cudaFree(h->d_jtab);
+    h->d_jtab = nullptr;
     cudaFree(h->d_state2);
     cudaFree(h->d_qcount);
     cudaFree(h->d_qitems);
@@ -221,10 +224,16 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
     if (cudaMalloc(&h->d_m2[0], sizeof(double) * 4 * h->nxc) != cudaSuccess ||
         cudaMalloc(&h->d_m2[1], sizeof(double) * 4 * h->nxc) != cudaSuccess ||
         cudaMalloc(&h->d_acc, sizeof(long long) * 4 * h->nxc) != cudaSuccess ||
-        cudaMalloc(&h->d_flags, sizeof(long long) * 4) != cudaSuccess) {
+        cudaMalloc(&h->d_flags, sizeof(long long) * 4) != cudaSuccess ||
+        cudaMalloc(&h->d_jtab, sizeof(int) * h->npc) != cudaSuccess) {
         free_scratch(h);
         delete h;
         return fail(nullptr, BZ_ENOMEM, "cannot allocate handle scratch");
+    }
+    if (launch_fill_jtab(h->d_jtab, g->np, 0) != cudaSuccess) {
+        free_scratch(h);
+        delete h;
+        return fail(nullptr, BZ_ECUDA, "cannot build the p-cell index table");
     }
     if ((rc = alloc_scratch(h)) != BZ_OK) {
         g_init_error = h->err;
@@ -644,11 +653,13 @@ static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long*
         a.slot_mslot[sl] = mass_slot(sp);
         a.deg[sl] = kDeg[sp];
         a.inv_deg[sl] = 1.0 / kDeg[sp];
+        a.fscale[sl] = (float)(TWO_POW_M40 * a.inv_deg[sl]);
     }
     for (int d = 0; d < 3; ++d) {
         double dp = dp_of(h, d);
         for (int j = 0; j < h->g.np[d]; ++j) a.pf[d][j] = (float)(-h->g.L + ((double)j + 0.5) * dp);
     }
+    a.jtab = h->d_jtab;
     return BZ_OK;
 }
 
@@ -671,6 +682,7 @@ static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, doub
     for (int sl = 0; sl < NSPEC; ++sl) a.slot_mslot[sl] = mass_slot(sl < h->nslots ? h->slot_species[sl] : 0);
     double twopi = 2.0 * PI;
     a.pref = dp[0] * dp[1] * dp[2] / (twopi * twopi * twopi) * TWO_POW_M40;
+    a.jtab = h->d_jtab;  // null for the boxes of a batch
     return BZ_OK;
 }
 

@@ -113,6 +113,8 @@ struct DriftArgs {
     int slot_mslot[NSPEC];
     double inv_deg[NSPEC];  // per slot: 1 / N_s (f = n 2^-40 / N_s in the FP64 conversion)
     double deg[NSPEC];
+    float fscale[NSPEC];    // per slot: FP32 rounding of 2^-40 / N_s (the FP32 f is n_fp32 * fscale)
+    const int* jtab;        // [npc] jx | jy << 8 | jz << 16
     float pf[3][MAX_NP];    // FP32 cell-centre momenta per axis
 };
 
@@ -127,10 +129,19 @@ struct MomentArgs {
     int slot_mslot[NSPEC];
     double pref, half_dp[3];
     float pf[3][MAX_NP];
+    const int* jtab;        // [npc] jx | jy << 8 | jz << 16, or null (decoded by division)
+};
+
+// Per-slot scales of the f conversion: FP64 degeneracy, and the FP32
+// rounding of 2^-40 / N_s
+struct ConvScale {
+    double deg[NSPEC];
+    float f32[NSPEC];
 };
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
+cudaError_t launch_fill_jtab(int* jtab, const int* np, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
 // FP32 path, uniform sampler: re-evaluation of the queued terms with an FP64
 // root solve (one warp per queue segment)

@@ -17,6 +17,7 @@
 // mantissa bits; weights are rounded to int64 with integer operations only,
 // so the FP64 pipe is never used.
 #include "collide.cuh"
+#include "intconv.cuh"
 
 namespace bz {
 
@@ -49,25 +50,6 @@ __device__ __forceinline__ float unif23(uint32_t x)
 {
     // ((x >> 9) + 1/2) 2^-23, exactly: 1.m - 1 gives m 2^-23, + 2^-24 is exact
     return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-8f;
-}
-
-// round-half-even of |w| < 2^62 to int64 without conversion instructions
-__device__ __forceinline__ long long rint_ll(float w)
-{
-    const float aw = fabsf(w);
-    if (aw < 4194304.0f) {  // 2^22: the 1.5 2^23 shifter puts round(w) in the low mantissa bits
-        return (long long)(__float_as_int(w + 12582912.0f) - 0x4B400000);
-    }
-    const unsigned b = __float_as_uint(w);
-    const int e = (int)((b >> 23) & 0xffu) - 150;  // |w| >= 2^22: w is m 2^e with e >= -1
-    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
-    long long v;
-    if (e >= 0) {
-        v = m << e;
-    } else {  // e == -1: m/2, half even
-        v = (m >> 1) + ((m & 1) & ((m >> 1) & 1));
-    }
-    return (b >> 31) ? -v : v;
 }
 
 __device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)

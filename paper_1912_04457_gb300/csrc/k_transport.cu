@@ -4,6 +4,7 @@
 // which threads accumulate.
 #include <cstdint>
 #include "bz_internal.h"
+#include "intconv.cuh"
 
 namespace bz {
 
@@ -31,33 +32,6 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
         v += ((__int128)hi2 << 64) | (__int128)lo2;
     }
     return v;
-}
-
-// Conversions between FP32 and int64 without the FP64 pipe (the hardware
-// int64 conversions issue there, at 1/64 of the FP32 rate on this part).
-// f2ll_rn: round to nearest even; inside int32 range the 32-bit conversion
-// gives the same integer.
-__device__ __forceinline__ long long f2ll_rn(float v)
-{
-    return fabsf(v) < 2147483648.0f ? (long long)__float2int_rn(v) : __float2ll_rn(v);
-}
-
-// ll2float_rn: int64 to the nearest float (ties to even) with integer
-// instructions: keep the leading 24 bits, round on the rest, scale by 2^sh.
-__device__ __forceinline__ float ll2float_rn(long long v)
-{
-    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    float f;
-    if (a < (1ull << 24)) {
-        f = (float)(unsigned)a;
-    } else {
-        const int sh = 40 - __clzll((long long)a);
-        unsigned long long m = a >> sh;
-        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-        m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;
-        f = (float)(unsigned)m * __int_as_float((127 + sh) << 23);
-    }
-    return v < 0 ? -f : f;
 }
 
 // ---------------------------------------------------------------------------
@@ -206,7 +180,7 @@ __device__ __forceinline__ long long courant_fx(float m, float pdf, float ppf, f
 {
     const float inv = 1.0f / sqrtf(ppf + m);
     const float cf = (pdf * inv) * dtdxf;
-    return f2ll_rn(cf * 1073741824.0f);
+    return rint_ll(cf * 1073741824.0f);
 }
 
 // floor((n C + 2^29) / 2^30) as an int64 (two's complement, like the exact
@@ -229,6 +203,9 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
 {
     __shared__ float s_m[7];          // mass of this row's x cell, then (lower, upper) neighbour per axis
     __shared__ long long s_off[6];    // cell offsets of the (lower, upper) neighbour rows per axis
+    __shared__ float s_pf[3][MAX_NP]; // cell-centre momenta (lanes index them at different cells)
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
     const int64_t row = blockIdx.x;
     const int sl = (int)(row / P.nxc);
     const int64_t x = row - (int64_t)sl * P.nxc;
@@ -249,22 +226,15 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
     const float m_own = s_m[0];
     const long long* in_row = P.in + row * P.npc;
     long long* out_row = P.out + row * P.npc;
-    const int np1 = P.np[1], np2 = P.np[2];
     const int npc = (int)P.npc;
     const int j0 = blockIdx.y * DRIFT_TILE + threadIdx.x;
-    long long nc[DRIFT_PER_THREAD];
-#pragma unroll
-    for (int k = 0; k < DRIFT_PER_THREAD; ++k) {
-        const int j = j0 + k * DRIFT_THREADS;
-        nc[k] = j < npc ? __ldg(in_row + j) : 0;
-    }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < DRIFT_PER_THREAD; ++k) {
         const int j = j0 + k * DRIFT_THREADS;
         if (j >= npc) break;
-        const int jz = j % np2, jxy = j / np2;
-        const int jy = jxy % np1, jx = jxy / np1;
-        const float pf[3] = {P.pf[0][jx], P.pf[1][jy], P.pf[2][jz]};
+        const long long ncj = __ldg(in_row + j);
+        const int jp = __ldg(P.jtab + j);
+        const float pf[3] = {s_pf[0][jp & 0xff], s_pf[1][(jp >> 8) & 0xff], s_pf[2][jp >> 16]};
         const float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
         long long acc = 0;
         bool own_done = false;
@@ -275,24 +245,24 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
             if (!own_done) {
                 const float inv = 1.0f / sqrtf(ppf + m_own);
 #pragma unroll
-                for (int e = 0; e < 3; ++e) own_C[e] = f2ll_rn(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
+                for (int e = 0; e < 3; ++e) own_C[e] = rint_ll(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
                 own_done = true;
             }
             if (pf[d] > 0.0f) {  // inflow through the lower face from the lower neighbour
                 const long long nn = __ldg(in_row + s_off[2 * d] + j);
-                acc += flux_fx(nc[k], own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
+                acc += flux_fx(ncj, own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
             } else {             // inflow through the upper face from the upper neighbour
                 const long long nn = __ldg(in_row + s_off[2 * d + 1] + j);
-                acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(nc[k], own_C[d]);
+                acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(ncj, own_C[d]);
             }
         }
-        out_row[j] = nc[k] - acc;
+        out_row[j] = ncj - acc;
         if (P.freal) {
             const int64_t cell = row * P.npc + j;
             if (P.freal_double)
-                static_cast<double*>(P.freal)[cell] = (double)nc[k] * TWO_POW_M40 / P.deg[sl];
+                static_cast<double*>(P.freal)[cell] = (double)ncj * TWO_POW_M40 / P.deg[sl];
             else
-                static_cast<float*>(P.freal)[cell] = ll2float_rn(nc[k]) * (float)(TWO_POW_M40 * P.inv_deg[sl]);
+                static_cast<float*>(P.freal)[cell] = ll2float_rn(ncj) * P.fscale[sl];
         }
     }
 }
@@ -311,19 +281,17 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
 // FP32 rounding.
 // ---------------------------------------------------------------------------
 __global__ void k_convert(const long long* state, void* freal, int as_double, int64_t nxc, int64_t npc,
-                          int nslots, double deg0, double deg1, double deg2, double deg3, double deg4,
-                          double deg5, double deg6)
+                          int nslots, ConvScale sc)
 {
-    const double degs[NSPEC] = {deg0, deg1, deg2, deg3, deg4, deg5, deg6};
     const int64_t n = (int64_t)nslots * nxc * npc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int sl = (int)(i / (nxc * npc));
         const long long v = state[i];
         if (as_double)
-            static_cast<double*>(freal)[i] = (double)v * TWO_POW_M40 / degs[sl];
+            static_cast<double*>(freal)[i] = (double)v * TWO_POW_M40 / sc.deg[sl];
         else
-            static_cast<float*>(freal)[i] = ll2float_rn(v) * (float)(TWO_POW_M40 / degs[sl]);
+            static_cast<float*>(freal)[i] = ll2float_rn(v) * sc.f32[sl];
     }
 }
 
@@ -337,8 +305,30 @@ cudaError_t launch_convert(const long long* state, void* freal, int as_double, i
     int64_t blocks = (n + 255) / 256;
     if (blocks > (int64_t)nsm * 8) blocks = (int64_t)nsm * 8;
     if (blocks < 1) blocks = 1;
-    k_convert<<<(unsigned)blocks, 256, 0, s>>>(state, freal, as_double, nxc, npc, nslots, deg[0], deg[1],
-                                               deg[2], deg[3], deg[4], deg[5], deg[6]);
+    ConvScale sc;
+    for (int sl = 0; sl < NSPEC; ++sl) {
+        sc.deg[sl] = deg[sl];
+        sc.f32[sl] = (float)(TWO_POW_M40 * (1.0 / deg[sl]));  // as the drift's fscale
+    }
+    k_convert<<<(unsigned)blocks, 256, 0, s>>>(state, freal, as_double, nxc, npc, nslots, sc);
+    return cudaGetLastError();
+}
+
+// Packed momentum-cell indices jx | jy << 8 | jz << 16 of the linear p index
+// (np <= 256 per axis), built once per grid so the streaming kernels need no
+// integer division.
+__global__ void k_fill_jtab(int* jtab, int np0, int np1, int np2)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np0 * np1 * np2) return;
+    const int jz = j % np2, jxy = j / np2;
+    jtab[j] = (jxy / np1) | ((jxy % np1) << 8) | (jz << 16);
+}
+
+cudaError_t launch_fill_jtab(int* jtab, const int* np, cudaStream_t s)
+{
+    const int n = np[0] * np[1] * np[2];
+    k_fill_jtab<<<(n + 255) / 256, 256, 0, s>>>(jtab, np[0], np[1], np[2]);
     return cudaGetLastError();
 }
 
@@ -354,15 +344,30 @@ __device__ __forceinline__ double i128_to_double(__int128 v)
 // Exact sums of one (x cell, slot); writes 5 doubles at o.
 __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, int sl, double* o)
 {
+    __shared__ float s_pf[3][MAX_NP];  // cell-centre momenta (lanes index them at different cells)
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
+    __syncthreads();
     const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
     const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
+    const int npc = (int)P.npc, np1 = P.np[1], np2 = P.np[2];
     __int128 v[5] = {0, 0, 0, 0, 0};
-    for (int64_t j = threadIdx.x; j < P.npc; j += blockDim.x) {
-        const int jv[3] = {(int)(j / ((int64_t)P.np[1] * P.np[2])), (int)((j / P.np[2]) % P.np[1]),
-                           (int)(j % P.np[2])};
-        const float pf0 = P.pf[0][jv[0]], pf1 = P.pf[1][jv[1]], pf2 = P.pf[2][jv[2]];
+    for (int j = threadIdx.x; j < npc; j += blockDim.x) {
+        int jv[3];
+        if (P.jtab) {
+            const int jp = __ldg(P.jtab + j);
+            jv[0] = jp & 0xff;
+            jv[1] = (jp >> 8) & 0xff;
+            jv[2] = jp >> 16;
+        } else {
+            const int jxy = j / np2;
+            jv[0] = jxy / np1;
+            jv[1] = jxy % np1;
+            jv[2] = j % np2;
+        }
+        const float pf0 = s_pf[0][jv[0]], pf1 = s_pf[1][jv[1]], pf2 = s_pf[2][jv[2]];
         const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
-        const long long Efx = f2ll_rn(sqrtf(ppf + m) * 16777216.0f);
+        const long long Efx = rint_ll(sqrtf(ppf + m) * 16777216.0f);
         const long long n = __ldg(&st[j]);
         v[0] += n;
         v[1] += (__int128)Efx * n;
