@@ -487,6 +487,29 @@ static void fill_terms(bz_handle h, TermDev (*terms)[MAX_TERMS], int* nterms)
             o.cls = (int8_t)t[i].cls;
             o.sym = t[i].sym;
         }
+        // Kinematic groups: terms whose legs k1, k2, k3 carry the same masses have
+        // the same roots (only |M|^2 and the legs' species differ), so they are
+        // made adjacent, in order of first appearance, and the FP32 kernel solves
+        // the roots once per group.  With the massless dispersion every term has
+        // zero masses in the kinematics: one group.
+        TermDev sorted[MAX_TERMS];
+        bool used[MAX_TERMS] = {false};
+        int k = 0;
+        for (int i = 0; i < m; ++i) {
+            if (used[i]) continue;
+            for (int j = i; j < m; ++j) {
+                const bool same = h->mass_mode == BZ_MASS_MASSLESS ||
+                                  (terms[d][j].mslot[0] == terms[d][i].mslot[0] &&
+                                   terms[d][j].mslot[1] == terms[d][i].mslot[1] &&
+                                   terms[d][j].mslot[2] == terms[d][i].mslot[2]);
+                if (used[j] || !same) continue;
+                sorted[k] = terms[d][j];
+                sorted[k].gfirst = (int8_t)(j == i);
+                used[j] = true;
+                ++k;
+            }
+        }
+        for (int i = 0; i < m; ++i) terms[d][i] = sorted[i];
         nterms[d] = m;
     }
 }

@@ -31,7 +31,8 @@ struct TermDev {
     int8_t mslot[4];  // mass slot (0 g, 1..3 flavour) of each leg
     int8_t quark[4];  // 1 if the leg is a (anti)quark: F = 1 - f, else F = 1 + f
     int8_t cls;       // |M|^2 row
-    int8_t pad[3];
+    int8_t gfirst;    // 1 if the term opens a kinematic group (consecutive terms with equal leg masses)
+    int8_t pad[2];
     double sym;       // 1/2 for identical initial particles
 };
 

@@ -44,6 +44,10 @@ struct WarpSmem {
     // this unit's terms: masses of the legs and sym, packed leg slots / flags / row
     float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
     int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
+    int tfirst[MAX_TERMS];        // the term opens a kinematic group (its roots are solved, not reused)
+    // the running kinematic group's roots, per lane
+    float gz0[32], gz1[32], gE3[32], gsq[32];
+    int gfl[32];                  // root 0 valid | root 1 valid << 1 | defer << 2
 };
 
 __device__ __forceinline__ float unif23(uint32_t x)
@@ -57,10 +61,13 @@ __device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)
     return k == 0 ? a : (k == 1 ? b : (k == 2 ? c : d));
 }
 
+// Bin of a solved coordinate, clamped to [0, n).  floor(t) for 0 <= t < 2^23
+// is read from the mantissa of t + 2^23 added with rounding down (no
+// float-to-int conversion instruction; those issue on the FP64 pipe here).
 __device__ __forceinline__ int binf(float k, float L, float inv_dp, int n)
 {
-    int j = (int)floorf((k + L) * inv_dp);
-    j = j < 0 ? 0 : j;
+    const float t = fminf(fmaxf((k + L) * inv_dp, 0.0f), (float)n - 0.5f);
+    const int j = __float_as_int(__fadd_rd(t, 8388608.0f)) - 0x4B000000;
     return j >= n ? n - 1 : j;
 }
 
@@ -158,6 +165,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                                  sel4(T.mslot[2], m0, m1, m2v, m3), (float)T.sym);
         S.tinfo[lane] = T.slot[0] | (T.slot[1] << 3) | (T.slot[2] << 6) | (T.quark[0] << 9) | (T.quark[1] << 10)
                         | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
+        S.tfirst[lane] = T.gfirst;
     }
     const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
     float pm0 = 0.0f, pm1 = 0.0f, pm2 = 0.0f, ps3 = 1.0f, ps1 = 1.0f, pa = 1.0f;
@@ -274,56 +282,33 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         }
         flush = false;
         if (ti >= 0 && ti < nt) {
-            // ---- phase A: roots of term ti for this lane's live sample ----
-            const bool act = lane < bcnt;
+            // ---- phase A: term ti for this lane's live sample.  Terms of one
+            // kinematic group (equal leg masses) share E3, D, kappa, H, the roots
+            // and the FP64 deferral decision: the group's first term solves them,
+            // the others reuse them from shared memory. ----
             const int seq = bstart + lane;
-            const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
-            const float4 tmv = S.tm[ti];
-            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
-            const float E3 = sqrtf(bkk3 + mc2);
-            const float E = bEp + E3;
-            const float Pz = bPz;
-            const float a2 = ba2m + ma2;
-            const float b2 = bb2m + mb2;
-            const float D = E * E - Pz * Pz;
-            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
-            const float H = kap * kap - a2 * D;
-            bool v0 = false, v1 = false;
-            float z0 = 0.0f, z1 = 0.0f, sqH = 0.0f;
-            if (act && D > 0.0f) {
-                // FP64 re-evaluation of this term when it is ill-conditioned
-                // (|H| < tau kappa^2) or a solved coordinate sits on an edge
-                bool defer = may_defer && fabsf(H) < P.tau * (kap * kap);
-                bool e0 = false, e1v = false;
-                if (!defer && H > 0.0f) {
-                    sqH = sqrtf(H);
-                    const float kp = kap * Pz;
-                    const float sq = E * sqH;
-                    const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-                    if (Q != 0.0f) {
-                        z0 = Q / D;
-                        z1 = (E * E * a2 - kap * kap) / Q;
-                        const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
-                        e0 = e10 > 0.0f && e10 < E;
-                        e1v = e11 > 0.0f && e11 < E;
-                        const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                        defer = may_defer && ((marg_xy && (e0 || e1v))
-                                || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
-                                || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu))));
-                    }
-                }
-                if (defer) {
-                    const int qs = atomicAdd(dq.s_count, 1);
-                    if (qs < dq.cap) {
-                        dq.seg[qs] = box_tag | ((unsigned long long)a << 24)
-                                     | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)ti;
-                    } else {
-                        red_add(&P.flags[3], 1);  // queue full: keep the FP32 evaluation
-                        defer = false;
-                    }
-                }
-                if (!defer && k2xy_in && H > 0.0f) {
-                    if (sqH == 0.0f) {  // queue overflow of an ill-conditioned term
+            int gfl;
+            float z0, z1, E3, sqH;
+            if (S.tfirst[ti]) {
+                const bool act = lane < bcnt;
+                const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
+                const float4 tmv = S.tm[ti];
+                const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
+                E3 = sqrtf(bkk3 + mc2);
+                const float E = bEp + E3;
+                const float Pz = bPz;
+                const float a2 = ba2m + ma2;
+                const float b2 = bb2m + mb2;
+                const float D = E * E - Pz * Pz;
+                const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+                const float H = kap * kap - a2 * D;
+                bool v0 = false, v1 = false, defer = false;
+                z0 = z1 = sqH = 0.0f;
+                if (act && D > 0.0f) {
+                    // FP64 re-evaluation when the term is ill-conditioned
+                    // (|H| < tau kappa^2) or a solved coordinate sits on an edge
+                    defer = may_defer && fabsf(H) < P.tau * (kap * kap);
+                    if (H > 0.0f) {
                         sqH = sqrtf(H);
                         const float kp = kap * Pz;
                         const float sq = E * sqH;
@@ -331,13 +316,34 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                         if (Q != 0.0f) {
                             z0 = Q / D;
                             z1 = (E * E * a2 - kap * kap) / Q;
-                            const float e10 = (kap + Pz * z0) / E, e11 = (kap + Pz * z1) / E;
-                            e0 = e10 > 0.0f && e10 < E;
-                            e1v = e11 > 0.0f && e11 < E;
+                            // kappa + Pz z = E E2 at a root: valid iff 0 < E2 < E
+                            const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
+                            const bool e0 = w0 > 0.0f && w0 < EE, e1v = w1 > 0.0f && w1 < EE;
+                            if (may_defer && !defer) {
+                                const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+                                defer = (marg_xy && (e0 || e1v))
+                                        || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
+                                        || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
+                            }
+                            v0 = k2xy_in && e0 && in_box(z0, L) && in_box(Pz - z0, L);
+                            v1 = k2xy_in && e1v && in_box(z1, L) && in_box(Pz - z1, L);
                         }
                     }
-                    v0 = e0 && in_box(z0, L) && in_box(Pz - z0, L);
-                    v1 = e1v && in_box(z1, L) && in_box(Pz - z1, L);
+                }
+                gfl = (int)v0 | ((int)v1 << 1) | ((int)defer << 2);
+                S.gz0[lane] = z0; S.gz1[lane] = z1; S.gE3[lane] = E3; S.gsq[lane] = sqH; S.gfl[lane] = gfl;
+            } else {
+                z0 = S.gz0[lane]; z1 = S.gz1[lane]; E3 = S.gE3[lane]; sqH = S.gsq[lane]; gfl = S.gfl[lane];
+            }
+            bool v0 = gfl & 1, v1 = (gfl >> 1) & 1;
+            if (gfl & 4) {  // queued for FP64; when the queue is full the FP32 roots stand
+                const int qs = atomicAdd(dq.s_count, 1);
+                if (qs < dq.cap) {
+                    dq.seg[qs] = box_tag | ((unsigned long long)a << 24)
+                                 | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)ti;
+                    v0 = v1 = false;
+                } else {
+                    red_add(&P.flags[3], 1);
                 }
             }
             // append the valid roots to the ring
