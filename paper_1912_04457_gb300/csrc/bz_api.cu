@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -492,24 +493,35 @@ static void fill_terms(bz_handle h, TermDev (*terms)[MAX_TERMS], int* nterms)
         // made adjacent, in order of first appearance, and the FP32 kernel solves
         // the roots once per group.  With the massless dispersion every term has
         // zero masses in the kinematics: one group.
-        TermDev sorted[MAX_TERMS];
+        // The groups are then ordered by the |M|^2 row of their first term, so
+        // that the 32 roots evaluated together mostly share one row.
+        TermDev grouped[MAX_TERMS];
+        int gstart[MAX_TERMS], glen[MAX_TERMS], ng = 0;
         bool used[MAX_TERMS] = {false};
         int k = 0;
         for (int i = 0; i < m; ++i) {
             if (used[i]) continue;
+            gstart[ng] = k;
             for (int j = i; j < m; ++j) {
                 const bool same = h->mass_mode == BZ_MASS_MASSLESS ||
                                   (terms[d][j].mslot[0] == terms[d][i].mslot[0] &&
                                    terms[d][j].mslot[1] == terms[d][i].mslot[1] &&
                                    terms[d][j].mslot[2] == terms[d][i].mslot[2]);
                 if (used[j] || !same) continue;
-                sorted[k] = terms[d][j];
-                sorted[k].gfirst = (int8_t)(j == i);
+                grouped[k] = terms[d][j];
+                grouped[k].gfirst = (int8_t)(j == i);
                 used[j] = true;
                 ++k;
             }
+            glen[ng] = k - gstart[ng];
+            ++ng;
         }
-        for (int i = 0; i < m; ++i) terms[d][i] = sorted[i];
+        int order[MAX_TERMS];
+        for (int g = 0; g < ng; ++g) order[g] = g;
+        std::stable_sort(order, order + ng, [&](int x, int y) { return grouped[gstart[x]].cls < grouped[gstart[y]].cls; });
+        k = 0;
+        for (int g = 0; g < ng; ++g)
+            for (int i = 0; i < glen[order[g]]; ++i) terms[d][k++] = grouped[gstart[order[g]] + i];
         nterms[d] = m;
     }
 }
