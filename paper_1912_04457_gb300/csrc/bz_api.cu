@@ -563,6 +563,14 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.twoL = (R)twoL;
     a.L64 = h->g.L;
     for (int d = 0; d < 3; ++d) a.dp64[d] = twoL / h->g.np[d];
+    {
+        const int64_t nchunk = (nsamples + 31) / 32;
+        a.dv_group = div_magic((uint32_t)((nchunk + F32_GROUP - 1) / F32_GROUP));
+        a.dv_slot = div_magic((uint32_t)std::min<int64_t>(h->nxc * h->npc, 0x7fffffff));
+        a.dv_npc = div_magic((uint32_t)h->npc);
+        a.dv_yz = div_magic((uint32_t)(h->g.np[1] * h->g.np[2]));
+        a.dv_z = div_magic((uint32_t)h->g.np[2]);
+    }
     a.key0 = (uint32_t)(h->g.seed & 0xffffffffu) ^ h->g.box;
     a.key1 = (uint32_t)(h->g.seed >> 32);
     a.nsamples = nsamples;
@@ -615,6 +623,9 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
     if (h->ncell >= (int64_t)1 << 31)
         return fail(h, BZ_EINVAL, "the FP32 path needs fewer than 2^31 cells (has %lld)", (long long)h->ncell);
     const int64_t units = f32_units(n_sel, nsamples);
+    if (units >= ((int64_t)1 << 31))
+        return fail(h, BZ_EINVAL, "anchors x samples too large for one FP32 call (%lld work units); use an anchor subset",
+                    (long long)units);
     blocks = (units + F32_WARPS - 1) / F32_WARPS;
     if (blocks > (int64_t)h->nsm * 48) blocks = (int64_t)h->nsm * 48;
     if (blocks < 1) blocks = 1;
@@ -979,9 +990,9 @@ extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxe
     b->nmchunks = b->mchunk_prefix[nboxes];
     b->ncchunks = b->cchunk_prefix[nboxes];
     b->total_slots = b->slot_prefix[nboxes];
-    if (b->ncell >= ((int64_t)1 << 31)) {
+    if (b->ncell >= ((int64_t)1 << 31) || b->nunits >= ((int64_t)1 << 31)) {
         delete b;
-        return bfail(nullptr, BZ_EINVAL, "the batch needs fewer than 2^31 cells");
+        return bfail(nullptr, BZ_EINVAL, "the batch needs fewer than 2^31 cells and work units");
     }
     // persistent grid of up to 32 warps per SM; per-warp queue room for 4% of an
     // even share at 24 warps per SM (2.7% at 16, 5.3% at 32)
@@ -1432,6 +1443,7 @@ extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, in
     CK(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     const int64_t n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
     const int64_t units = f32_units(n_sel, nsamples);
+    if (units >= ((int64_t)1 << 31)) return fail(h, BZ_EINVAL, "anchors x samples too large for one record call");
     int64_t blocks = (units + F32_WARPS - 1) / F32_WARPS;
     if (blocks > (int64_t)h->nsm * 48) blocks = (int64_t)h->nsm * 48;
     if (blocks < 1) blocks = 1;

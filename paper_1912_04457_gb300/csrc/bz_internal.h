@@ -51,6 +51,25 @@ struct ProposalRecord {
 };
 constexpr int SAMPLER_LEARNED = 2;
 
+// Exact division of 0 <= n < 2^31 by a fixed d >= 1 (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with
+// l = ceil(log2 d) and m = ceil(2^(31+l) / d) < 2^32, n / d = (n m) >> (31 + l).
+struct DivMagic {
+    uint32_t m;
+    int s;
+};
+inline DivMagic div_magic(uint32_t d)
+{
+    int l = 0;
+    while (l < 32 && (1ull << l) < (unsigned long long)d) ++l;
+    const unsigned long long num = 1ull << (31 + l);
+    return DivMagic{(uint32_t)((num + d - 1) / d), 31 + l};
+}
+__host__ __device__ __forceinline__ uint32_t udiv(uint32_t n, DivMagic dm)
+{
+    return (uint32_t)(((unsigned long long)n * dm.m) >> dm.s);
+}
+
 template <typename R>
 struct CollideArgs {
     const void* f;          // f per cell [slot][x][p] (unused in equilibrium mode)
@@ -63,6 +82,9 @@ struct CollideArgs {
     int np[3];
     R L, twoL, dp[3];
     double L64, dp64[3];    // L and 2L/n in FP64 (the FP32 path's fixup works in FP64 geometry)
+    // FP32 path index decode without hardware division (all indices < 2^31):
+    // units per anchor, cells per slot, p cells, np[1] np[2], np[2]
+    DivMagic dv_group, dv_slot, dv_npc, dv_yz, dv_z;
     uint32_t key0, key1;
     int nsamples, step;
     int64_t n_sel, a_stride, a_offset;

@@ -138,15 +138,22 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     const int64_t nxc = P.nxc, npc = P.npc;
     const int nchunk = (P.nsamples + 31) >> 5;
     const int ngroup = (nchunk + F32_GROUP - 1) / F32_GROUP;
-    const int64_t al = unit / ngroup;
-    const int grp = (int)(unit - al * ngroup);
+    // index decode with exact multiply-shift division (all indices < 2^31)
+    const uint32_t al = udiv((uint32_t)unit, P.dv_group);
+    const int grp = (int)((uint32_t)unit - al * (uint32_t)ngroup);
     const int c0 = grp * F32_GROUP, c1 = min(c0 + F32_GROUP, nchunk);
-    const int64_t a = P.a_offset + al * P.a_stride;
-    const int sl = (int)(a / (nxc * npc));
-    const int64_t x = (a / npc) % nxc;
-    const int j = (int)(a % npc);
+    const int64_t a = P.a_offset + (int64_t)al * P.a_stride;
+    const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
+    const uint32_t rem = (uint32_t)a - sl_u * (uint32_t)(nxc * npc);
+    const uint32_t x_u = udiv(rem, P.dv_npc);
+    const int sl = (int)sl_u;
+    const int64_t x = x_u;
+    const int j = (int)(rem - x_u * (uint32_t)npc);
     const int d = P.slot_species[sl];
-    const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
+    const uint32_t jx_u = udiv((uint32_t)j, P.dv_yz);
+    const uint32_t ryz = (uint32_t)j - jx_u * (uint32_t)(P.np[1] * P.np[2]);
+    const uint32_t jy_u = udiv(ryz, P.dv_z);
+    const int jx = (int)jx_u, jy = (int)jy_u, jz = (int)(ryz - jy_u * (uint32_t)P.np[2]);
     const unsigned xoff = (unsigned)(x * npc);
     const unsigned slot_stride = (unsigned)(nxc * npc);
     // warp-uniform masses: lanes 0..4 convert one double each, then broadcast
@@ -639,11 +646,17 @@ __device__ __forceinline__ int bin64(double k, double L, double dp, int n)
 __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step)
 {
     const int64_t nxc = P.nxc, npc = P.npc;
-    const int sl = (int)(a / (nxc * npc));
-    const int64_t x = (a / npc) % nxc;
-    const int j = (int)(a % npc);
+    const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
+    const uint32_t rem = (uint32_t)a - sl_u * (uint32_t)(nxc * npc);
+    const uint32_t x_u = udiv(rem, P.dv_npc);
+    const int sl = (int)sl_u;
+    const int64_t x = x_u;
+    const int j = (int)(rem - x_u * (uint32_t)npc);
     const int d = P.slot_species[sl];
-    const int jx = j / (P.np[1] * P.np[2]), jy = (j / P.np[2]) % P.np[1], jz = j % P.np[2];
+    const uint32_t jx_u = udiv((uint32_t)j, P.dv_yz);
+    const uint32_t ryz = (uint32_t)j - jx_u * (uint32_t)(P.np[1] * P.np[2]);
+    const uint32_t jy_u = udiv(ryz, P.dv_z);
+    const int jx = (int)jx_u, jy = (int)jy_u, jz = (int)(ryz - jy_u * (uint32_t)P.np[2]);
     const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
     const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
     const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
