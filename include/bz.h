@@ -113,6 +113,22 @@ int bz_query_sizes(bz_handle h, int32_t* nslots, int64_t* nxcells, int64_t* npce
 int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples,
                       int32_t step, double dt, int32_t prec, int32_t sampler, void* stream);
 
+/* FP64 collision term (as bz_collision_term with BZ_PREC_F64 and the given
+ * sampler) plus the audit of Sec. III.B's conservation laws, computed on
+ * the GPU: audit_host (host double [8]) receives
+ *   [0] sum_roots w (E_p + E_3 - E_1 - E_2)   energy balance of the continuous legs,
+ *   [1..3] sum_roots w (p + k3 - k1 - k2)     momentum balance (x, y, z),
+ *   [4] sum_roots |w| (E_p + E_3 + E_1 + E_2)  the scale of [0..3],
+ *   [5] accepted roots, [6] sum_roots |w|,
+ *   [7] sum of A over all cells (exactly 0 with the symmetric sampler),
+ * w = c~ (2L)^5/(4N) dt/hbar_c 2^40 unquantised (the learned sampler
+ * includes 1/(32 q)).  [0..3] vanish to rounding (energy and momentum are
+ * conserved at the continuous leg momenta; the binned deposits are not,
+ * Sec. III.B).  The FP64 sums are accumulated with atomics, so their last
+ * bits depend on the order.  Synchronises.  Errors as bz_collision_term. */
+int bz_collision_audit(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples, int32_t step, double dt,
+                       int32_t sampler, double* audit_host, void* stream);
+
 /* Free streaming, Eq. (left handside) without the force term: first-order
  * upwind in flux form, periodic in x, v = p/E_p(x) with the handle's current
  * masses (E = |p| in mass mode MASSLESS).  Courant numbers in IEEE FP32 held
@@ -315,6 +331,23 @@ int bz_proposal_infer(bz_handle h, void* stream);
 int bz_proposal_anchor_params(bz_handle h, float* out_host, const float* in_host);
 /* Sampler used by bz_step: BZ_SAMPLER_SYMMETRIC (default) or BZ_SAMPLER_LEARNED. */
 int bz_set_step_sampler(bz_handle h, int32_t sampler);
+
+/* ------------------------------------------------------------------------
+ * Checkpoint (not in the paper).  The state, the step index (part of every
+ * Philox counter) and the current thermal masses (the next mass evaluation's
+ * dispersion) determine the rest of a run, so a run restarted from a
+ * checkpoint continues bit for bit.
+ * bz_save writes a little-endian file: a header (grid, seed, box, species
+ * mask, alpha_s, mass mode, step), the masses if set, the state (device
+ * int64 [ncell], copied; synchronises).
+ * bz_load reads it into h, which must have the same grid, seed, box,
+ * species, alpha_s and mass mode (else BZ_EINVAL): the state (device int64
+ * [ncell]) and *step (host) receive the saved values, and the saved masses
+ * become the handle's current masses.  Errors: BZ_EINVAL for a missing,
+ * unreadable, truncated or mismatched file.
+ * ------------------------------------------------------------------------ */
+int bz_save(bz_handle h, const int64_t* state, int64_t step, const char* path);
+int bz_load(bz_handle h, int64_t* state, int64_t* step, const char* path);
 
 /* Library version string. */
 const char* bz_version(void);

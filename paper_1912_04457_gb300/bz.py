@@ -72,6 +72,9 @@ SIGNATURES = {
     "bz_batch_tuning": (C.c_int, [_P, _P, _P, _P]),
     "bz_batch_get_masses": (C.c_int, [_P, _P]),
     "bz_batch_get_flags": (C.c_int, [_P, _P]),
+    "bz_collision_audit": (C.c_int, [_P, _P, _P, _I32, _I32, _D, _I32, _P, _P]),
+    "bz_save": (C.c_int, [_P, _P, _I64, C.c_char_p]),
+    "bz_load": (C.c_int, [_P, _P, _P, C.c_char_p]),
     "bz_proposal_nparams": (C.c_int, []),
     "bz_proposal_init": (C.c_int, [_P, C.c_uint64]),
     "bz_proposal_get_params": (C.c_int, [_P, _P]),
@@ -273,6 +276,29 @@ class Handle:
             self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
             _dev_ptr(A, torch.int64, self.ncell, "A"), nsamples, step, dt, prec, sampler,
             _stream_ptr(stream)))
+
+    def collision_audit(self, state, A, nsamples, step=0, dt=0.01, sampler=SAMPLER_SYMMETRIC, stream=None):
+        """FP64 collision term into A plus the conservation audit (numpy float64 [8])."""
+        import torch
+        out = np.zeros(8, dtype=np.float64)
+        self._check(self.lib.bz_collision_audit(
+            self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), _dev_ptr(A, torch.int64, self.ncell, "A"),
+            nsamples, step, dt, sampler, out.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return out
+
+    def save(self, state, step, path):
+        """Checkpoint of state (CUDA int64 tensor), the step index and the current masses."""
+        import torch
+        self._check(self.lib.bz_save(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), step,
+                                     os.fsencode(path)))
+
+    def load(self, state, path):
+        """Restores a checkpoint into state (CUDA int64 tensor); returns the saved step index."""
+        import torch
+        step = C.c_int64()
+        self._check(self.lib.bz_load(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"), C.byref(step),
+                                     os.fsencode(path)))
+        return step.value
 
     def drift(self, state_in, state_out, dt, stream=None):
         import torch

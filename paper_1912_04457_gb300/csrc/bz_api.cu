@@ -36,6 +36,8 @@ struct bz_handle_s {
     long long* d_flags = nullptr;
     void* d_freal = nullptr;       // f of the state, double-sized
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
+    double* d_audit = nullptr;     // bz_collision_audit sums (8)
+    bool audit_on = false;
     long long* d_state2 = nullptr; // second state buffer for bz_step
     int* d_qcount = nullptr;       // FP32 deferral queue: per-warp counts
     unsigned long long* d_qitems = nullptr;
@@ -131,6 +133,12 @@ static void prof_drain(bz_handle h)
     h->prof_pending.clear();
 }
 
+template <typename T>
+static bool dalloc(T** p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)) == cudaSuccess;
+}
+
 static void free_scratch(bz_handle h)
 {
     cudaFree(h->d_m2[0]);
@@ -140,6 +148,8 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_freal);
     cudaFree(h->d_jtab);
     h->d_jtab = nullptr;
+    cudaFree(h->d_audit);
+    h->d_audit = nullptr;
     cudaFree(h->d_state2);
     cudaFree(h->d_qcount);
     cudaFree(h->d_qitems);
@@ -547,6 +557,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.rec_count = nullptr;
     a.rec_cap = 0;
     a.rec_stride = 0;
+    a.audit = h->audit_on ? h->d_audit : nullptr;
     a.qcount = nullptr;
     a.qitems = nullptr;
     a.qcap = 0;
@@ -767,6 +778,115 @@ extern "C" int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, 
     return run_collide(h, reinterpret_cast<long long*>(A), nsamples, step, dt, prec, sampler, s);
 }
 
+extern "C" int bz_collision_audit(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples, int32_t step,
+                                  double dt, int32_t sampler, double* audit_host, void* stream)
+{
+    if (!h || !state || !A || !audit_host) return BZ_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!h->d_audit && !dalloc(&h->d_audit, 8)) return fail(h, BZ_ENOMEM, "scratch");
+    CK(h, cudaMemsetAsync(h->d_audit, 0, 8 * sizeof(double), s));
+    h->audit_on = true;
+    const int rc = bz_collision_term(h, state, A, nsamples, step, dt, BZ_PREC_F64, sampler, stream);
+    h->audit_on = false;
+    if (rc) return rc;
+    // slot 7 (zeroed above, as an int64) receives the exact sum of A
+    long long* sum = reinterpret_cast<long long*>(h->d_audit + 7);
+    CK(h, launch_sum_ll(reinterpret_cast<const long long*>(A), h->ncell, sum, s));
+    double host[8];
+    CK(h, cudaMemcpyAsync(host, h->d_audit, sizeof host, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    long long sa;
+    std::memcpy(&sa, &host[7], sizeof sa);
+    host[7] = (double)sa;
+    std::memcpy(audit_host, host, sizeof host);
+    return BZ_OK;
+}
+
+namespace {
+// Checkpoint file: this header, then the current masses (double [nx][4]) if
+// have_masses, then the state (int64 [ncell]), all little-endian.
+struct CkptHeader {
+    char magic[8];  // "BZCKPT1"
+    int32_t nx[3], np[3];
+    double dx, L;
+    uint64_t seed;
+    uint32_t box, species_mask;
+    double alpha_s;
+    int32_t mass_mode, have_masses;
+    int64_t step, ncell;
+};
+const char kCkptMagic[8] = {'B', 'Z', 'C', 'K', 'P', 'T', '1', 0};
+}  // namespace
+
+extern "C" int bz_save(bz_handle h, const int64_t* state, int64_t step, const char* path)
+{
+    if (!h || !state || !path) return BZ_EINVAL;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    for (int d = 0; d < 3; ++d) {
+        hd.nx[d] = h->g.nx[d];
+        hd.np[d] = h->g.np[d];
+    }
+    hd.dx = h->g.dx;
+    hd.L = h->g.L;
+    hd.seed = h->g.seed;
+    hd.box = h->g.box;
+    hd.species_mask = h->mask;
+    hd.alpha_s = h->alpha_s;
+    hd.mass_mode = h->mass_mode;
+    hd.have_masses = h->have_masses ? 1 : 0;
+    hd.step = step;
+    hd.ncell = h->ncell;
+    std::vector<double> m2(h->have_masses ? 4 * h->nxc : 0);
+    std::vector<int64_t> st(h->ncell);
+    CK(h, cudaDeviceSynchronize());
+    if (h->have_masses)
+        CK(h, cudaMemcpy(m2.data(), h->d_m2[h->cur], sizeof(double) * m2.size(), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(st.data(), state, sizeof(int64_t) * st.size(), cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(h, BZ_EINVAL, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 &&
+              (m2.empty() || std::fwrite(m2.data(), sizeof(double), m2.size(), f) == m2.size()) &&
+              std::fwrite(st.data(), sizeof(int64_t), st.size(), f) == st.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(h, BZ_EINVAL, "cannot write %s", path);
+    return BZ_OK;
+}
+
+extern "C" int bz_load(bz_handle h, int64_t* state, int64_t* step, const char* path)
+{
+    if (!h || !state || !step || !path) return BZ_EINVAL;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, BZ_EINVAL, "cannot open %s", path);
+    CkptHeader hd{};
+    bool ok = std::fread(&hd, sizeof hd, 1, f) == 1 && std::memcmp(hd.magic, kCkptMagic, 8) == 0;
+    if (ok) {
+        for (int d = 0; d < 3; ++d) ok = ok && hd.nx[d] == h->g.nx[d] && hd.np[d] == h->g.np[d];
+        ok = ok && hd.dx == h->g.dx && hd.L == h->g.L && hd.seed == h->g.seed && hd.box == h->g.box &&
+             hd.species_mask == h->mask && hd.alpha_s == h->alpha_s && hd.mass_mode == h->mass_mode &&
+             hd.ncell == h->ncell;
+        if (!ok) {
+            std::fclose(f);
+            return fail(h, BZ_EINVAL, "checkpoint %s was written for another grid, species set or mass mode", path);
+        }
+    }
+    std::vector<double> m2(ok && hd.have_masses ? 4 * h->nxc : 0);
+    std::vector<int64_t> st(h->ncell);
+    ok = ok && (m2.empty() || std::fread(m2.data(), sizeof(double), m2.size(), f) == m2.size()) &&
+         std::fread(st.data(), sizeof(int64_t), st.size(), f) == st.size();
+    std::fclose(f);
+    if (!ok) return fail(h, BZ_EINVAL, "%s is not a complete checkpoint", path);
+    CK(h, cudaMemcpy(state, st.data(), sizeof(int64_t) * st.size(), cudaMemcpyHostToDevice));
+    if (!m2.empty()) {
+        CK(h, cudaMemcpy(h->d_m2[h->cur], m2.data(), sizeof(double) * m2.size(), cudaMemcpyHostToDevice));
+        h->have_masses = true;
+    } else {
+        h->have_masses = false;
+    }
+    *step = hd.step;
+    return BZ_OK;
+}
+
 extern "C" int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt, void* stream)
 {
     if (!h || !in || !out) return BZ_EINVAL;
@@ -923,11 +1043,6 @@ static void batch_free(bz_batch b)
     }
 }
 
-template <typename T>
-static bool dalloc(T** p, size_t n)
-{
-    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)) == cudaSuccess;
-}
 
 extern "C" int bz_batch_create(bz_batch* out, int32_t nboxes, const bz_box* boxes)
 {

@@ -103,6 +103,10 @@ struct CollideArgs {
     long long rec_cap;
     int rec_stride;  // 0: off; else units with index % rec_stride == 0 are recorded
     // FP32 path: terms with |H| < tau kappa^2 are queued per warp for FP64
+    // FP64 path: continuous-leg audit sums per accepted root, or null:
+    // [0] sum w (Ep + E3 - E1 - E2), [1..3] sum w (p + k3 - k1 - k2), [4] sum |w| (Ep + E3 + E1 + E2),
+    // [5] roots, [6] sum |w|; w = c~ Kq (unquantised)
+    double* audit;
     R tau;                          // 0: never defer
     int* qcount;                    // [warps] items queued by each warp
     unsigned long long* qitems;     // [warps][qcap] packed (anchor << 24 | sample << 4 | term)
@@ -165,6 +169,8 @@ struct ConvScale {
 // launchers (return cudaGetLastError())
 cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStream_t s);
 cudaError_t launch_fill_jtab(int* jtab, const int* np, cudaStream_t s);
+// exact int64 sum of a[0, n) added into *out
+cudaError_t launch_sum_ll(const long long* a, int64_t n, long long* out, cudaStream_t s);
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
 // FP32 path, uniform sampler: re-evaluation of the queued terms with an FP64
 // root solve (one warp per queue segment)

@@ -316,6 +316,16 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
             red_add(&P.flags[1], 1);
             continue;
         }
+        if (P.audit) {  // continuous-leg energy / momentum balance of this deposit set
+            const double w = (double)(ct * P.Kq * (P.sampler == SAMPLER_LEARNED ? G.wfac : R(1)));
+            atomicAdd(&P.audit[0], w * (double)((Ep + E3) - (E1 + E2)));
+            atomicAdd(&P.audit[1], w * (double)((G.p[0] + G.k3[0]) - (G.k1x + G.bx)));
+            atomicAdd(&P.audit[2], w * (double)((G.p[1] + G.k3[1]) - (G.k1y + G.by)));
+            atomicAdd(&P.audit[3], w * (double)((G.p[2] + G.k3[2]) - (z + dz)));
+            atomicAdd(&P.audit[4], fabs(w) * (double)(Ep + E3 + E1 + E2));
+            atomicAdd(&P.audit[5], 1.0);
+            atomicAdd(&P.audit[6], fabs(w));
+        }
         const long long q = O::rint_(wq);
         if (q == 0) continue;
         own += q;

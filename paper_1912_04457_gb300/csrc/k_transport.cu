@@ -314,6 +314,24 @@ cudaError_t launch_convert(const long long* state, void* freal, int as_double, i
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_sum_ll(const long long* __restrict__ a, int64_t n, long long* out)
+{
+    long long v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v += a[i];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0 && v != 0) red_add_ll(out, v);
+}
+
+cudaError_t launch_sum_ll(const long long* a, int64_t n, long long* out, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_sum_ll<<<(unsigned)blocks, 256, 0, s>>>(a, n, out);
+    return cudaGetLastError();
+}
+
 // Packed momentum-cell indices jx | jy << 8 | jz << 16 of the linear p index
 // (np <= 256 per axis), built once per grid so the streaming kernels need no
 // integer division.

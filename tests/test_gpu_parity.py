@@ -80,6 +80,33 @@ def test_collision_f64_bit_exact(name, np_, mask, N, mass_mode, sampler):
     assert np.array_equal(h.flags()[:2], ref["flags"])
 
 
+@pytest.mark.parametrize("mask,mass_mode,sampler", [(0x01, 0, 0), (0x7F, 0, 0), (0x7F, 1, 1)])
+def test_collision_audit_matches_oracle(mask, mass_mode, sampler):
+    """bz_collision_audit: the same int64 deposits as the oracle, its continuous-leg
+    energy / momentum balance (zero to rounding against the |w| E scale), the root
+    count exactly, the other sums to FP64 summation-order rounding, and sum A = 0
+    for the symmetric sampler."""
+    torch = torch_mod()
+    np_ = (8, 8, 8)
+    h, cfg = make_pair(np_=np_, mask=mask, mass_mode=mass_mode, seed=5)
+    st = random_state(mask, 1, np_, 21)
+    A = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    N, step, dt = 48, 2, 0.01
+    aud = h.collision_audit(to_dev(st), A, N, step, dt, sampler)
+    ref = O.collision(cfg, st, O.masses(cfg, st), N, step=step, dt=dt, sampler=sampler, want_audit=True)
+    assert np.array_equal(A.cpu().numpy().reshape(ref["A"].shape), ref["A"])
+    ra = ref["audit"]
+    assert aud[5] == ra[5] and aud[5] > 0
+    for k in (4, 6):
+        assert aud[k] == pytest.approx(ra[k], rel=1e-12)
+    for k in range(4):
+        assert abs(aud[k]) <= 1e-12 * aud[4] and abs(aud[k] - ra[k]) <= 1e-12 * aud[4]
+    if sampler == 0:
+        assert aud[7] == 0.0
+    else:
+        assert aud[7] == float(ref["A"].sum()) and aud[7] != 0.0
+
+
 def test_second_call_uses_previous_dispersion():
     from paper_1912_04457_gb300 import bz
     torch = torch_mod()
