@@ -167,6 +167,12 @@ int bz_reset_masses(bz_handle h);
 int bz_get_flags(bz_handle h, int64_t* flags_host);
 int bz_clear_flags(bz_handle h);
 
+/* Resolution of the uniforms of the FP64 path: 32 (default, u = (x + 1/2)
+ * 2^-32 from each Philox word x) or 23 (u = ((x >> 9) + 1/2) 2^-23, the
+ * uniforms of the FP32 path, so both paths evaluate the same sample points).
+ * Errors: BZ_EINVAL for other values. */
+int bz_set_uniform_bits(bz_handle h, int32_t bits);
+
 /* Restricts the anchors to those with linear index a = (slot nx + x) np + p
  * satisfying a % stride == offset (stride 1 = all).  Used to check full
  * size workloads against the CPU oracle on a sample of anchors. */

@@ -37,6 +37,7 @@ struct bz_handle_s {
     void* d_freal = nullptr;       // f of the state, double-sized
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
+    int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
     bool audit_on = false;
     long long* d_state2 = nullptr; // second state buffer for bz_step
     int* d_qcount = nullptr;       // FP32 deferral queue: per-warp counts
@@ -330,6 +331,14 @@ extern "C" int bz_query_sizes(bz_handle h, int32_t* nslots, int64_t* nxcells, in
     return BZ_OK;
 }
 
+extern "C" int bz_set_uniform_bits(bz_handle h, int32_t bits)
+{
+    if (!h) return BZ_EINVAL;
+    if (bits != 32 && bits != 23) return fail(h, BZ_EINVAL, "uniform bits must be 32 or 23");
+    h->f64_ubits = bits;
+    return BZ_OK;
+}
+
 extern "C" int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset)
 {
     if (!h) return BZ_EINVAL;
@@ -550,7 +559,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     double twopi5 = twopi * twopi * twopi * twopi * twopi;
     a.f = h->d_freal;
     a.f_is_float = sizeof(R) == 4 ? 1 : 0;
-    a.ubits = sizeof(R) == 4 ? 23 : 32;
+    a.ubits = sizeof(R) == 4 ? 23 : h->f64_ubits;
     a.tau = 0;
     a.prop = h->d_anchor_prm;
     a.rec = nullptr;

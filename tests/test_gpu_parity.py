@@ -107,6 +107,28 @@ def test_collision_audit_matches_oracle(mask, mass_mode, sampler):
         assert aud[7] == float(ref["A"].sum()) and aud[7] != 0.0
 
 
+def test_f64_path_on_23_bit_uniforms():
+    """With bz_set_uniform_bits(23) the FP64 path evaluates the FP32 path's sample
+    points: bit-identical to the oracle at ubits = 23, and the FP32 path within
+    the FP32 tolerance of it."""
+    from paper_1912_04457_gb300 import bz
+    torch = torch_mod()
+    np_, mask, N = (8, 8, 8), 0x7F, 48
+    h, cfg = make_pair(np_=np_, mask=mask, seed=13)
+    st = random_state(mask, 1, np_, 17)
+    A64 = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    A32 = torch.empty_like(A64)
+    h.set_uniform_bits(23)
+    h.collision_term(to_dev(st), A64, N, 4, 0.01, bz.PREC_F64)
+    h.reset_masses()
+    h.collision_term(to_dev(st), A32, N, 4, 0.01, bz.PREC_F32)
+    ref = O.collision(cfg, st, O.masses(cfg, st), N, step=4, dt=0.01, ubits=23)["A"]
+    assert np.array_equal(A64.cpu().numpy().reshape(ref.shape), ref)
+    assert rel_l2(A32.cpu().numpy(), A64.cpu().numpy()) <= F32_TOL
+    with pytest.raises(bz.BzError):
+        h.set_uniform_bits(24)
+
+
 def test_second_call_uses_previous_dispersion():
     from paper_1912_04457_gb300 import bz
     torch = torch_mod()
