@@ -36,6 +36,7 @@ struct bz_handle_s {
     long long* d_flags = nullptr;
     void* d_freal = nullptr;       // f of the state, double-sized
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
+    float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
     int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
     bool audit_on = false;
@@ -149,6 +150,8 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_freal);
     cudaFree(h->d_jtab);
     h->d_jtab = nullptr;
+    cudaFree(h->d_inv_e);
+    h->d_inv_e = nullptr;
     cudaFree(h->d_audit);
     h->d_audit = nullptr;
     cudaFree(h->d_state2);
@@ -177,11 +180,15 @@ static int alloc_scratch(bz_handle h)
 {
     cudaFree(h->d_freal);
     cudaFree(h->d_state2);
+    cudaFree(h->d_inv_e);
     h->d_freal = nullptr;
     h->d_state2 = nullptr;
+    h->d_inv_e = nullptr;
     h->ncell = (int64_t)h->nslots * h->nxc * h->npc;
     if (cudaMalloc(&h->d_freal, sizeof(double) * h->ncell) != cudaSuccess)
         return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for f", (long long)(8 * h->ncell));
+    if (h->nxc > 1 && cudaMalloc(&h->d_inv_e, sizeof(float) * h->ncell) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for the drift", (long long)(4 * h->ncell));
     return BZ_OK;
 }
 
@@ -726,6 +733,7 @@ static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long*
         for (int j = 0; j < h->g.np[d]; ++j) a.pf[d][j] = (float)(-h->g.L + ((double)j + 0.5) * dp);
     }
     a.jtab = h->d_jtab;
+    a.inv_e = h->d_inv_e;
     return BZ_OK;
 }
 

@@ -142,6 +142,7 @@ struct DriftArgs {
     double deg[NSPEC];
     float fscale[NSPEC];    // per slot: FP32 rounding of 2^-40 / N_s (the FP32 f is n_fp32 * fscale)
     const int* jtab;        // [npc] jx | jy << 8 | jz << 16
+    float* inv_e;           // [ncell] scratch: 1/sqrt(p^2 + m^2) of every cell, written by k_inv_energy
     float pf[3][MAX_NP];    // FP32 cell-centre momenta per axis
 };
 

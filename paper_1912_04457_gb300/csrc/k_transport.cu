@@ -199,6 +199,51 @@ __device__ __forceinline__ long long flux_fx(long long n, long long C)
     return (long long)(prod >> 30);
 }
 
+// Inverse energy 1/sqrt(p^2 + m^2(x)) (IEEE FP32, the factor of every
+// Courant number) of each cell, once per step, so that the drift reads the
+// upwind neighbours' values instead of recomputing them per face.
+__global__ void __launch_bounds__(DRIFT_THREADS) k_inv_energy(const __grid_constant__ DriftArgs P)
+{
+    __shared__ float s_pf[3][MAX_NP];
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
+    __syncthreads();
+    const int64_t row = blockIdx.x;
+    const int sl = (int)(row / P.nxc);
+    const int64_t x = row - (int64_t)sl * P.nxc;
+    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
+    const int npc = (int)P.npc;
+    float* out = P.inv_e + row * P.npc;
+    for (int j = blockIdx.y * DRIFT_TILE + threadIdx.x, k = 0; k < DRIFT_PER_THREAD && j < npc;
+         ++k, j += DRIFT_THREADS) {
+        const int jp = __ldg(P.jtab + j);
+        const float p0 = s_pf[0][jp & 0xff], p1 = s_pf[1][(jp >> 8) & 0xff], p2 = s_pf[2][jp >> 16];
+        out[j] = 1.0f / sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + m);
+    }
+}
+
+// Narrow forms for |C| < 2^31 (every stable step: |c| <= dt/dx < 2): round to
+// int32, and n C split exactly into a signed 32 x 32 and an unsigned
+// 32 x 32 product, n = nh 2^32 + nl.
+__device__ __forceinline__ int rint_i32(float w)  // round half even, |w| < 2^31
+{
+    if (fabsf(w) < 4194304.0f) return __float_as_int(w + 12582912.0f) - 0x4B400000;
+    const unsigned b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xffu) - 150;  // w = m 2^e, e >= -1
+    const int m = (int)((b & 0x7fffffu) | 0x800000u);
+    const int v = e >= 0 ? m << e : (m >> 1) + ((m & 1) & ((m >> 1) & 1));
+    return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ long long flux32(int nh, unsigned nl, int C)
+{
+    const long long hi = (long long)nh * C;
+    long long lo = (long long)((unsigned long long)nl * (unsigned)C);
+    if (C < 0) lo -= (long long)((unsigned long long)nl << 32);  // nl (C + 2^32) - nl 2^32
+    return (long long)(((unsigned long long)hi << 2) + (unsigned long long)((lo + (1LL << 29)) >> 30));
+}
+
+template <bool NARROW>
 __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__ DriftArgs P)
 {
     __shared__ float s_m[7];          // mass of this row's x cell, then (lower, upper) neighbour per axis
@@ -237,23 +282,54 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
         const float pf[3] = {s_pf[0][jp & 0xff], s_pf[1][(jp >> 8) & 0xff], s_pf[2][jp >> 16]};
         const float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
         long long acc = 0;
-        bool own_done = false;
-        long long own_C[3] = {0, 0, 0};
+        if (NARROW && P.inv_e) {
+            const float* ie_row = P.inv_e + row * P.npc;
+            const float inv = __ldg(ie_row + j);
+            const int nh = (int)(ncj >> 32);
+            const unsigned nl = (unsigned)ncj;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (P.nx[d] == 1) continue;
-            if (!own_done) {
-                const float inv = 1.0f / sqrtf(ppf + m_own);
-#pragma unroll
-                for (int e = 0; e < 3; ++e) own_C[e] = rint_ll(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
-                own_done = true;
+            for (int d = 0; d < 3; ++d) {
+                if (P.nx[d] == 1) continue;
+                const int own_C = rint_i32(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
+                const long long off = s_off[2 * d + (pf[d] > 0.0f ? 0 : 1)];  // the upwind neighbour
+                const long long nn = __ldg(in_row + off + j);
+                const int nb_C = rint_i32(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
+                const long long f_own = flux32(nh, nl, own_C), f_nb = flux32((int)(nn >> 32), (unsigned)nn, nb_C);
+                // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down
+                acc += pf[d] > 0.0f ? f_own - f_nb : f_nb - f_own;
             }
-            if (pf[d] > 0.0f) {  // inflow through the lower face from the lower neighbour
-                const long long nn = __ldg(in_row + s_off[2 * d] + j);
-                acc += flux_fx(ncj, own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
-            } else {             // inflow through the upper face from the upper neighbour
-                const long long nn = __ldg(in_row + s_off[2 * d + 1] + j);
-                acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(ncj, own_C[d]);
+        } else if (P.inv_e) {  // inverse energies of every cell precomputed by k_inv_energy
+            const float* ie_row = P.inv_e + row * P.npc;
+            const float inv = __ldg(ie_row + j);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (P.nx[d] == 1) continue;
+                const long long own_C = rint_ll(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
+                const long long off = s_off[2 * d + (pf[d] > 0.0f ? 0 : 1)];  // the upwind neighbour
+                const long long nn = __ldg(in_row + off + j);
+                const long long nb_C = rint_ll(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
+                // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down
+                acc += pf[d] > 0.0f ? flux_fx(ncj, own_C) - flux_fx(nn, nb_C) : flux_fx(nn, nb_C) - flux_fx(ncj, own_C);
+            }
+        } else {
+            bool own_done = false;
+            long long own_C[3] = {0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (P.nx[d] == 1) continue;
+                if (!own_done) {
+                    const float inv = 1.0f / sqrtf(ppf + m_own);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) own_C[e] = rint_ll(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
+                    own_done = true;
+                }
+                if (pf[d] > 0.0f) {  // inflow through the lower face from the lower neighbour
+                    const long long nn = __ldg(in_row + s_off[2 * d] + j);
+                    acc += flux_fx(ncj, own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
+                } else {             // inflow through the upper face from the upper neighbour
+                    const long long nn = __ldg(in_row + s_off[2 * d + 1] + j);
+                    acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(ncj, own_C[d]);
+                }
             }
         }
         out_row[j] = ncj - acc;
@@ -272,7 +348,14 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
     const int64_t rows = a.ncell / a.npc;
     const int64_t tiles = (a.npc + DRIFT_TILE - 1) / DRIFT_TILE;
     if (rows < 1 || rows > 2147483647LL || tiles > 65535) return cudaErrorInvalidConfiguration;
-    k_drift<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
+    const bool moving = a.nx[0] > 1 || a.nx[1] > 1 || a.nx[2] > 1;
+    if (a.inv_e && moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
+    DriftArgs b = a;
+    if (!moving) b.inv_e = nullptr;
+    if (a.dtdxf < 1.99f)  // |C| <= 2^30 dt/dx < 2^31
+        k_drift<true><<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(b);
+    else
+        k_drift<false><<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(b);
     return cudaGetLastError();
 }
 
