@@ -682,22 +682,9 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         ProfScope ps(h, BZ_K_COLLIDE, s);
         CK(h, launch_collide_f32(a, (int)blocks, s));
     }
-    if (sampler != BZ_SAMPLER_LEARNED) {  // FP64 root solve, FP32 integrand
+    {  // FP64 sample point and root solve, FP32 integrand
         ProfScope ps(h, BZ_K_FIXUP, s);
         CK(h, launch_fixup_f32(a, (int)warps, s));
-        return BZ_OK;
-    }
-    // learned sampler: the whole term in FP64 (its inverse-CDF coordinates need FP64 logarithms)
-    CollideArgs<double> b{};
-    fill_collide(h, b, A, nsamples, step, dt, sampler);
-    b.f_is_float = 1;
-    b.ubits = 23;
-    b.qcount = h->d_qcount;
-    b.qitems = h->d_qitems;
-    b.qcap = qcap;
-    {
-        ProfScope ps(h, BZ_K_FIXUP, s);
-        CK(h, launch_fixup(b, (int)warps, s));
     }
     return BZ_OK;
 }

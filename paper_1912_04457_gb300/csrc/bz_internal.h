@@ -178,7 +178,6 @@ cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream
 cudaError_t launch_fixup_f32(const CollideArgs<float>& a, int nseg, cudaStream_t s);
 cudaError_t launch_fixup_f32_batch(const CollideArgs<float>* boxes, const int* qcount, const unsigned long long* qitems,
                                    int64_t qcap, const int* step_dev, int nseg, cudaStream_t s);
-cudaError_t launch_fixup(const CollideArgs<double>& a, int nseg, cudaStream_t s);
 cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int64_t* prefix, int nboxes,
                                      unsigned long long* counter, const int* step_dev, int chunk, int grid,
                                      int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s);

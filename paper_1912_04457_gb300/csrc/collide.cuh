@@ -18,9 +18,10 @@
 // ellipsoid the discriminant H = kappa^2 - a^2 D is a small difference of
 // O(E^4) numbers and the integrand goes like 1/sqrt(H), so FP32 rounding
 // of the inputs alone gives O(eps kappa^2 / H) relative error.  The FP32
-// kernel therefore queues every term with |H| < tau kappa^2 (about 0.4% of
-// them at tau = 2e-3) and k_fixup re-evaluates those in FP64 from the same
-// Philox counter; deposits are still exact integers.
+// kernel therefore queues every term with |H| < tau kappa^2 (about 0.3% of
+// the in-box terms at tau = 2e-3) and k_fixup_f32 redoes their sample point
+// and root solve in FP64 from the same Philox counter; deposits are still
+// exact integers.
 #pragma once
 #include <cstdint>
 #include "bz_internal.h"
@@ -218,11 +219,9 @@ struct DeferCtx {
 };
 
 // Evaluates term ti of sample (a, smp); deposits the k1, k2, k3 legs and
-// returns the anchor cell's +q.  With DEFER, an ill-conditioned term is
-// queued instead (returns 0) unless the warp's queue segment is full.
-template <typename R, bool DEFER>
-__device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Geom<R>& G, int64_t a, int smp, int ti,
-                                               DeferCtx* dq)
+// returns the anchor cell's +q.
+template <typename R>
+__device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Geom<R>& G, int64_t a, int smp, int ti)
 {
     using O = Ops<R>;
     const R L = P.L;
@@ -240,16 +239,6 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
     const R D = E * E - Pz * Pz;
     const R kap = (E * E + a2 - b2 - Pz * Pz) * R(0.5);
     const R H = kap * kap - a2 * D;
-    if (DEFER) {
-        if (G.k2xy_in && D > R(0) && O::fabs_(H) < P.tau * (kap * kap)) {
-            const int slot = atomicAdd(dq->s_count, 1);
-            if (slot < dq->cap) {
-                dq->seg[slot] = ((unsigned long long)a << 24) | ((unsigned long long)smp << 4) | (unsigned long long)ti;
-                return 0;
-            }
-            red_add(&P.flags[3], 1);  // queue full: evaluate in FP32 below
-        }
-    }
     if (H < R(0) || D <= R(0)) return 0;
     if (!G.k2xy_in) return 0;
     const R kp = kap * Pz;
@@ -338,26 +327,15 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
     return own;
 }
 
-// Main kernel: grid-stride over (anchor, sample) items, 32 consecutive items
-// per warp.  With DEFER, each warp owns a queue segment of P.qcap items.
-template <typename R, bool DEFER>
+// FP64 kernel: grid-stride over (anchor, sample) items, 32 consecutive items
+// per warp.
+template <typename R>
 __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ CollideArgs<R> P)
 {
     const int64_t total = P.n_sel * (int64_t)P.nsamples;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
     const bool warp_anchor = (P.nsamples & 31) == 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    __shared__ int s_count[8];
-    DeferCtx dq;
-    if (DEFER) {
-        if (lane == 0) s_count[warp] = 0;
-        __syncwarp();
-        const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-        dq.s_count = &s_count[warp];
-        dq.seg = P.qitems + gw * P.qcap;
-        dq.cap = (int)P.qcap;
-    }
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
         const int64_t item = base + lane;
         long long own = 0;
@@ -369,7 +347,7 @@ __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ Collide
             Geom<R> G;
             make_geom(P, a, smp, G, P.step);
             const int nt = P.nterms[G.d];
-            for (int ti = 0; ti < nt; ++ti) own += eval_term<R, DEFER>(P, G, a, smp, ti, &dq);
+            for (int ti = 0; ti < nt; ++ti) own += eval_term<R>(P, G, a, smp, ti);
         }
         if (warp_anchor) {
             own = warp_sum_ll(own);
@@ -378,34 +356,8 @@ __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ Collide
             red_add(&P.A[a], own);
         }
     }
-    if (DEFER) {
-        __syncwarp();
-        if (lane == 0) {
-            const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-            const int c = s_count[warp];
-            P.qcount[gw] = c < P.qcap ? c : (int)P.qcap;
-        }
-    }
 }
 
-// Re-evaluates the queued terms in FP64 (one block per warp segment).
-template <typename R>
-__global__ void __launch_bounds__(256) k_fixup(const __grid_constant__ CollideArgs<R> P, const int* qcount,
-                                               const unsigned long long* qitems, int64_t qcap)
-{
-    const int64_t seg = blockIdx.x;
-    const int n = qcount[seg];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long it = qitems[seg * qcap + i];
-        const int64_t a = (int64_t)(it >> 24);
-        const int smp = (int)((it >> 4) & 0xFFFFFu);
-        const int ti = (int)(it & 0xFu);
-        Geom<R> G;
-        make_geom(P, a, smp, G, P.step);
-        const long long own = eval_term<R, false>(P, G, a, smp, ti, nullptr);
-        if (own != 0) red_add(&P.A[a], own);
-    }
-}
 
 
 }  // namespace bz

@@ -643,7 +643,16 @@ __device__ __forceinline__ int bin64(double k, double L, double dp, int n)
     return j >= n ? n - 1 : j;
 }
 
-__device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step)
+// Learned sampler: FP64 truncation constants of the last anchor a thread saw
+// (consecutive queue items mostly come from one anchor).
+struct PropCache {
+    int64_t a = -1;
+    double mu[3], s1, s3, alpha;
+    double Fa[4], cFb[4], D[4];  // components: k1 (centre 0, sigma1), k3x, k3y, k3z
+};
+
+template <bool LEARNED>
+__device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step, PropCache& pc)
 {
     const int64_t nxc = P.nxc, npc = P.npc;
     const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
@@ -665,8 +674,65 @@ __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp,
     const double p0 = (-L + ((double)jx + 0.5) * P.dp64[0]) + P.dp64[0] * (u23(r0.x) - 0.5);
     const double p1 = (-L + ((double)jy + 0.5) * P.dp64[1]) + P.dp64[1] * (u23(r0.y) - 0.5);
     const double p2 = (-L + ((double)jz + 0.5) * P.dp64[2]) + P.dp64[2] * (u23(r0.z) - 0.5);
-    const double k1x = -L + twoL * u23(r0.w), k1y = -L + twoL * u23(r1.x);
-    const double k30 = -L + twoL * u23(r1.y), k31 = -L + twoL * u23(r1.z), k32 = -L + twoL * u23(r1.w);
+    double k1x, k1y, k30, k31, k32, wfac = 1.0;
+    int b1xy, lin3;
+    if (LEARNED) {
+        // the learned sample point in FP64: y = mu + sigma logit(Fa + u (Fb - Fa)) on logistic draws
+        // (F(y) = v there, so the density needs no exponential), y = 2u - 1 on uniform draws
+        if (pc.a != a) {
+            const float* pr = P.prop + a * 8;
+            for (int i = 0; i < 3; ++i) pc.mu[i] = pr[i];
+            pc.s3 = pr[3];
+            pc.s1 = pr[4];
+            pc.alpha = pr[5];
+            for (int c = 0; c < 4; ++c) {
+                const double mu = c == 0 ? 0.0 : pc.mu[c - 1], sg = c == 0 ? pc.s1 : pc.s3;
+                pc.Fa[c] = 1.0 / (1.0 + exp((1.0 + mu) / sg));
+                pc.cFb[c] = 1.0 / (1.0 + exp((1.0 - mu) / sg));
+                pc.D[c] = 1.0 / (1.0 + exp(-(1.0 - mu) / sg)) - pc.Fa[c];
+            }
+            pc.a = a;
+        }
+        const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
+                                       P.key0, P.key1);
+        const double uv[5] = {u23(r0.w), u23(r1.x), u23(r1.y), u23(r1.z), u23(r1.w)};
+        const bool uni = u23(r2.x) < pc.alpha;
+        double y[5], G = 1.0;
+        for (int i = 0; i < 5; ++i) {
+            const int c = i < 2 ? 0 : i - 1;
+            const double mu = i < 2 ? 0.0 : pc.mu[i - 2], sg = i < 2 ? pc.s1 : pc.s3;
+            double F, cF;
+            if (uni) {
+                y[i] = 2.0 * uv[i] - 1.0;
+                const double zz = (y[i] - mu) / sg, e = exp(-fabs(zz)), inv = 1.0 / (1.0 + e);
+                F = zz >= 0.0 ? inv : e * inv;
+                cF = zz >= 0.0 ? e * inv : inv;
+            } else {
+                F = pc.Fa[c] + uv[i] * pc.D[c];
+                cF = pc.cFb[c] + (1.0 - uv[i]) * pc.D[c];
+                y[i] = mu + sg * log(F / cF);
+                y[i] = y[i] < -1.0 ? -1.0 : (y[i] >= 1.0 ? 0.99999994 : y[i]);
+            }
+            G *= F * cF / (sg * pc.D[c]);
+        }
+        wfac = 1.0 / (32.0 * (pc.alpha / 32.0 + (1.0 - pc.alpha) * G));
+        k1x = L * y[0];
+        k1y = L * y[1];
+        k30 = L * y[2];
+        k31 = L * y[3];
+        k32 = L * y[4];
+        b1xy = bin64(k1x, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(k1y, L, P.dp64[1], P.np[1]);
+        lin3 = (bin64(k30, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(k31, L, P.dp64[1], P.np[1])) * P.np[2]
+               + bin64(k32, L, P.dp64[2], P.np[2]);
+    } else {
+        k1x = -L + twoL * u23(r0.w);
+        k1y = -L + twoL * u23(r1.x);
+        k30 = -L + twoL * u23(r1.y);
+        k31 = -L + twoL * u23(r1.z);
+        k32 = -L + twoL * u23(r1.w);
+        b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+        lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+    }
     const double Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
     const double bx = Px - k1x, by = Py - k1y;
     if (!(bx >= -L && bx < L && by >= -L && by < L)) return 0;
@@ -693,9 +759,7 @@ __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp,
     const double s = E * E - ((Px * Px + Py * Py) + Pz * Pz);
     const double k13 = k1x * k30 + k1y * k31, k1p = k1x * p0 + k1y * p1;
     const unsigned slot_stride = (unsigned)(nxc * npc), xoff = (unsigned)(x * npc);
-    const int b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
     const int b2xy = bin64(bx, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(by, L, P.dp64[1], P.np[1]);
-    const int lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
     const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
     long long own = 0;
 #pragma unroll
@@ -738,7 +802,7 @@ __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp,
         // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
         const float den = (float)((double)P.twopi5 * 16.0 * sqH * E3 * Ep);
         const float ct = (float)T.sym * W * M2 / den;
-        const float wq = ct * P.Kown;
+        const float wq = ct * P.Kown * (LEARNED ? (float)wfac : 1.0f);
         if (!(fabsf(wq) < 4611686018427387904.0f)) {
             red_add(&P.flags[1], 1);
             continue;
@@ -755,17 +819,24 @@ __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp,
     return own;
 }
 
-// One warp per queue segment (segments hold about a hundred items).
+// One warp per queue segment (segments hold about a hundred items).  The
+// learned form gives each lane a contiguous run of items, so that its cached
+// per-anchor constants are reused.
+template <bool LEARNED>
 __global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ CollideArgs<float> P, const int* qcount,
                                                    const unsigned long long* qitems, int64_t qcap, int nseg)
 {
     const int64_t seg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (seg >= nseg) return;
     const int n = qcount[seg];
-    for (int i = threadIdx.x & 31; i < n; i += 32) {
+    const int lane = threadIdx.x & 31;
+    const int run = LEARNED ? (n + 31) / 32 : 1;
+    const int i0 = LEARNED ? lane * run : lane, i1 = LEARNED ? min(n, i0 + run) : n, di = LEARNED ? 1 : 32;
+    PropCache pc;
+    for (int i = i0; i < i1; i += di) {
         const unsigned long long it = qitems[seg * qcap + i];
         const int64_t a = (int64_t)(it >> 24);
-        const long long own = fixup_term(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), P.step);
+        const long long own = fixup_term<LEARNED>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), P.step, pc);
         if (own != 0) red_add(&P.A[a], own);
     }
 }
@@ -784,14 +855,18 @@ __global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float
         const unsigned long long it = qitems[seg * qcap + i];
         const CollideArgs<float>& P = boxes[(int)(it >> 48)];
         const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
-        const long long own = fixup_term(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step);
+        PropCache pc;
+        const long long own = fixup_term<false>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step, pc);
         if (own != 0) red_add(&P.A[a], own);
     }
 }
 
 cudaError_t launch_fixup_f32(const CollideArgs<float>& a, int nseg, cudaStream_t s)
 {
-    k_fixup_f32<<<(nseg + 7) / 8, 256, 0, s>>>(a, a.qcount, a.qitems, a.qcap, nseg);
+    if (a.sampler == SAMPLER_LEARNED)
+        k_fixup_f32<true><<<(nseg + 7) / 8, 256, 0, s>>>(a, a.qcount, a.qitems, a.qcap, nseg);
+    else
+        k_fixup_f32<false><<<(nseg + 7) / 8, 256, 0, s>>>(a, a.qcount, a.qitems, a.qcap, nseg);
     return cudaGetLastError();
 }
 
