@@ -187,6 +187,33 @@ def oracle_sample(w, target_s, step=0):
     return anchors * w.nsamples / secs, anchors, O.num_threads(), secs, roots_per_term, stride
 
 
+# ---------------------------------------------------------------------------
+# Weak scaling over ranks (one GPU each): every rank runs its own box (the
+# path shards into independent problems, so there is no data-path
+# collective); only the timing is reduced.
+# ---------------------------------------------------------------------------
+def rank_seed(base_seed, rank):
+    """Seed of a rank's own box: rank 0 keeps the workload's seed."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(t_local, world, device=None):
+    """The slowest rank's time (seconds) of the timed region; the job is as
+    fast as its slowest rank."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, t_max):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank_step * steps * world / t_max
+
+
 def run_reference(args):
     """FP64 CPU oracle as the reference arm, on a bounded sample of anchors."""
     rank = int(os.environ.get("RANK", "0"))
@@ -240,7 +267,7 @@ def run_bz(args):
 
     mk = workloads()[args.workload]
     kw = {"nsamples": args.nsamples} if args.nsamples else {}
-    w = mk(seed=mk().seed + 1000 * rank, **kw) if world > 1 else mk(**kw)
+    w = mk(seed=rank_seed(mk().seed, rank), **kw) if world > 1 else mk(**kw)
     prec = bz.PREC_F32 if args.prec == "f32" else bz.PREC_F64
     h = bz.Handle(nx=w.nx, dx=w.dx, np_=w.np_, L=w.L, seed=w.seed, species_mask=w.species_mask,
                   alpha_s=w.alpha_s)
@@ -278,16 +305,12 @@ def run_bz(args):
     h.profile(False)
     clk = clocks.stop()
     t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    t_max = t_steps
-    if world > 1:
-        t = torch.tensor([t_steps], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(t_steps, world, "cuda")
 
     anchors = w.nslots * w.nxc * w.npc
     samples_step = anchors * w.nsamples
-    value = samples_step * args.steps * world / t_max
-    cell_updates = anchors * args.steps * world / t_max
+    value = whole_job_rate(samples_step, args.steps, world, t_max)
+    cell_updates = whole_job_rate(anchors, args.steps, world, t_max)
 
     # e2e through the public API with host buffers
     n_e2e = min(args.steps, 5)
@@ -427,7 +450,7 @@ def run_batch(args):
     from paper_1912_04457_gb300 import bz
     from paper_1912_04457_gb300 import inputs as I
 
-    boxes, states, dt, nsteps = I.batched_boxes(seed=5 + 1000 * rank)
+    boxes, states, dt, nsteps = I.batched_boxes(seed=rank_seed(5, rank))
     batch = bz.Batch(boxes)
     host = torch.from_numpy(np.concatenate([s.reshape(-1) for s in states])).pin_memory()
     state = host.cuda()
@@ -457,13 +480,9 @@ def run_batch(args):
         ev[k][1].record(stream)
     barrier()
     clk = clocks.stop()
-    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world, "cuda")
     tun = batch.tuning()
-    value = samples_step * args.steps * world / t
+    value = whole_job_rate(samples_step, args.steps, world, t)
     # e2e: host state in, state and moments out, every step
     out_host = torch.empty_like(host).pin_memory()
     barrier()
