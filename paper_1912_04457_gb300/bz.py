@@ -59,6 +59,7 @@ SIGNATURES = {
     "bz_get_flags": (C.c_int, [_P, _P]),
     "bz_clear_flags": (C.c_int, [_P]),
     "bz_set_anchor_subset": (C.c_int, [_P, _I64, _I64]),
+    "bz_get_state_flags": (C.c_int, [_P, _P]),
     "bz_set_uniform_bits": (C.c_int, [_P, _I32]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
@@ -200,6 +201,12 @@ class Handle:
     def flags(self):
         out = np.zeros(4, dtype=np.int64)
         self._check(self.lib.bz_get_flags(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def state_flags(self):
+        """[cells with f < 0, fermion cells with f > 1] counted by the moments evaluations."""
+        out = np.zeros(2, dtype=np.int64)
+        self._check(self.lib.bz_get_state_flags(self.h, out.ctypes.data_as(C.c_void_p)))
         return out
 
     def clear_flags(self):

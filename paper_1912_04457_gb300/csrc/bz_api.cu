@@ -38,6 +38,7 @@ struct bz_handle_s {
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
+    long long* d_sflags = nullptr; // state warnings (2): f < 0 cells, fermion f > 1 cells
     int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
     bool audit_on = false;
     long long* d_state2 = nullptr; // second state buffer for bz_step
@@ -154,6 +155,8 @@ static void free_scratch(bz_handle h)
     h->d_inv_e = nullptr;
     cudaFree(h->d_audit);
     h->d_audit = nullptr;
+    cudaFree(h->d_sflags);
+    h->d_sflags = nullptr;
     cudaFree(h->d_state2);
     cudaFree(h->d_qcount);
     cudaFree(h->d_qitems);
@@ -244,6 +247,7 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
         cudaMalloc(&h->d_m2[1], sizeof(double) * 4 * h->nxc) != cudaSuccess ||
         cudaMalloc(&h->d_acc, sizeof(long long) * 4 * h->nxc) != cudaSuccess ||
         cudaMalloc(&h->d_flags, sizeof(long long) * 4) != cudaSuccess ||
+        cudaMalloc(&h->d_sflags, sizeof(long long) * 2) != cudaSuccess ||
         cudaMalloc(&h->d_jtab, sizeof(int) * h->npc) != cudaSuccess) {
         free_scratch(h);
         delete h;
@@ -261,6 +265,7 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
         return rc;
     }
     cudaMemset(h->d_flags, 0, sizeof(long long) * 4);
+    cudaMemset(h->d_sflags, 0, sizeof(long long) * 2);
     cudaMemset(h->d_m2[0], 0, sizeof(double) * 4 * h->nxc);
     cudaMemset(h->d_m2[1], 0, sizeof(double) * 4 * h->nxc);
     if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -391,6 +396,14 @@ extern "C" int bz_reset_masses(bz_handle h)
     return BZ_OK;
 }
 
+extern "C" int bz_get_state_flags(bz_handle h, int64_t* flags_host)
+{
+    if (!h || !flags_host) return BZ_EINVAL;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(flags_host, h->d_sflags, sizeof(long long) * 2, cudaMemcpyDeviceToHost));
+    return BZ_OK;
+}
+
 extern "C" int bz_get_flags(bz_handle h, int64_t* flags_host)
 {
     if (!h || !flags_host) return BZ_EINVAL;
@@ -403,6 +416,7 @@ extern "C" int bz_clear_flags(bz_handle h)
 {
     if (!h) return BZ_EINVAL;
     CK(h, cudaMemset(h->d_flags, 0, sizeof(long long) * 4));
+    CK(h, cudaMemset(h->d_sflags, 0, sizeof(long long) * 2));
     return BZ_OK;
 }
 
@@ -744,6 +758,11 @@ static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, doub
     double twopi = 2.0 * PI;
     a.pref = dp[0] * dp[1] * dp[2] / (twopi * twopi * twopi) * TWO_POW_M40;
     a.jtab = h->d_jtab;  // null for the boxes of a batch
+    a.sflags = h->d_sflags;
+    for (int sl = 0; sl < NSPEC; ++sl) {
+        const int sp = sl < h->nslots ? h->slot_species[sl] : 0;
+        a.pauli[sl] = is_quark(sp) ? (long long)(kDeg[sp] * TWO_POW_40) : 0x7fffffffffffffffLL;
+    }
     return BZ_OK;
 }
 

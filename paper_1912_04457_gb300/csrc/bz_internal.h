@@ -158,6 +158,8 @@ struct MomentArgs {
     double pref, half_dp[3];
     float pf[3][MAX_NP];
     const int* jtab;        // [npc] jx | jy << 8 | jz << 16, or null (decoded by division)
+    long long* sflags;      // [2] cells with n < 0, fermion cells with f > 1 (added), or null
+    long long pauli[NSPEC]; // per slot: N_s 2^40 (f = 1) for (anti)quarks, LLONG_MAX for gluons
 };
 
 // Per-slot scales of the f conversion: FP64 degeneracy, and the FP32

@@ -453,6 +453,8 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
     const int npc = (int)P.npc, np1 = P.np[1], np2 = P.np[2];
     __int128 v[5] = {0, 0, 0, 0, 0};
+    const long long pauli = P.pauli[sl];
+    int neg = 0, over = 0;  // state warnings: f < 0 anywhere, f > 1 for fermions (Pauli)
     for (int j = threadIdx.x; j < npc; j += blockDim.x) {
         int jv[3];
         if (P.jtab) {
@@ -470,6 +472,8 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
         const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
         const long long Efx = rint_ll(sqrtf(ppf + m) * 16777216.0f);
         const long long n = __ldg(&st[j]);
+        neg += n < 0;
+        over += n > pauli;
         v[0] += n;
         v[1] += (__int128)Efx * n;
 #pragma unroll
@@ -477,6 +481,12 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     }
     __shared__ __int128 red[5][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (P.sflags) {
+        neg = warp_sum(neg);
+        over = warp_sum(over);
+        if (lane == 0 && neg) red_add_ll(&P.sflags[0], neg);
+        if (lane == 0 && over) red_add_ll(&P.sflags[1], over);
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         v[i] = warp_sum_i128(v[i]);

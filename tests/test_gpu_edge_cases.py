@@ -58,6 +58,27 @@ def test_maximum_cells_along_one_axis():
     assert np.array_equal(A.cpu().numpy(), ref)
 
 
+def test_state_warnings_count_negative_and_pauli_cells():
+    """bz_moments counts cells with f < 0 and (anti)quark cells with f > 1."""
+    import torch
+    from paper_1912_04457_gb300 import bz
+    np_, mask = (6, 6, 6), 0x13          # g, u, ubar
+    h, _ = _pair(np_, mask)
+    f = I.random_f(np_, 3, 1, 12, 0.0, 0.9)
+    f[0, 0, :5] = -0.01                  # 5 negative gluon cells
+    f[1, 0, 10:17] = 1.2                 # 7 quark cells above 1
+    f[2, 0, 3] = -0.5                    # 1 negative antiquark cell
+    f[2, 0, 4] = 1.0 + 1e-9              # 1 antiquark cell just above 1
+    f[0, 0, 20] = 3.0                    # gluons may exceed 1
+    st = torch.from_numpy(I.encode(f, mask).reshape(-1)).cuda()
+    mom = torch.empty(3 * 5, dtype=torch.float64, device="cuda")
+    h.clear_flags()
+    h.moments(st, mom)
+    assert list(h.state_flags()) == [6, 8]
+    h.clear_flags()
+    assert list(h.state_flags()) == [0, 0]
+
+
 def test_limits_are_refused():
     import torch
     from paper_1912_04457_gb300 import bz
