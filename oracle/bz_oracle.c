@@ -33,6 +33,9 @@
  *   - the integration box is (k1x,k1y,k3) in [-L,L)^5; a root whose k1z or
  *     k2 leaves the box is rejected;
  *   - the drift is first-order upwind in flux form, periodic in x;
+ *   - the optional force term is upwind in p with dE/dx = (dm^2/dx)/(2E),
+ *     dm^2/dx a central difference, and no flux through the momentum-box
+ *     faces;
  *   - time is in fm/c, momenta in GeV, so dt enters as dt/hbar_c;
  *   - the mass integrals are summed exactly in 2^-30 fixed point, so their
  *     value does not depend on summation order.
@@ -96,6 +99,7 @@ typedef struct {
     int32_t analytic;       /* 1: f at each leg from the equilibrium formula (Eqs. fg, fq) */
     double T;               /* temperature for analytic f, GeV                 */
     double mu[NSPEC];       /* chemical potentials for analytic f, GeV         */
+    int32_t force;          /* 1: the drift includes the force term -div_p[(grad_x E) f] */
 } bzo_config;
 
 static int is_quark(int s) { return s != 0; }
@@ -733,12 +737,35 @@ static int64_t xlin(const bzo_config* c, int ix, int iy, int iz)
     return ((int64_t)ix * c->nx[1] + iy) * c->nx[2] + iz;
 }
 
+/* Force term of Eq. (left handside), -div_p[(grad_x E) f] (Eq. (boltzmann  */
+/* equation general form): dp/dt = -grad_x E).  Along p_i a cell moves     */
+/* with -dE/dx_i = -(dm^2/dx_i) / (2E); dm^2/dx_i is the central           */
+/* difference (m^2(x + e_i) - m^2(x - e_i)) / (2 dx) of the species' mass,  */
+/* so with g_i = (m^2(x + e_i) - m^2(x - e_i)) / (4 dx) (FP64, then FP32)   */
+/* the Courant number is ((-g_i) (1/E)) dt/dp_i in IEEE single precision,   */
+/* held in 2^-30 fixed point like the x fluxes.  Upwind in p (every p cell  */
+/* of an x cell moves the same way), and no flux crosses a face of the      */
+/* momentum box, so the sum of the state stays exact.                       */
+static float force_g(const bzo_config* c, const double* m2, int64_t xl, int64_t xh, int s, double inv4dx)
+{
+    if (c->mass_mode == 1) return 0.0f;
+    return (float)((m2[xh * 4 + mass_slot(s)] - m2[xl * 4 + mass_slot(s)]) * inv4dx);
+}
+
+static int64_t force_courant(float g, float inv, float dtdpf)
+{
+    float cf = ((-g) * inv) * dtdpf;
+    return llrintf(cf * 1073741824.0f);
+}
+
 int bzo_drift(const bzo_config* c, const int64_t* in, const double* m2, double dt, int64_t* out)
 {
     int ns = nslots(c);
     int64_t nxc = n_xcells(c), npc = n_pcells(c);
     float dtdxf = (float)(dt / c->dx);
     double dp[3] = {2.0 * c->L / c->np[0], 2.0 * c->L / c->np[1], 2.0 * c->L / c->np[2]};
+    float dtdpf[3] = {(float)(dt / dp[0]), (float)(dt / dp[1]), (float)(dt / dp[2])};
+    double inv4dx = 1.0 / (4.0 * c->dx);
     int species[NSPEC];
     for (int s = 0; s < NSPEC; ++s)
         if (slot_of(c, s) >= 0) species[slot_of(c, s)] = s;
@@ -775,6 +802,33 @@ int bzo_drift(const bzo_config* c, const int64_t* in, const double* m2, double d
                         fminus = flux_fx(nc, courant_fx(c, m2, x, s, pf[d], ppf, dtdxf));
                     }
                     acc += fplus - fminus;
+                }
+                if (c->force) {
+                    float m = c->mass_mode == 1 ? 0.0f : (float)m2[x * 4 + mass_slot(s)];
+                    float inv = 1.0f / sqrtf(ppf + m);
+                    for (int i = 0; i < 3; ++i) {
+                        if (c->nx[i] == 1) continue;
+                        int lo[3] = {xi[0], xi[1], xi[2]}, hi[3] = {xi[0], xi[1], xi[2]};
+                        lo[i] = (xi[i] - 1 + c->nx[i]) % c->nx[i];
+                        hi[i] = (xi[i] + 1) % c->nx[i];
+                        float g = force_g(c, m2, xlin(c, lo[0], lo[1], lo[2]), xlin(c, hi[0], hi[1], hi[2]), s,
+                                          inv4dx);
+                        int up = (-g) > 0.0f;  /* this x cell's p cells move towards larger p_i */
+                        int64_t own = 0, behind = 0;
+                        int jo = jv[i] + (up ? 1 : -1), jb = jv[i] + (up ? -1 : 1);
+                        if (jo >= 0 && jo < c->np[i]) own = flux_fx(nc, force_courant(g, inv, dtdpf[i]));
+                        if (jb >= 0 && jb < c->np[i]) {
+                            int jw[3] = {jv[0], jv[1], jv[2]};
+                            float pw[3] = {pf[0], pf[1], pf[2]};
+                            jw[i] = jb;
+                            pw[i] = (float)(-c->L + ((double)jb + 0.5) * dp[i]);
+                            float ppw = (pw[0] * pw[0] + pw[1] * pw[1]) + pw[2] * pw[2];
+                            float invb = 1.0f / sqrtf(ppw + m);
+                            int64_t jbl = ((int64_t)jw[0] * c->np[1] + jw[1]) * c->np[2] + jw[2];
+                            behind = flux_fx(in[((int64_t)sl * nxc + x) * npc + jbl], force_courant(g, invb, dtdpf[i]));
+                        }
+                        acc += up ? own - behind : behind - own;
+                    }
                 }
                 out[((int64_t)sl * nxc + x) * npc + j] = nc - acc;
             }

@@ -24,6 +24,7 @@ class Config(C.Structure):
         ("species_mask", C.c_uint32), ("alpha_s", C.c_double),
         ("mass_mode", C.c_int32), ("analytic", C.c_int32),
         ("T", C.c_double), ("mu", C.c_double * NSPEC),
+        ("force", C.c_int32),
     ]
 
 
@@ -73,7 +74,7 @@ def _ptr(a):
 
 
 def make_config(nx=(1, 1, 1), dx=1.0, np_=(20, 20, 20), L=2.0, seed=1, box=0,
-                species_mask=1, alpha_s=0.3, mass_mode=0, analytic=False, T=0.5, mu=None):
+                species_mask=1, alpha_s=0.3, mass_mode=0, analytic=False, T=0.5, mu=None, force=False):
     c = Config()
     c.nx[:] = list(nx)
     c.dx = dx
@@ -87,6 +88,7 @@ def make_config(nx=(1, 1, 1), dx=1.0, np_=(20, 20, 20), L=2.0, seed=1, box=0,
     c.analytic = 1 if analytic else 0
     c.T = T
     c.mu[:] = list(mu) if mu is not None else [0.0] * NSPEC
+    c.force = 1 if force else 0
     return c
 
 
