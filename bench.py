@@ -329,11 +329,18 @@ def run_bz(args):
     t_e2e = e0.elapsed_time(e1) / 1e3
     e2e_value = samples_step * n_e2e * world / t_e2e
 
+    # streaming kernels of inhomogeneous grids against the HBM roofline, and the
+    # cost of the optional force term (outside the timed region)
+    transport = None
+    if w.nxc > 1 and rank == 0:
+        transport = transport_rooflines(h, w, state, mom, prof, args.steps, stream, barrier)
+
     result = None
     if rank == 0:
         coll_ms, coll_n = prof["collide"]
-        launches = (2 * prof["masses"][1] + prof["drift"][1] + prof["collide"][1] + prof["fixup"][1]
-                    + prof["moments"][1] + prof["convert"][1])
+        drift_kernels = 2 if w.nxc > 1 else 1   # k_inv_energy + the drift kernel on inhomogeneous grids
+        launches = (2 * prof["masses"][1] + drift_kernels * prof["drift"][1] + prof["collide"][1]
+                    + prof["fixup"][1] + prof["moments"][1] + prof["convert"][1])
         # algorithmic work of one collision launch
         cpu_rate, cpu_anchors, cores, cpu_secs, roots_per_term, cpu_stride = (None,) * 6
         if not args.no_cpu_baseline and world == 1:
@@ -414,6 +421,7 @@ def run_bz(args):
             "gpu_launches": launches,
             "clocks": clk,
             "fp64_gpu_path": fp64,
+            "transport": transport,
             "physics": {
                 "number_conserved_exactly": number_conserved,
                 "species": {I.SPECIES[sp]: {"number_density_GeV3": float(mom_last[:, k, 0].mean()),
@@ -430,6 +438,48 @@ def run_bz(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def transport_rooflines(h, w, state, mom, prof, steps, stream, barrier):
+    """Drift (k_inv_energy + drift kernel; algorithmic bytes 8 B read + 8 B
+    write + 4 B f per cell) and moments (8 B read per cell) of the timed steps
+    against the HBM peak, and the drift with the force term switched on,
+    timed over separate calls."""
+    import torch
+    ncell = w.nslots * w.nxc * w.npc
+    peak, basis = measured_hbm_gbs()
+    out = {"hbm_peak_GBs": peak, "peak_basis": basis}
+    for name, nbytes in (("drift", 20 * ncell), ("moments", 8 * ncell)):
+        ms = prof[name][0] / max(prof[name][1], 1)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "achieved_GBs": gbs, "frac": gbs / peak}
+    nxt = torch.empty_like(state)
+    reps = 10
+    for force in (False, True):
+        h.set_force_term(force)
+        h.drift(state, nxt, w.dt)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            h.drift(state, nxt, w.dt)
+        b.record(stream)
+        barrier()
+        out["drift_force_on_ms" if force else "drift_force_off_ms"] = a.elapsed_time(b) / reps
+    h.set_force_term(False)
+    out["force_note"] = ("bz_drift over the same state with the force term -div_p[(grad_x E) f] off and on "
+                         "(not part of the timed step)")
+    del nxt
+    return out
 
 
 def run_batch(args):

@@ -179,6 +179,18 @@ int bz_clear_flags(bz_handle h);
  * Errors: BZ_EINVAL for other values. */
 int bz_set_uniform_bits(bz_handle h, int32_t bits);
 
+/* Force term -div_p[(grad_x E) f] of Eq. (left handside) (dp/dt = -grad_x E,
+ * Eq. (boltzmann equation general form)), added to the drift of bz_drift and
+ * bz_step when enable = 1 (default 0).  Along p_i the p cells of an x cell
+ * move with -g_i / E, g_i = (m^2(x + e_i) - m^2(x - e_i)) / (4 dx) (the
+ * central difference of the species' m^2, halved: dE/dx = (dm^2/dx)/(2E));
+ * upwind in p with the Courant number ((-g_i) (1/E)) dt/dp_i held in 2^-30
+ * fixed point like the x fluxes; no flux through the faces of the momentum
+ * box, so the sum of the state stays exact.  It has no effect with one x
+ * cell or the massless dispersion (no gradient).  Errors: BZ_EINVAL for
+ * enable other than 0 or 1. */
+int bz_set_force_term(bz_handle h, int32_t enable);
+
 /* Restricts the anchors to those with linear index a = (slot nx + x) np + p
  * satisfying a % stride == offset (stride 1 = all).  Used to check full
  * size workloads against the CPU oracle on a sample of anchors. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "bz_set_anchor_subset": (C.c_int, [_P, _I64, _I64]),
     "bz_get_state_flags": (C.c_int, [_P, _P]),
     "bz_set_uniform_bits": (C.c_int, [_P, _I32]),
+    "bz_set_force_term": (C.c_int, [_P, _I32]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
     "bz_profile_read": (C.c_int, [_P, _P, _P, _I32]),
@@ -177,6 +178,9 @@ class Handle:
 
     def set_uniform_bits(self, bits):
         self._check(self.lib.bz_set_uniform_bits(self.h, bits))
+
+    def set_force_term(self, enable=True):
+        self._check(self.lib.bz_set_force_term(self.h, 1 if enable else 0))
 
     def set_anchor_subset(self, stride=1, offset=0):
         self._check(self.lib.bz_set_anchor_subset(self.h, stride, offset))

@@ -37,6 +37,8 @@ struct bz_handle_s {
     void* d_freal = nullptr;       // f of the state, double-sized
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
+    float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
+    bool force = false;            // the drift includes the force term -div_p[(grad_x E) f]
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
     long long* d_sflags = nullptr; // state warnings (2): f < 0 cells, fermion f > 1 cells
     int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
@@ -153,6 +155,8 @@ static void free_scratch(bz_handle h)
     h->d_jtab = nullptr;
     cudaFree(h->d_inv_e);
     h->d_inv_e = nullptr;
+    cudaFree(h->d_gforce);
+    h->d_gforce = nullptr;
     cudaFree(h->d_audit);
     h->d_audit = nullptr;
     cudaFree(h->d_sflags);
@@ -192,6 +196,8 @@ static int alloc_scratch(bz_handle h)
         return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for f", (long long)(8 * h->ncell));
     if (h->nxc > 1 && cudaMalloc(&h->d_inv_e, sizeof(float) * h->ncell) != cudaSuccess)
         return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for the drift", (long long)(4 * h->ncell));
+    if (h->nxc > 1 && !h->d_gforce && cudaMalloc(&h->d_gforce, sizeof(float) * 12 * h->nxc) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the force-term scratch");
     return BZ_OK;
 }
 
@@ -348,6 +354,14 @@ extern "C" int bz_set_uniform_bits(bz_handle h, int32_t bits)
     if (!h) return BZ_EINVAL;
     if (bits != 32 && bits != 23) return fail(h, BZ_EINVAL, "uniform bits must be 32 or 23");
     h->f64_ubits = bits;
+    return BZ_OK;
+}
+
+extern "C" int bz_set_force_term(bz_handle h, int32_t enable)
+{
+    if (!h) return BZ_EINVAL;
+    if (enable != 0 && enable != 1) return fail(h, BZ_EINVAL, "enable must be 0 or 1");
+    h->force = enable == 1;
     return BZ_OK;
 }
 
@@ -735,6 +749,11 @@ static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long*
     }
     a.jtab = h->d_jtab;
     a.inv_e = h->d_inv_e;
+    // the force needs a mass gradient: none with one x cell or the massless dispersion
+    a.force = h->force && h->nxc > 1 && h->mass_mode != BZ_MASS_MASSLESS;
+    a.gforce = h->d_gforce;
+    a.inv4dx = 1.0 / (4.0 * h->g.dx);
+    for (int d = 0; d < 3; ++d) a.Kp[d] = (float)(dt / dp_of(h, d)) * 1073741824.0f;
     return BZ_OK;
 }
 

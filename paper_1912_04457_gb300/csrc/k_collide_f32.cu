@@ -17,6 +17,7 @@
 // mantissa bits; weights are rounded to int64 with integer operations only,
 // so the FP64 pipe is never used.
 #include "collide.cuh"
+#include "ff.cuh"
 #include "intconv.cuh"
 
 namespace bz {
@@ -819,6 +820,143 @@ __device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp,
     return own;
 }
 
+// The same re-evaluation for the uniform sampler in float-float arithmetic
+// (about 48 bits, FP32 instructions only) instead of FP64: the sample point,
+// energies, D, kappa, H, the roots, validity, box and bin decisions, E1, s, t
+// and u.  Returns the anchor's +q.  Not inlined: the single-box and the batch
+// fixup kernels call one compiled body, so a queued term gives the same bits
+// in both.
+__device__ __forceinline__ int bin_ff(ff k, ff L, ff dp, int n)
+{
+    int j = ff_floor(ff_div(ff_add(k, L), dp));
+    j = j < 0 ? 0 : j;
+    return j >= n ? n - 1 : j;
+}
+
+__device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step)
+{
+    const int64_t nxc = P.nxc, npc = P.npc;
+    const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
+    const uint32_t rem = (uint32_t)a - sl_u * (uint32_t)(nxc * npc);
+    const uint32_t x_u = udiv(rem, P.dv_npc);
+    const int sl = (int)sl_u;
+    const int64_t x = x_u;
+    const int j = (int)(rem - x_u * (uint32_t)npc);
+    const int d = P.slot_species[sl];
+    const uint32_t jx_u = udiv((uint32_t)j, P.dv_yz);
+    const uint32_t ryz = (uint32_t)j - jx_u * (uint32_t)(P.np[1] * P.np[2]);
+    const uint32_t jy_u = udiv(ryz, P.dv_z);
+    const int jx = (int)jx_u, jy = (int)jy_u, jz = (int)(ryz - jy_u * (uint32_t)P.np[2]);
+    const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
+    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+    // 23-bit uniforms (x + 1/2) 2^-23 are exact in FP32, and so is u - 1/2
+    auto u23 = [](uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); };
+    const ff L = ff_from_double(P.L64), nL = ff_neg(L), twoL = ff_from_double(2.0 * P.L64);
+    const ff dp[3] = {ff_from_double(P.dp64[0]), ff_from_double(P.dp64[1]), ff_from_double(P.dp64[2])};
+    const int jv[3] = {jx, jy, jz};
+    const float uj[3] = {u23(r0.x), u23(r0.y), u23(r0.z)};
+    ff p[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        p[i] = ff_add(ff_add(nL, ff_mul_f(dp[i], (float)jv[i] + 0.5f)), ff_mul_f(dp[i], uj[i] - 0.5f));
+    const ff k1x = ff_add(nL, ff_mul_f(twoL, u23(r0.w)));
+    const ff k1y = ff_add(nL, ff_mul_f(twoL, u23(r1.x)));
+    const ff k30 = ff_add(nL, ff_mul_f(twoL, u23(r1.y)));
+    const ff k31 = ff_add(nL, ff_mul_f(twoL, u23(r1.z)));
+    const ff k32 = ff_add(nL, ff_mul_f(twoL, u23(r1.w)));
+    const int b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+    const int lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+    const ff Px = ff_add(p[0], k30), Py = ff_add(p[1], k31), Pz = ff_add(p[2], k32);
+    const ff bx = ff_sub(Px, k1x), by = ff_sub(Py, k1y);
+    if (!(ff_ge(bx, nL) && ff_lt(bx, L) && ff_ge(by, nL) && ff_lt(by, L))) return 0;
+    const TermDev& T = P.terms[d][ti];
+    auto mass = [&](int i) { return P.mass_mode == 1 ? ff{0.0f, 0.0f} : ff_from_double(P.m2[x * 4 + i]); };
+    const ff mg2 = ff_from_double(P.m2[x * 4]);
+    const ff ma2 = mass(T.mslot[0]), mb2 = mass(T.mslot[1]), mc2 = mass(T.mslot[2]), md2 = mass(T.mslot[3]);
+    const ff Ep = ff_sqrt(ff_add(ff_add(ff_add(ff_sqr(p[0]), ff_sqr(p[1])), ff_sqr(p[2])), md2));
+    const ff E3 = ff_sqrt(ff_add(ff_add(ff_add(ff_sqr(k30), ff_sqr(k31)), ff_sqr(k32)), mc2));
+    const ff E = ff_add(Ep, E3), EE = ff_sqr(E);
+    const ff a2 = ff_add(ff_add(ff_sqr(k1x), ff_sqr(k1y)), ma2);
+    const ff b2 = ff_add(ff_add(ff_sqr(bx), ff_sqr(by)), mb2);
+    const ff Pz2 = ff_sqr(Pz);
+    const ff D = ff_sub(EE, Pz2);
+    ff kap = ff_sub(ff_sub(ff_add(EE, a2), b2), Pz2);
+    kap = {kap.hi * 0.5f, kap.lo * 0.5f};
+    const ff H = ff_sub(ff_sqr(kap), ff_mul(a2, D));
+    if (!ff_gt0(D) || !ff_gt0(H)) return 0;
+    const ff sqH = ff_sqrt(H);
+    const ff kp = ff_mul(kap, Pz), sq = ff_mul(E, sqH);
+    const ff Q = ff_ge0(kp) ? ff_add(kp, sq) : ff_sub(kp, sq);
+    if (Q.hi == 0.0f) return 0;
+    const ff zr[2] = {ff_div(Q, D), ff_div(ff_sub(ff_mul(EE, a2), ff_sqr(kap)), Q)};
+    const float s = ff_to_float(ff_sub(EE, ff_add(ff_add(ff_sqr(Px), ff_sqr(Py)), Pz2)));
+    const ff k13 = ff_add(ff_mul(k1x, k30), ff_mul(k1y, k31)), k1p = ff_add(ff_mul(k1x, p[0]), ff_mul(k1y, p[1]));
+    const ff mac = ff_add(ma2, mc2), mad = ff_add(ma2, md2);
+    const unsigned slot_stride = (unsigned)(nxc * npc), xoff = (unsigned)(x * npc);
+    const int b2xy = bin_ff(bx, L, dp[0], P.np[0]) * P.np[1] + bin_ff(by, L, dp[1], P.np[1]);
+    const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
+    const float den0 = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(P.twopi5, 16.0f), ff_to_float(sqH)), ff_to_float(E3)),
+                                 ff_to_float(Ep));
+    long long own = 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const ff z = zr[r], dz = ff_sub(Pz, z);
+        const ff e2E = ff_add(kap, ff_mul(Pz, z));  // E2 E at a root: valid iff 0 < E2 < E
+        if (!(ff_gt0(e2E) && ff_lt(e2E, EE))) continue;
+        if (!(ff_ge(z, nL) && ff_lt(z, L) && ff_ge(dz, nL) && ff_lt(dz, L))) continue;
+        const ff E1 = ff_sqrt(ff_add(a2, ff_sqr(z)));
+        const ff tt = ff_sub(mac, ff_mul_f(ff_sub(ff_mul(E1, E3), ff_add(k13, ff_mul(z, k32))), 2.0f));
+        const ff uf = ff_sub(mad, ff_mul_f(ff_sub(ff_mul(E1, Ep), ff_add(k1p, ff_mul(z, p[2]))), 2.0f));
+        if (!(s > 0.0f) || ff_ge0(ff_sub(tt, mg2)) || ff_ge0(ff_sub(uf, mg2))) {
+            red_add(&P.flags[0], 1);
+            continue;
+        }
+        const float M2 = msq<float>(T.cls, P, s, ff_to_float(tt), ff_to_float(uf), ff_to_float(mg2));
+        const int lin1 = b1xy * P.np[2] + bin_ff(z, L, dp[2], P.np[2]);
+        const int lin2 = b2xy * P.np[2] + bin_ff(dz, L, dp[2], P.np[2]);
+        const unsigned i1 = (unsigned)T.slot[0] * slot_stride + xoff + lin1;
+        const unsigned i2 = (unsigned)T.slot[1] * slot_stride + xoff + lin2;
+        const unsigned i3 = (unsigned)T.slot[2] * slot_stride + xoff + lin3;
+        float f1, f2, f3, fpp;
+        if (P.analytic) {
+            f1 = f_equilibrium(P, P.slot_species[T.slot[0]], ff_to_float(E1));
+            f2 = f_equilibrium(P, P.slot_species[T.slot[1]], ff_to_float(ff_sub(E, E1)));
+            f3 = f_equilibrium(P, P.slot_species[T.slot[2]], ff_to_float(E3));
+            fpp = f_equilibrium(P, d, ff_to_float(Ep));
+        } else {
+            const float* F = static_cast<const float*>(P.f);
+            f1 = __ldg(F + i1);
+            f2 = __ldg(F + i2);
+            f3 = __ldg(F + i3);
+            fpp = fp;
+        }
+        const float F1 = T.quark[0] ? 1.0f - f1 : 1.0f + f1;
+        const float F2 = T.quark[1] ? 1.0f - f2 : 1.0f + f2;
+        const float F3 = T.quark[2] ? 1.0f - f3 : 1.0f + f3;
+        const float Fp = T.quark[3] ? 1.0f - fpp : 1.0f + fpp;
+        // W and c~ rounded as written (no contraction), like the float-float part
+        const float W = __fsub_rn(__fmul_rn(__fmul_rn(__fmul_rn(f1, f2), F3), Fp),
+                                  __fmul_rn(__fmul_rn(__fmul_rn(F1, F2), f3), fpp));
+        // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
+        const float ct = __fdiv_rn(__fmul_rn(__fmul_rn((float)T.sym, W), M2), den0);
+        const float wq = __fmul_rn(ct, P.Kown);
+        if (!(fabsf(wq) < 4611686018427387904.0f)) {
+            red_add(&P.flags[1], 1);
+            continue;
+        }
+        const long long q = rint_ll(wq);
+        if (q == 0) continue;
+        own += q;
+        if (P.sampler != 1) {
+            red_add(&P.A[i3], q);
+            red_add(&P.A[i1], -q);
+            red_add(&P.A[i2], -q);
+        }
+    }
+    return own;
+}
+
 // One warp per queue segment (segments hold about a hundred items).  The
 // learned form gives each lane a contiguous run of items, so that its cached
 // per-anchor constants are reused.
@@ -836,7 +974,12 @@ __global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ Colli
     for (int i = i0; i < i1; i += di) {
         const unsigned long long it = qitems[seg * qcap + i];
         const int64_t a = (int64_t)(it >> 24);
-        const long long own = fixup_term<LEARNED>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), P.step, pc);
+        const int smp = (int)((it >> 4) & 0xFFFFFu), ti = (int)(it & 0xFu);
+        long long own;
+        if constexpr (LEARNED)
+            own = fixup_term<true>(P, a, smp, ti, P.step, pc);
+        else
+            own = fixup_term_ff(P, a, smp, ti, P.step);
         if (own != 0) red_add(&P.A[a], own);
     }
 }
@@ -855,8 +998,7 @@ __global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float
         const unsigned long long it = qitems[seg * qcap + i];
         const CollideArgs<float>& P = boxes[(int)(it >> 48)];
         const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
-        PropCache pc;
-        const long long own = fixup_term<false>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step, pc);
+        const long long own = fixup_term_ff(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step);
         if (own != 0) red_add(&P.A[a], own);
     }
 }

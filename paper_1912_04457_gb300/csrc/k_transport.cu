@@ -46,18 +46,26 @@ constexpr int MASS_CHUNK = 2048;
 // Fixed-point partial sums of one (x cell, chunk of MASS_CHUNK bins) block.
 __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64_t c0, bool use_prev)
 {
+    __shared__ double s_p[3][MAX_NP];  // cell-centre momenta, -L + (j + 1/2) dp
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_p[d][i] = -P.L + ((double)i + 0.5) * P.dp[d];
+    __syncthreads();
     double m2p[4] = {0.0, 0.0, 0.0, 0.0};
     if (use_prev && P.m2_prev)
         for (int i = 0; i < 4; ++i) m2p[i] = P.m2_prev[x * 4 + i];
+    // A species pair with no state (no active slot) contributes the product
+    // 0 r = +0 to every sum as long as r is finite, i.e. E^2 = p^2 + m^2 > 0:
+    // its 1/(2E) is then not evaluated (set to 0, the same +0 product).
+    const bool skip_g = P.slot_of[0] < 0 && m2p[0] >= 0.0;
+    bool skip_q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) skip_q[i] = P.slot_of[1 + i] < 0 && P.slot_of[4 + i] < 0 && m2p[1 + i] >= 0.0;
+    const int np1 = P.np[1], np2 = P.np[2], np12 = np1 * np2;
     long long sg = 0, sq[3] = {0, 0, 0};
     bool ovf = false;
     for (int64_t j = c0 + threadIdx.x; j < c0 + MASS_CHUNK && j < P.npc; j += blockDim.x) {
-        const int jx = (int)(j / ((int64_t)P.np[1] * P.np[2]));
-        const int jy = (int)((j / P.np[2]) % P.np[1]);
-        const int jz = (int)(j % P.np[2]);
-        const double px = -P.L + ((double)jx + 0.5) * P.dp[0];
-        const double py = -P.L + ((double)jy + 0.5) * P.dp[1];
-        const double pz = -P.L + ((double)jz + 0.5) * P.dp[2];
+        const int jj = (int)j;  // npc < 2^31
+        const double px = s_p[0][jj / np12], py = s_p[1][(jj / np2) % np1], pz = s_p[2][jj % np2];
         const double pp = (px * px + py * py) + pz * pz;
         // N_s f_s = n_s 2^-40 and r_a = 1/(2 E_a): 3x the Eq. (mg) bin integrand
         // is 2^-40 (9 n_g r_g + 4 sum_i q_i r_qi), 24x the Eq. (mq) one is
@@ -68,13 +76,13 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
             const int sl = P.slot_of[s];
             nsp[s] = sl < 0 ? 0 : P.state[((int64_t)sl * P.nxc + x) * P.npc + j];
         }
-        const double ng = (double)nsp[0];
-        const double rg = 0.5 / sqrt(pp + m2p[0]);
+        const double ng = skip_g ? 0.0 : (double)nsp[0];
+        const double rg = skip_g ? 0.0 : 0.5 / sqrt(pp + m2p[0]);
         double q[3], rq[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            q[i] = (double)(nsp[1 + i] + nsp[4 + i]);
-            rq[i] = 0.5 / sqrt(pp + m2p[1 + i]);
+            q[i] = skip_q[i] ? 0.0 : (double)(nsp[1 + i] + nsp[4 + i]);
+            rq[i] = skip_q[i] ? 0.0 : 0.5 / sqrt(pp + m2p[1 + i]);
         }
         const double g3 = 9.0 * ng * rg + 4.0 * ((q[0] * rq[0] + q[1] * rq[1]) + q[2] * rq[2]);
         const long long qg = __double2ll_rn(g3 * MASS_FX);
@@ -211,7 +219,10 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_inv_energy(const __grid_const
     const int64_t row = blockIdx.x;
     const int sl = (int)(row / P.nxc);
     const int64_t x = row - (int64_t)sl * P.nxc;
-    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
+    __shared__ float s_m;  // the row's mass, converted once
+    if (threadIdx.x == 0) s_m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
+    __syncthreads();
+    const float m = s_m;
     const int npc = (int)P.npc;
     float* out = P.inv_e + row * P.npc;
     for (int j = blockIdx.y * DRIFT_TILE + threadIdx.x, k = 0; k < DRIFT_PER_THREAD && j < npc;
@@ -241,6 +252,93 @@ __device__ __forceinline__ long long flux32(int nh, unsigned nl, int C)
     long long lo = (long long)((unsigned long long)nl * (unsigned)C);
     if (C < 0) lo -= (long long)((unsigned long long)nl << 32);  // nl (C + 2^32) - nl 2^32
     return (long long)(((unsigned long long)hi << 2) + (unsigned long long)((lo + (1LL << 29)) >> 30));
+}
+
+// rint(w), round half even, for |w| < 2^31, branch-free with FP32 and
+// integer instructions: w = h 2^16 + l exactly, where h = rint(w 2^-16) and
+// |l| <= 2^15, and each half is rounded with the 1.5 2^23 shifter (h 2^16 is
+// even, so rint(w) = h 2^16 + rint(l), ties included).
+__device__ __forceinline__ int rint_split(float w)
+{
+    const float hs = fmaf(w, 1.0f / 65536.0f, 12582912.0f);  // exact product, one rounding: rint(w / 2^16) + 1.5 2^23
+    const float h = hs - 12582912.0f;
+    const float l = fmaf(-h, 65536.0f, w);                    // exact
+    const float ls = l + 12582912.0f;
+    return (int)(((unsigned)(__float_as_int(hs) - 0x4B400000) << 16) + (unsigned)(__float_as_int(ls) - 0x4B400000));
+}
+
+// Courant integer of the narrow form, rint((p_d inv) K) with K = dt/dx 2^30:
+// the exact power-of-two factor folded into K gives the same float as
+// ((p_d inv) dt/dx) 2^30 wherever the rounded value can be nonzero.
+__device__ __forceinline__ int courant_i32(float pd, float inv, float K)
+{
+    return rint_split((pd * inv) * K);
+}
+
+__device__ __forceinline__ long long flux_n(long long n, int C)
+{
+    return flux32((int)(n >> 32), (unsigned)n, C);
+}
+
+// Force term of Eq. (left handside), -div_p[(grad_x E) f]: along p_i the p
+// cells of an x cell all move with dp_i/dt = -dE/dx_i = -g_i / E, where
+// g_i = (m^2(x + e_i) - m^2(x - e_i)) / (4 dx) is half the central difference
+// of the species' m^2 (written per x cell and mass slot by k_force_grad, FP64
+// then FP32).  Courant number ((-g_i) (1/E)) dt/dp_i in FP32, in 2^-30 fixed
+// point; upwind in p; no flux through the faces of the momentum box, so the
+// sum of the state is exact.
+__global__ void k_force_grad(const __grid_constant__ DriftArgs P)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P.nxc * 4) return;
+    const int64_t x = t >> 2;
+    const int ms = (int)(t & 3);
+    const int ny = P.nx[1], nz = P.nx[2];
+    const int xi[3] = {(int)(x / ((int64_t)ny * nz)), (int)((x / nz) % ny), (int)(x % nz)};
+    const int64_t xs[3] = {(int64_t)ny * nz, nz, 1};
+    for (int i = 0; i < 3; ++i) {
+        float g = 0.0f;
+        if (P.nx[i] > 1 && P.mass_mode != 1) {
+            const int64_t xl = x + (int64_t)(xi[i] == 0 ? P.nx[i] - 1 : -1) * xs[i];
+            const int64_t xh = x + (int64_t)(xi[i] == P.nx[i] - 1 ? 1 - P.nx[i] : 1) * xs[i];
+            g = (float)((P.m2[xh * 4 + ms] - P.m2[xl * 4 + ms]) * P.inv4dx);
+        }
+        P.gforce[t * 3 + i] = g;
+    }
+}
+
+// one face flux of the force term: narrow integer form for |w| < 2^31
+__device__ __forceinline__ long long force_flux(long long n, float g, float inv, float K)
+{
+    const float w = ((-g) * inv) * K;
+    if (fabsf(w) < 2147483648.0f) return flux32((int)(n >> 32), (unsigned)n, rint_split(w));
+    return flux_fx(n, rint_ll(w));
+}
+
+// Force-term part of the update of cell j (p indices jv) of one (slot, x)
+// row: the cell's own outflow through the face it moves towards and the
+// inflow from the cell behind it, each only if that face is inside the box.
+__device__ __forceinline__ long long force_acc(const DriftArgs& P, const float* g3, int jp, int j,
+                                               const long long* in_row, const float* ie_row, long long n, float inv)
+{
+    const int jv[3] = {jp & 0xff, (jp >> 8) & 0xff, jp >> 16};
+    const int stride[3] = {P.np[1] * P.np[2], P.np[2], 1};
+    long long acc = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (P.nx[i] == 1) continue;
+        const float g = g3[i];
+        const bool up = (-g) > 0.0f;  // towards larger p_i
+        const int jo = jv[i] + (up ? 1 : -1), jb = jv[i] + (up ? -1 : 1);
+        long long own = 0, behind = 0;
+        if (jo >= 0 && jo < P.np[i]) own = force_flux(n, g, inv, P.Kp[i]);
+        if (jb >= 0 && jb < P.np[i]) {
+            const int jj = j + (up ? -stride[i] : stride[i]);
+            behind = force_flux(__ldg(in_row + jj), g, __ldg(ie_row + jj), P.Kp[i]);
+        }
+        acc += up ? own - behind : behind - own;
+    }
+    return acc;
 }
 
 template <bool NARROW>
@@ -298,6 +396,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
                 // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down
                 acc += pf[d] > 0.0f ? f_own - f_nb : f_nb - f_own;
             }
+            if (P.force) acc += force_acc(P, P.gforce + (x * 4 + ms) * 3, jp, j, in_row, ie_row, ncj, inv);
         } else if (P.inv_e) {  // inverse energies of every cell precomputed by k_inv_energy
             const float* ie_row = P.inv_e + row * P.npc;
             const float inv = __ldg(ie_row + j);
@@ -311,6 +410,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
                 // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down
                 acc += pf[d] > 0.0f ? flux_fx(ncj, own_C) - flux_fx(nn, nb_C) : flux_fx(nn, nb_C) - flux_fx(ncj, own_C);
             }
+            if (P.force) acc += force_acc(P, P.gforce + (x * 4 + ms) * 3, jp, j, in_row, ie_row, ncj, inv);
         } else {
             bool own_done = false;
             long long own_C[3] = {0, 0, 0};
@@ -343,6 +443,133 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
     }
 }
 
+// Drift by (y, z) planes, the same integer fluxes as k_drift with every face
+// flux of the two inner x axes computed once: a thread owns one p cell of one
+// (slot, x index ix) and walks a segment of y rows in the upwind order of its
+// p_y, and each row in ascending z.  The y-face flux of the row upwind of the
+// current one is kept per z cell in shared memory; the z-face fluxes of cells
+// z - 1, z, z + 1 in registers (the next cell's state is loaded one step
+// ahead).  Only the x axis reads its upwind neighbour.  Face fluxes per cell:
+// 4 + 1/n_z + 1/(rows per segment), against 6 in k_drift.
+constexpr int PLANE_THREADS = 128;
+constexpr int PLANE_MAX_NZ = 40;  // y-face buffer: n_z x PLANE_THREADS int64 of dynamic shared memory
+#ifndef BZ_PLANE_THREADS_PER_SM
+#define BZ_PLANE_THREADS_PER_SM 2048
+#endif
+#ifndef BZ_PLANE_XFAST
+#define BZ_PLANE_XFAST 1  // 1: blocks of all (slot, x index, segment) of a p tile run together (x neighbours in L2)
+#endif
+#ifndef BZ_HW_CVT
+#define BZ_HW_CVT 0       // 1: f conversion with the hardware int64 -> float instruction (slower here)
+#endif
+
+template <bool FORCE>
+__global__ void __launch_bounds__(PLANE_THREADS) k_drift_plane(const __grid_constant__ DriftArgs P, int nseg, float K)
+{
+    __shared__ float s_pf[3][MAX_NP];
+    extern __shared__ long long s_fy[];  // [n_z][PLANE_THREADS]
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
+    __syncthreads();
+    const int npc = (int)P.npc;
+    const unsigned bj = BZ_PLANE_XFAST ? blockIdx.y : blockIdx.x, bs = BZ_PLANE_XFAST ? blockIdx.x : blockIdx.y;
+    const int j = bj * PLANE_THREADS + threadIdx.x;
+    if (j >= npc) return;
+    const int nx0 = P.nx[0], ny = P.nx[1], nz = P.nx[2];
+    const int seg = (int)(bs % (unsigned)nseg);
+    const int rest = (int)(bs / (unsigned)nseg);
+    const int ix = rest % nx0, sl = rest / nx0;
+    const int jp = __ldg(P.jtab + j);
+    const float p0 = s_pf[0][jp & 0xff], p1 = s_pf[1][(jp >> 8) & 0xff], p2 = s_pf[2][jp >> 16];
+    const bool sx = p0 > 0.0f, sy = p1 > 0.0f, sz = p2 > 0.0f;  // p_d > 0: the upwind neighbour is the lower one
+    const int ixu = sx ? (ix == 0 ? nx0 - 1 : ix - 1) : (ix == nx0 - 1 ? 0 : ix + 1);
+    const int64_t plane = (int64_t)ny * nz * P.npc;  // cells of one x index
+    const int64_t zs = P.npc;                         // cells between z neighbours
+    const int64_t b_own = (int64_t)sl * P.nxc * P.npc + (int64_t)ix * plane + j;
+    const int64_t b_up = (int64_t)sl * P.nxc * P.npc + (int64_t)ixu * plane + j;
+    const long long* in = P.in;
+    const float* ie = P.inv_e;
+    long long* fy = s_fy + threadIdx.x;
+    const bool mx = nx0 > 1, my = ny > 1, mz = nz > 1;
+    const int t0 = (int)((int64_t)seg * ny / nseg), t1 = (int)((int64_t)(seg + 1) * ny / nseg);
+    if (my) {  // y-face fluxes of the row upwind of the segment's first row
+        const int tw = t0 == 0 ? ny - 1 : t0 - 1;
+        const int64_t rw = b_own + (int64_t)(sy ? tw : ny - 1 - tw) * nz * zs;
+        for (int iz = 0; iz < nz; ++iz) {
+            const int64_t o = rw + iz * zs;
+            fy[iz * PLANE_THREADS] = flux_n(__ldg(in + o), courant_i32(p1, __ldg(ie + o), K));
+        }
+    }
+#pragma unroll 1
+    for (int t = t0; t < t1; ++t) {
+        const int64_t rb = b_own + (int64_t)(sy ? t : ny - 1 - t) * nz * zs;
+        const int64_t ru = b_up + (rb - b_own);
+        long long n_cur = __ldg(in + rb);
+        float i_cur = __ldg(ie + rb);
+        long long fz_cur = 0, fz_prev = 0, fz_first = 0;
+        if (mz) {
+            fz_cur = flux_n(n_cur, courant_i32(p2, i_cur, K));
+            fz_first = fz_cur;
+            const int64_t ol = rb + (int64_t)(nz - 1) * zs;
+            fz_prev = flux_n(__ldg(in + ol), courant_i32(p2, __ldg(ie + ol), K));
+        }
+#pragma unroll 1
+        for (int iz = 0; iz < nz; ++iz) {
+            const int64_t oc = rb + iz * zs;
+            long long n_nx = 0, fz_next = fz_first;
+            float i_nx = 0.0f;
+            if (iz + 1 < nz) {
+                n_nx = __ldg(in + oc + zs);
+                i_nx = __ldg(ie + oc + zs);
+                fz_next = flux_n(n_nx, courant_i32(p2, i_nx, K));
+            }
+            long long acc = 0;
+            // p_d > 0: outflow through the upper face, inflow from below; else the mirror
+            if (mz) acc += sz ? fz_cur - fz_prev : fz_next - fz_cur;
+            if (my) {
+                const long long f1 = flux_n(n_cur, courant_i32(p1, i_cur, K));
+                const long long fu = fy[iz * PLANE_THREADS];
+                acc += sy ? f1 - fu : fu - f1;
+                fy[iz * PLANE_THREADS] = f1;
+            }
+            if (mx) {
+                const long long f0 = flux_n(n_cur, courant_i32(p0, i_cur, K));
+                const int64_t ou = ru + iz * zs;
+                const long long fu = flux_n(__ldg(in + ou), courant_i32(p0, __ldg(ie + ou), K));
+                acc += sx ? f0 - fu : fu - f0;
+            }
+            if (FORCE) {
+                const int64_t xr = (oc - j) / P.npc;  // slot * nxc + x
+                const float* g3 = P.gforce + ((xr - (int64_t)sl * P.nxc) * 4 + P.slot_mslot[sl]) * 3;
+                acc += force_acc(P, g3, jp, j, in + (oc - j), ie + (oc - j), n_cur, i_cur);
+            }
+            P.out[oc] = n_cur - acc;
+            if (P.freal) {
+                if (P.freal_double)
+                    static_cast<double*>(P.freal)[oc] = (double)n_cur * TWO_POW_M40 / P.deg[sl];
+                else
+                    static_cast<float*>(P.freal)[oc] = (BZ_HW_CVT ? __ll2float_rn(n_cur) : ll2float_rn(n_cur)) * P.fscale[sl];
+            }
+            fz_prev = fz_cur;
+            fz_cur = fz_next;
+            n_cur = n_nx;
+            i_cur = i_nx;
+        }
+    }
+}
+
+static int device_sms()
+{
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            nsm < 1)
+            nsm = 1;
+    }
+    return nsm;
+}
+
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
 {
     const int64_t rows = a.ncell / a.npc;
@@ -350,6 +577,26 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
     if (rows < 1 || rows > 2147483647LL || tiles > 65535) return cudaErrorInvalidConfiguration;
     const bool moving = a.nx[0] > 1 || a.nx[1] > 1 || a.nx[2] > 1;
     if (a.inv_e && moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
+    if (a.force && !(a.inv_e && a.gforce && moving)) return cudaErrorInvalidValue;
+    if (a.force) k_force_grad<<<(unsigned)((a.nxc * 4 + 127) / 128), 128, 0, s>>>(a);
+    const int64_t nslots = rows / a.nxc;
+    if (a.inv_e && moving && a.dtdxf < 1.99f && a.nx[2] <= PLANE_MAX_NZ) {
+        // y segments: enough threads for every SM at full occupancy
+        const int64_t base = nslots * a.nx[0] * a.npc;
+        int64_t nseg = ((int64_t)device_sms() * BZ_PLANE_THREADS_PER_SM + base - 1) / base;
+        nseg = nseg < 1 ? 1 : (nseg > a.nx[1] ? a.nx[1] : nseg);
+        const int64_t gs = nslots * a.nx[0] * nseg, gj = (a.npc + PLANE_THREADS - 1) / PLANE_THREADS;
+        const int64_t gx = BZ_PLANE_XFAST ? gs : gj, gy = BZ_PLANE_XFAST ? gj : gs;
+        if (gy <= 65535 && gx <= 2147483647LL) {
+            const size_t smem = sizeof(long long) * PLANE_THREADS * (size_t)a.nx[2];
+            const dim3 grid((unsigned)gx, (unsigned)gy);
+            if (a.force)
+                k_drift_plane<true><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, a.dtdxf * 1073741824.0f);
+            else
+                k_drift_plane<false><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, a.dtdxf * 1073741824.0f);
+            return cudaGetLastError();
+        }
+    }
     DriftArgs b = a;
     if (!moving) b.inv_e = nullptr;
     if (a.dtdxf < 1.99f)  // |C| <= 2^30 dt/dx < 2^31
@@ -442,6 +689,13 @@ __device__ __forceinline__ double i128_to_double(__int128 v)
     return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
 }
 
+#ifndef BZ_MOM_UNROLL
+#define BZ_MOM_UNROLL 2  // cells in flight per thread
+#endif
+#ifndef BZ_MOM_MINB
+#define BZ_MOM_MINB 4    // resident blocks per SM (register budget)
+#endif
+
 // Exact sums of one (x cell, slot); writes 5 doubles at o.
 __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, int sl, double* o)
 {
@@ -452,33 +706,79 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
     const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
     const int npc = (int)P.npc, np1 = P.np[1], np2 = P.np[2];
-    __int128 v[5] = {0, 0, 0, 0, 0};
     const long long pauli = P.pauli[sl];
     int neg = 0, over = 0;  // state warnings: f < 0 anywhere, f > 1 for fermions (Pauli)
-    for (int j = threadIdx.x; j < npc; j += blockDim.x) {
-        int jv[3];
-        if (P.jtab) {
-            const int jp = __ldg(P.jtab + j);
-            jv[0] = jp & 0xff;
-            jv[1] = (jp >> 8) & 0xff;
-            jv[2] = jp >> 16;
-        } else {
-            const int jxy = j / np2;
-            jv[0] = jxy / np1;
-            jv[1] = jxy % np1;
-            jv[2] = j % np2;
-        }
-        const float pf0 = s_pf[0][jv[0]], pf1 = s_pf[1][jv[1]], pf2 = s_pf[2][jv[2]];
-        const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
-        const long long Efx = rint_ll(sqrtf(ppf + m) * 16777216.0f);
-        const long long n = __ldg(&st[j]);
-        neg += n < 0;
-        over += n > pauli;
-        v[0] += n;
-        v[1] += (__int128)Efx * n;
+    // n = nh 2^32 + nl (nl unsigned): every product below is 32 x 32 bits and
+    // every partial sum is exact, for at most 2^16 cells per thread
+    // (npc <= 2^24, 256 threads): sum nl < 2^48, sum (k_d + 256) nl < 2^57,
+    // sum k_d nh < 2^55 with |k_d| = |2 j_d + 1 - n_d| < 2^8.  E_fx n is
+    // accumulated in 128 bits (lo word and carries).
+    unsigned long long s_nl = 0;
+    long long s_nh = 0;
+    unsigned long long el_lo = 0, el_hi = 0;  // sum E_fx nl (unsigned, 128 bits)
+    unsigned long long eh_lo = 0;             // sum E_fx nh (signed, 128 bits: lo word ...
+    long long eh_hi = 0;                      // ... and high word)
+    unsigned long long kl[3] = {0, 0, 0};     // sum (k_d + 256) nl
+    long long kh[3] = {0, 0, 0};              // sum k_d nh
+    __int128 e_wide = 0;                      // sum E_fx n of cells with E_fx >= 2^31 (exact, rare)
+    constexpr int U = BZ_MOM_UNROLL;          // cells in flight per thread
+    for (int j0 = threadIdx.x; j0 < npc; j0 += U * (int)blockDim.x) {
+        long long nv[U];
+        int jpv[U];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) v[2 + d] += (__int128)(2 * jv[d] + 1 - P.np[d]) * n;
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * (int)blockDim.x;
+            nv[u] = j < npc ? __ldg(&st[j]) : 0;
+            if (P.jtab) {
+                jpv[u] = j < npc ? __ldg(P.jtab + j) : 0;
+            } else {
+                const int jj = j < npc ? j : 0, jxy = jj / np2;
+                jpv[u] = (jxy / np1) | ((jxy % np1) << 8) | ((jj % np2) << 16);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * (int)blockDim.x;
+            if (j >= npc) break;
+            const long long n = nv[u];
+            const int jv[3] = {jpv[u] & 0xff, (jpv[u] >> 8) & 0xff, jpv[u] >> 16};
+            const float pf0 = s_pf[0][jv[0]], pf1 = s_pf[1][jv[1]], pf2 = s_pf[2][jv[2]];
+            const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
+            const float ew = sqrtf(ppf + m) * 16777216.0f;
+            neg += n < 0;
+            over += n > pauli;
+            const unsigned nl = (unsigned)n;
+            const int nh = (int)(n >> 32);
+            s_nl += nl;
+            s_nh += nh;
+            if (ew < 2147483648.0f) {  // E_fx < 2^31 (ew is >= 0 or NaN)
+                const unsigned Efx = (unsigned)rint_split(ew);
+                const unsigned long long tl = (unsigned long long)Efx * nl;
+                el_lo += tl;
+                el_hi += el_lo < tl;
+                const long long th = (long long)(int)Efx * nh;
+                const unsigned long long o = eh_lo;
+                eh_lo += (unsigned long long)th;
+                eh_hi += (th >> 63) + (eh_lo < o);
+            } else {
+                e_wide += (__int128)rint_ll(ew) * n;
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int k = 2 * jv[d] + 1 - P.np[d];
+                kl[d] += (unsigned long long)(unsigned)(k + 256) * nl;
+                kh[d] += (long long)k * nh;
+            }
+        }
     }
+    __int128 v[5];
+    const __int128 snl = (__int128)s_nl;
+    const __int128 two32 = (__int128)1 << 32;
+    v[0] = (__int128)s_nh * two32 + snl;
+    const __int128 eh = (__int128)(((unsigned __int128)(unsigned long long)eh_hi << 64) | eh_lo);
+    v[1] = (__int128)(((unsigned __int128)el_hi << 64) | el_lo) + eh * two32 + e_wide;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[2 + d] = (__int128)kh[d] * two32 + ((__int128)kl[d] - 256 * snl);
     __shared__ __int128 red[5][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (P.sflags) {
@@ -503,7 +803,7 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     }
 }
 
-__global__ void __launch_bounds__(256) k_moments(const __grid_constant__ MomentArgs P)
+__global__ void __launch_bounds__(256, BZ_MOM_MINB) k_moments(const __grid_constant__ MomentArgs P)
 {
     const int64_t x = blockIdx.x / P.nslots;
     const int sl = blockIdx.x % P.nslots;
@@ -558,7 +858,7 @@ cudaError_t launch_convert_batch(const long long* state, float* f, const int64_t
 
 // Moments of every (box, slot): one block each, through slot_prefix; out
 // advances by one step's worth per call index (*kidx).
-__global__ void __launch_bounds__(256) k_moments_batch(const MomentArgs* __restrict__ boxes,
+__global__ void __launch_bounds__(256, BZ_MOM_MINB) k_moments_batch(const MomentArgs* __restrict__ boxes,
                                                        const int* __restrict__ slot_prefix, int nboxes,
                                                        double* out, const int* kidx, int per_step)
 {

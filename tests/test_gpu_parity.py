@@ -195,41 +195,84 @@ def test_equilibrium_vanishes_on_gpu():
     assert off > 1000 * max(eq, 1)
 
 
-def test_drift_bit_exact_with_x_dependent_masses():
+DRIFT_CASES = [
+    # nx, np, mask, dt (dx = 0.2), f range
+    ((4, 3, 5), (6, 6, 6), 0x03, 0.05, (0.0, 0.6)),
+    ((1, 4, 1), (5, 6, 4), 0x01, 0.3, (-0.2, 0.6)),     # y only, odd np_x (p_x = 0 cells)
+    ((3, 1, 1), (4, 4, 4), 0x01, 0.1, (0.0, 0.6)),      # x only
+    ((1, 1, 5), (6, 5, 4), 0x01, 0.2, (-0.2, 0.6)),     # z only, |c| up to 1
+    ((2, 5, 3), (4, 6, 4), 0x11, 0.39, (-0.2, 0.6)),    # dt/dx = 1.95, narrow integer form
+    ((2, 3, 2), (4, 4, 4), 0x01, 0.45, (0.0, 0.6)),     # dt/dx = 2.25, wide (128-bit) form
+    ((1, 2, 41), (4, 4, 4), 0x01, 0.05, (0.0, 0.6)),    # n_z above the plane kernel's buffer
+    ((7, 6, 5), (6, 8, 10), 0x7F, 0.1, (-0.1, 0.6)),    # 7 species, ragged
+]
+
+
+@pytest.mark.parametrize("force", [False, True])
+@pytest.mark.parametrize("nx,np_,mask,dt,frange", DRIFT_CASES)
+def test_drift_bit_exact_with_x_dependent_masses(nx, np_, mask, dt, frange, force):
+    """x drift (and with force=True the force term -div_p[(grad_x E) f]) on
+    random masses per x cell, bit for bit."""
     torch = torch_mod()
-    nx, np_, mask = (4, 3, 5), (6, 6, 6), 0x03
+    nxc = nx[0] * nx[1] * nx[2]
     h, cfg = make_pair(nx=nx, dx=0.2, np_=np_, mask=mask, mass_mode=2)
+    cfg.force = 1 if force else 0
+    h.set_force_term(force)
     rng = np.random.default_rng(2)
-    m2 = rng.uniform(0.0, 0.5, size=(60, 4))
+    m2 = rng.uniform(0.0, 0.5, size=(nxc, 4))
     h.set_masses(m2)
-    st = random_state(mask, 60, np_, 8)
+    st = random_state(mask, nxc, np_, 8, *frange)
     out = torch.empty(st.size, dtype=torch.int64, device="cuda")
-    h.drift(to_dev(st), out, 0.05)
-    ref = O.drift(cfg, st, m2, 0.05)
+    h.drift(to_dev(st), out, dt)
+    ref = O.drift(cfg, st, m2, dt)
     got = out.cpu().numpy().reshape(ref.shape)
     assert np.array_equal(got, ref)
     assert got.sum() == st.sum()
 
 
-def test_moments_bit_exact():
+@pytest.mark.parametrize("mask", [0x01, 0x06, 0x31])
+def test_masses_bit_exact_species_subsets(mask):
+    """Masses with some species absent (their 1/(2E) is not evaluated) equal
+    the oracle's, which evaluates every species; the second call uses the
+    first call's dispersion."""
+    from paper_1912_04457_gb300 import bz
+    torch = torch_mod()
+    np_ = (6, 8, 6)
+    h, cfg = make_pair(np_=np_, mask=mask)
+    st = random_state(mask, 1, np_, 12)
+    A = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    h.collision_term(to_dev(st), A, 1, 0, 0.01, bz.PREC_F32)
+    m_first = O.masses(cfg, st)
+    assert np.array_equal(h.get_masses(), m_first)
+    h.collision_term(to_dev(st), A, 1, 1, 0.01, bz.PREC_F32)
+    assert np.array_equal(h.get_masses(), O.masses(cfg, st, m_first))
+
+
+@pytest.mark.parametrize("frange", [(0.0, 0.6), (-0.3, 0.6), (-1e5, 1e5)])
+def test_moments_bit_exact(frange):
+    """Exact sums, including negative cells and values near 2^61 (the high
+    words of every split product)."""
     torch = torch_mod()
     nx, np_, mask = (2, 1, 3), (6, 8, 10), 0x7F
     h, cfg = make_pair(nx=nx, dx=0.2, np_=np_, mask=mask, mass_mode=2)
     m2 = np.random.default_rng(3).uniform(0.0, 0.4, size=(6, 4))
     h.set_masses(m2)
-    st = random_state(mask, 6, np_, 9)
+    st = random_state(mask, 6, np_, 9, *frange)
     out = torch.empty(6 * 7 * 5, dtype=torch.float64, device="cuda")
     h.moments(to_dev(st), out)
     ref, _ = O.moments(cfg, st, m2)
     assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
 
 
-@pytest.mark.parametrize("mask,mass_mode", [(0x01, 0), (0x13, 0), (0x01, 1)])
-def test_step_bit_exact_inhomogeneous(mask, mass_mode):
+@pytest.mark.parametrize("mask,mass_mode,force", [(0x01, 0, False), (0x13, 0, False), (0x01, 1, False),
+                                                   (0x13, 0, True), (0x01, 1, True)])
+def test_step_bit_exact_inhomogeneous(mask, mass_mode, force):
     from paper_1912_04457_gb300 import bz
     torch = torch_mod()
     nx, np_, N, dt = (4, 4, 2), (6, 6, 6), 32, 0.02
     h, cfg = make_pair(nx=nx, dx=0.2, np_=np_, mask=mask, mass_mode=mass_mode)
+    cfg.force = 1 if force else 0
+    h.set_force_term(force)
     nxc = 32
     st = random_state(mask, nxc, np_, 10, 0.0, 0.4)
     dev = to_dev(st)
