@@ -940,6 +940,55 @@ int bzo_moments(const bzo_config* c, const int64_t* state, const double* m2, dou
 }
 
 /* ------------------------------------------------------------------ */
+/* Source of the kinetic energy-momentum tensor, Eq. (current            */
+/* conservation): S_ex^0 = (1/2) sum_a (dm_a^2/dt) I_a with              */
+/* I_a = int d^3p/(2pi)^3 N_a f_a / E_a, and the term -(1/4) m_a^2 I_a   */
+/* of the modified total energy T_total^00 (single flavour).  Per        */
+/* (x cell, slot), out[3] = {I_a, S_ex^0 part (1/2)((m^2 - m^2_prev)/dt) */
+/* I_a, -(1/4) m^2 I_a}.  I_a is an exact integer sum of n R with        */
+/* R = round(2^24 / E), 1/E = 1/sqrt(p^2 + m^2) in IEEE FP32 at the bin  */
+/* centre with the masses m2 (as the drift); with the massless           */
+/* dispersion E does not depend on m^2 and both m^2 terms are zero.      */
+/* ------------------------------------------------------------------ */
+int bzo_energy_source(const bzo_config* c, const int64_t* state, const double* m2, const double* m2_prev, double dt,
+                      double* out)
+{
+    int ns = nslots(c);
+    int64_t nxc = n_xcells(c), npc = n_pcells(c);
+    double dp[3] = {2.0 * c->L / c->np[0], 2.0 * c->L / c->np[1], 2.0 * c->L / c->np[2]};
+    double twopi = 2.0 * PI;
+    double pref = dp[0] * dp[1] * dp[2] / (twopi * twopi * twopi) * TWO_POW_M40;
+    int species[NSPEC];
+    for (int s = 0; s < NSPEC; ++s)
+        if (slot_of(c, s) >= 0) species[slot_of(c, s)] = s;
+    for (int64_t x = 0; x < nxc; ++x) {
+        for (int sl = 0; sl < ns; ++sl) {
+            int ms = mass_slot(species[sl]);
+            float m = c->mass_mode == 1 ? 0.0f : (float)m2[x * 4 + ms];
+            __int128 acc = 0;
+            for (int64_t j = 0; j < npc; ++j) {
+                int jv[3] = {(int)(j / ((int64_t)c->np[1] * c->np[2])),
+                             (int)((j / c->np[2]) % c->np[1]), (int)(j % c->np[2])};
+                float pf[3];
+                for (int d = 0; d < 3; ++d) pf[d] = (float)(-c->L + ((double)jv[d] + 0.5) * dp[d]);
+                float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
+                float inv = 1.0f / sqrtf(ppf + m);
+                int64_t R = llrintf(inv * 16777216.0f);
+                acc += (__int128)R * state[((int64_t)sl * nxc + x) * npc + j];
+            }
+            double I = i128_to_double(acc) * pref * (1.0 / 16777216.0);
+            double mc = c->mass_mode == 1 ? 0.0 : m2[x * 4 + ms];
+            double mp = c->mass_mode == 1 ? 0.0 : m2_prev[x * 4 + ms];
+            double* o = out + (x * ns + sl) * 3;
+            o[0] = I;
+            o[1] = 0.5 * ((mc - mp) / dt) * I;
+            o[2] = -0.25 * mc * I;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* One forward-Euler step, all terms from f^n (unsplit):                */
 /*   m^2 <- masses(n^n, E from m2_prev);  n^{n+1} = drift(n^n) + A(n^n) */
 /* m2 (in/out): previous masses on entry (ignored when first != 0),     */

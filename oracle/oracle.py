@@ -60,6 +60,7 @@ def lib():
         _lib.bzo_drift.argtypes = [P, P, P, C.c_double, P]
         _lib.bzo_drift_f64.argtypes = [P, P, P, C.c_double, P]
         _lib.bzo_moments.argtypes = [P, P, P, P, P]
+        _lib.bzo_energy_source.argtypes = [P, P, P, P, C.c_double, P]
         _lib.bzo_step.argtypes = [P, P, P, P, C.c_int, P, P]
         _lib.bzo_num_threads.restype = C.c_int
         _lib.bzo_proposal_sample.argtypes = [P, C.c_double, P, P]
@@ -218,6 +219,18 @@ def moments(cfg, state, m2):
     nsum = np.zeros(ns, dtype=np.int64)
     lib().bzo_moments(C.byref(cfg), _ptr(state), _ptr(m2), _ptr(out), _ptr(nsum))
     return out, nsum
+
+
+def energy_source(cfg, state, m2, m2_prev, dt):
+    """Per (x cell, slot): [I = int d^3p/(2pi)^3 N f / E, S_ex^0 part
+    (1/2)((m^2 - m^2_prev)/dt) I, -(1/4) m^2 I] (Eq. (current conservation))."""
+    ns, nxc, npc = ncells(cfg)
+    state = np.ascontiguousarray(state, dtype=np.int64).reshape(-1)
+    m2 = np.ascontiguousarray(m2, dtype=np.float64).reshape(nxc, 4)
+    m2_prev = np.ascontiguousarray(m2_prev, dtype=np.float64).reshape(nxc, 4)
+    out = np.zeros((nxc, ns, 3))
+    lib().bzo_energy_source(C.byref(cfg), _ptr(state), _ptr(m2), _ptr(m2_prev), C.c_double(dt), _ptr(out))
+    return out
 
 
 def step(cfg, state, m2, first, nsamples, step_index, dt, sampler=SYMMETRIC, ubits=32):
