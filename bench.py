@@ -329,6 +329,27 @@ def run_bz(args):
     t_e2e = e0.elapsed_time(e1) / 1e3
     e2e_value = samples_step * n_e2e * world / t_e2e
 
+    # energy balance of one more step (outside the timed region), Eq. (current
+    # conservation): d_0 T^00 against S_ex^0 = (1/2) sum_a (dm_a^2/dt) int N_a f_a/E_a
+    energy = None
+    if rank == 0:
+        mom_a = torch.empty_like(mom)
+        h.step(state, w.dt, 1, w.nsamples, prec, step0=3000, moments_out=mom_a)
+        m_prev = h.get_masses()
+        f_n = state.clone()
+        mom_b = torch.empty_like(mom)
+        h.step(state, w.dt, 1, w.nsamples, prec, step0=3001, moments_out=mom_b)
+        src = h.energy_source(f_n, w.dt, m_prev).view(w.nxc, w.nslots, 3)
+        t_a = mom_a.view(w.nxc, w.nslots, 5)[:, :, 1].sum(1).mean().item()
+        t_b = mom_b.view(w.nxc, w.nslots, 5)[:, :, 1].sum(1).mean().item()
+        energy = {"dT00_dt": (t_b - t_a) / w.dt, "S_ex0": src[:, :, 1].sum(1).mean().item(),
+                  "T00": t_b, "T_total_term": src[:, :, 2].sum(1).mean().item(),
+                  "unit": "GeV^4 per fm/c (T00 and T_total_term: GeV^4), averaged over x cells",
+                  "note": "one step of the FP32 path after the timed loop: the change of the kinetic energy "
+                          "density against the mass-variation source; the collisions conserve energy up to "
+                          "the binning of the legs, so the two agree up to that error"}
+        del f_n, mom_a, mom_b, src
+
     # streaming kernels of inhomogeneous grids against the HBM roofline, and the
     # cost of the optional force term (outside the timed region)
     transport = None
@@ -430,6 +451,7 @@ def run_bz(args):
                                                                       for i in range(3)]}
                             for k, sp in enumerate(I.slots(w.species_mask))},
                 "after_steps": args.warmup + args.steps, "dt_fm": w.dt,
+                "energy_balance": energy,
             },
         }
         print(json.dumps(result), flush=True)

@@ -129,12 +129,13 @@ int bz_collision_term(bz_handle h, const int64_t* state, int64_t* A, int32_t nsa
 int bz_collision_audit(bz_handle h, const int64_t* state, int64_t* A, int32_t nsamples, int32_t step, double dt,
                        int32_t sampler, double* audit_host, void* stream);
 
-/* Free streaming, Eq. (left handside) without the force term: first-order
- * upwind in flux form, periodic in x, v = p/E_p(x) with the handle's current
- * masses (E = |p| in mass mode MASSLESS).  Courant numbers in IEEE FP32 held
- * in 2^-30 fixed point; each face flux is an exact rounded integer product
- * applied with opposite signs to its two cells, so the sum of the state is
- * invariant.  in, out: device int64 [nslots][nx][np], must not overlap. */
+/* Free streaming, Eq. (left handside): first-order upwind in flux form,
+ * periodic in x, v = p/E_p(x) with the handle's current masses (E = |p| in
+ * mass mode MASSLESS), plus the force term when bz_set_force_term enabled
+ * it.  Courant numbers in IEEE FP32 held in 2^-30 fixed point; each face
+ * flux is an exact rounded integer product applied with opposite signs to
+ * its two cells, so the sum of the state is invariant.  in, out: device
+ * int64 [nslots][nx][np], must not overlap. */
 int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt, void* stream);
 
 /* nsteps forward-Euler steps of Eq. (left handside) with all terms from
@@ -151,6 +152,23 @@ int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, int32_t nsam
  * densities (GeV^3, GeV^4), E at the bin centres with the handle's current
  * masses.  state: device int64; out: device double [nx][nslots][5]. */
 int bz_moments(bz_handle h, const int64_t* state, double* out, void* stream);
+
+/* Energy source of the kinetic energy-momentum tensor, Eq. (current
+ * conservation): d_mu T_kin^{mu nu} = S_ex^nu = (1/2) sum_a d^nu m_a^2 I_a
+ * with I_a = int d^3p/(2pi)^3 N_a f_a / E_a.  Per x cell and active species,
+ * out[x][slot][0..2] = (I_a in GeV^2, (1/2)((m_a^2 - m_prev^2)/dt) I_a in
+ * GeV^4 per fm/c -- the species' part of S_ex^0 --, -(1/4) m_a^2 I_a in
+ * GeV^4 -- the term that turns T_kin^00 into the modified total energy
+ * T_total^00 of a single flavour).  E and m_a^2 are the handle's current
+ * masses (computed from state first if the handle has none); m2_prev_host
+ * (host double [nx][4], as bz_get_masses) are the masses of the previous
+ * evaluation, or NULL for no mass change (zero source).  I_a is an exact
+ * integer sum of n round(2^24 / E), 1/E in IEEE FP32 at the bin centres;
+ * with the massless dispersion both m^2 terms are zero.  state: device
+ * int64; out: device double [nx][nslots][3].  Errors: BZ_EINVAL for null
+ * pointers or dt <= 0, or mass mode FIXED without bz_set_masses. */
+int bz_energy_source(bz_handle h, const int64_t* state, const double* m2_prev_host, double dt, double* out,
+                     void* stream);
 
 /* Current masses, host double [nx][4] = (m_g^2, m_u^2, m_d^2, m_s^2) in
  * GeV^2.  bz_get_masses synchronises the stream of the last call.

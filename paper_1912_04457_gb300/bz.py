@@ -62,6 +62,7 @@ SIGNATURES = {
     "bz_get_state_flags": (C.c_int, [_P, _P]),
     "bz_set_uniform_bits": (C.c_int, [_P, _I32]),
     "bz_set_force_term": (C.c_int, [_P, _I32]),
+    "bz_energy_source": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
     "bz_profile_read": (C.c_int, [_P, _P, _P, _I32]),
@@ -336,6 +337,20 @@ class Handle:
         self._check(self.lib.bz_moments(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
                                         _dev_ptr(out, torch.float64, self.nxc * self.nslots * 5, "out"),
                                         _stream_ptr(stream)))
+
+    def energy_source(self, state, dt, m2_prev=None, out=None, stream=None):
+        """Per (x cell, slot): [int N f / E, S_ex^0 part, T_total term] (bz_energy_source);
+        m2_prev: host [nx, 4] masses of the previous evaluation, or None."""
+        import torch
+        if out is None:
+            out = torch.empty(self.nxc * self.nslots * 3, dtype=torch.float64, device=state.device)
+        prev = None if m2_prev is None else np.ascontiguousarray(m2_prev, dtype=np.float64).reshape(self.nxc, 4)
+        self._check(self.lib.bz_energy_source(self.h, _dev_ptr(state, torch.int64, self.ncell, "state"),
+                                              None if prev is None else prev.ctypes.data_as(C.c_void_p),
+                                              C.c_double(dt),
+                                              _dev_ptr(out, torch.float64, self.nxc * self.nslots * 3, "out"),
+                                              _stream_ptr(stream)))
+        return out
 
 
 class Batch:

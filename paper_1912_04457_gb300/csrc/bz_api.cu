@@ -38,6 +38,7 @@ struct bz_handle_s {
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
+    double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
     bool force = false;            // the drift includes the force term -div_p[(grad_x E) f]
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
     long long* d_sflags = nullptr; // state warnings (2): f < 0 cells, fermion f > 1 cells
@@ -157,6 +158,8 @@ static void free_scratch(bz_handle h)
     h->d_inv_e = nullptr;
     cudaFree(h->d_gforce);
     h->d_gforce = nullptr;
+    cudaFree(h->d_m2prev);
+    h->d_m2prev = nullptr;
     cudaFree(h->d_audit);
     h->d_audit = nullptr;
     cudaFree(h->d_sflags);
@@ -959,6 +962,36 @@ extern "C" int bz_moments(bz_handle h, const int64_t* state, double* out, void* 
     {
         ProfScope ps(h, BZ_K_MOMENTS, s);
         CK(h, launch_moments(a, s));
+    }
+    return BZ_OK;
+}
+
+extern "C" int bz_energy_source(bz_handle h, const int64_t* state, const double* m2_prev_host, double dt, double* out,
+                                void* stream)
+{
+    if (!h || !state || !out) return BZ_EINVAL;
+    if (!(dt > 0)) return fail(h, BZ_EINVAL, "dt must be positive");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if (!h->have_masses && h->mass_mode == BZ_MASS_THERMAL)
+        if ((rc = compute_masses(h, reinterpret_cast<const long long*>(state), s))) return rc;
+    if (!h->have_masses && h->mass_mode == BZ_MASS_FIXED)
+        return fail(h, BZ_EINVAL, "mass mode FIXED needs bz_set_masses first");
+    MomentArgs a{};  // with the massless dispersion the masses are not read
+    fill_moments(h, a, reinterpret_cast<const long long*>(state), out);
+    a.sflags = nullptr;
+    a.dt = dt;
+    if (m2_prev_host) {
+        if (!h->d_m2prev && cudaMalloc(&h->d_m2prev, sizeof(double) * 4 * h->nxc) != cudaSuccess)
+            return fail(h, BZ_ENOMEM, "cannot allocate the previous masses");
+        CK(h, cudaMemcpyAsync(h->d_m2prev, m2_prev_host, sizeof(double) * 4 * h->nxc, cudaMemcpyHostToDevice, s));
+        a.m2_prev = h->d_m2prev;
+    } else {
+        a.m2_prev = h->d_m2[h->cur];  // no previous masses given: no source
+    }
+    {
+        ProfScope ps(h, BZ_K_MOMENTS, s);
+        CK(h, launch_energy_source(a, s));
     }
     return BZ_OK;
 }

@@ -166,6 +166,9 @@ struct MomentArgs {
     const int* jtab;        // [npc] jx | jy << 8 | jz << 16, or null (decoded by division)
     long long* sflags;      // [2] cells with n < 0, fermion cells with f > 1 (added), or null
     long long pauli[NSPEC]; // per slot: N_s 2^40 (f = 1) for (anti)quarks, LLONG_MAX for gluons
+    // energy source (k_energy_source): out is [x][slot][3], masses of the previous evaluation, dt
+    const double* m2_prev;
+    double dt;
 };
 
 // Per-slot scales of the f conversion: FP64 degeneracy, and the FP32
@@ -227,6 +230,8 @@ cudaError_t launch_sum_weights(const ProposalRecord* rec, int64_t n, double* out
 cudaError_t launch_masses(const MassArgs& a, cudaStream_t s);
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s);
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
+// per (x cell, slot): int N f / E, its S_ex^0 part and the T_total term (Eq. (current conservation))
+cudaError_t launch_energy_source(const MomentArgs& a, cudaStream_t s);
 cudaError_t launch_convert(const long long* state, void* freal, int as_double, int64_t nxc,
                            int64_t npc, int nslots, const double* deg, cudaStream_t s);
 

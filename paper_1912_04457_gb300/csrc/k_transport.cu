@@ -816,6 +816,75 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Energy source, Eq. (current conservation): per (x cell, slot) the integral
+// I = int d^3p/(2pi)^3 N f / E as an exact integer sum of n round(2^24 / E)
+// (1/E in IEEE FP32 at the bin centre, as the drift), then
+// S_ex^0 part (1/2)((m^2 - m^2_prev)/dt) I and the T_total term -(1/4) m^2 I
+// in FP64.  With the massless dispersion both m^2 terms are zero.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_energy_source(const __grid_constant__ MomentArgs P)
+{
+    __shared__ float s_pf[3][MAX_NP];
+    for (int d = 0; d < 3; ++d)
+        for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
+    __syncthreads();
+    const int64_t x = blockIdx.x / P.nslots;
+    const int sl = blockIdx.x % P.nslots;
+    const int ms = P.slot_mslot[sl];
+    const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + ms];
+    const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
+    const int npc = (int)P.npc;
+    // n = nh 2^32 + nl: sum R nl (unsigned) and sum R nh (signed), each in 128 bits by carries
+    unsigned long long l_lo = 0, l_hi = 0, h_lo = 0;
+    long long h_hi = 0;
+    __int128 wide = 0;  // cells with 2^24 / E >= 2^31 (E < 2^-7 GeV)
+    for (int j = threadIdx.x; j < npc; j += blockDim.x) {
+        const int jp = __ldg(P.jtab + j);
+        const float pf0 = s_pf[0][jp & 0xff], pf1 = s_pf[1][(jp >> 8) & 0xff], pf2 = s_pf[2][jp >> 16];
+        const float ppf = (pf0 * pf0 + pf1 * pf1) + pf2 * pf2;
+        const float w = (1.0f / sqrtf(ppf + m)) * 16777216.0f;
+        const long long n = __ldg(st + j);
+        if (w < 2147483648.0f) {
+            const unsigned R = (unsigned)rint_split(w);
+            const unsigned long long tl = (unsigned long long)R * (unsigned)n;
+            l_lo += tl;
+            l_hi += l_lo < tl;
+            const long long th = (long long)(int)R * (int)(n >> 32);
+            const unsigned long long o = h_lo;
+            h_lo += (unsigned long long)th;
+            h_hi += (th >> 63) + (h_lo < o);
+        } else {
+            wide += (__int128)rint_ll(w) * n;
+        }
+    }
+    const __int128 hpart = (__int128)(((unsigned __int128)(unsigned long long)h_hi << 64) | h_lo);
+    __int128 v = (__int128)(((unsigned __int128)l_hi << 64) | l_lo) + hpart * ((__int128)1 << 32) + wide;
+    __shared__ __int128 red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    v = warp_sum_i128(v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 t = 0;
+        for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) t += red[w8];
+        const double I = i128_to_double(t) * P.pref * (1.0 / 16777216.0);
+        const double mc = P.mass_mode == 1 ? 0.0 : P.m2[x * 4 + ms];
+        const double mp = P.mass_mode == 1 ? 0.0 : P.m2_prev[x * 4 + ms];
+        double* o = P.out + (x * P.nslots + sl) * 3;
+        o[0] = I;
+        o[1] = 0.5 * ((mc - mp) / P.dt) * I;
+        o[2] = -0.25 * mc * I;
+    }
+}
+
+cudaError_t launch_energy_source(const MomentArgs& a, cudaStream_t s)
+{
+    if (!a.jtab || !a.m2_prev) return cudaErrorInvalidValue;
+    k_energy_source<<<(unsigned)(a.nxc * a.nslots), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 __global__ void k_zero_ll(long long* p, int64_t n)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
