@@ -287,6 +287,51 @@ static int solve_roots(const double p[3], double Ep, const double k3[3], double 
     return n;
 }
 
+/* ------------------------------------------------------------------ */
+/* The second choice of Sec. III.A: k3 = k1 + k2 - p eliminated.  Given */
+/* p, k2 and k1_perp, E1 - E3 = Ep - E2 = dl with E3^2 = c2 + (k1z +    */
+/* K)^2, c2 = (k1x + k2x - px)^2 + (k1y + k2y - py)^2 + mc^2, K = k2z - */
+/* pz.  Squaring twice gives (K^2 - dl^2) z^2 - K (A0 + 2 dl^2) z +     */
+/* A0^2/4 - dl^2 (c2 + K^2) = 0 with A0 = a2 - c2 - K^2 - dl^2; a root  */
+/* of it solves the original equation iff A0 - 2 K z (= 2 dl E3) has   */
+/* the sign of dl and E3 + dl > 0.  J = d(E1 - E3)/dk1z = k1z/E1 -      */
+/* (k1z + K)/E3.  Returns the roots with (k1z, E1, E3, J) in r[].       */
+/* ------------------------------------------------------------------ */
+static int solve_roots_k3(const double p[3], double Ep, const double k2[3], double E2, double k1x, double k1y,
+                          double ma2, double mc2, bzo_root r[2])
+{
+    double cx = (k1x + k2[0]) - p[0], cy = (k1y + k2[1]) - p[1], K = k2[2] - p[2];
+    double a2 = (k1x * k1x + k1y * k1y) + ma2;
+    double c2 = (cx * cx + cy * cy) + mc2;
+    double dl = Ep - E2;
+    double A0 = ((a2 - c2) - K * K) - dl * dl;
+    double qa = K * K - dl * dl;
+    double qb = -K * (A0 + 2.0 * dl * dl);
+    double qc = 0.25 * A0 * A0 - dl * dl * (c2 + K * K);
+    if (qa == 0.0 || dl == 0.0) return 0;
+    double disc = qb * qb - 4.0 * qa * qc;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    double Q = -0.5 * (qb >= 0.0 ? qb + sq : qb - sq);
+    if (Q == 0.0) return 0;
+    double zc[2] = {Q / qa, qc / Q};
+    int n = 0;
+    for (int i = 0; i < 2; ++i) {
+        double z = zc[i];
+        double w = A0 - 2.0 * K * z;
+        if (!(dl > 0.0 ? w > 0.0 : w < 0.0)) continue;
+        double zk = z + K;
+        double E3 = sqrt(c2 + zk * zk);
+        if (!(E3 + dl > 0.0)) continue;
+        double E1 = sqrt(a2 + z * z);
+        double J = z / E1 - zk / E3;
+        if (J == 0.0) continue;
+        r[n].z = z; r[n].E1 = E1; r[n].E2 = E3; r[n].J = J;  /* E2 slot carries E3 here */
+        ++n;
+    }
+    return n;
+}
+
 /* Exported for the two-body phase-space pin: returns the number of valid
  * roots and, per root, (k1z, E1, E2, J) in out[4*i..4*i+3]. */
 int bzo_roots(const double p[3], double md2, const double k3[3], double mc2,
@@ -438,6 +483,8 @@ typedef struct {
     int64_t anchor_offset;
     const double* u_explicit;/* optional [anchor][sample][8] uniforms replacing Philox */
     const double* prop;      /* sampler 2: per-anchor proposal (mu3 x3, sigma3, sigma1, alpha, -, -) */
+    int32_t param;           /* 0: k2 = k3 + p - k1 eliminated (the paper's choice); 1: k3 = k1 + k2 - p
+                                eliminated, (k1_perp, k2) sampled (Sec. III.A, "less stable") */
 } bzo_run;
 
 /* Learned-proposal sample: defensive mixture q(y) = alpha/32 + (1 - alpha)
@@ -473,6 +520,116 @@ static double uniform_of(uint32_t x, int ubits)
 {
     if (ubits == 23) return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
     return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* One sample of the k3-eliminating parameterisation (run param 1):     */
+/* (k1x, k1y, k2) uniform in the box, k1z from solve_roots_k3, k3 =      */
+/* k1 + k2 - p; a root is kept if k1z and k3 lie in the box.  Weights,   */
+/* |M|^2, W and the four deposits as in the k2 form, with the Jacobian   */
+/* of this root.                                                         */
+static void collide_sample_k3(const bzo_config* c, const bzo_run* r, const int64_t* state, const double* mdisp,
+                              double mg2reg, int d, int64_t x, const int jv[3], const double p[3], double k1x,
+                              double k1y, const double k2[3], const bzo_term* terms, int nterms, const bzo_mconst* mk,
+                              double Kq, double Kown, double twopi5, int64_t* A, double* c64, double* g64,
+                              double* audit, int64_t* flags)
+{
+    int64_t nxc = n_xcells(c), npc = n_pcells(c);
+    double L = c->L, twoL = 2.0 * c->L;
+    double dp[3] = {twoL / c->np[0], twoL / c->np[1], twoL / c->np[2]};
+    double pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
+    double kk2 = (k2[0] * k2[0] + k2[1] * k2[1]) + k2[2] * k2[2];
+    int64_t linp = ((int64_t)jv[0] * c->np[1] + jv[1]) * c->np[2] + jv[2];
+    int64_t lin2 = ((int64_t)bin_of(k2[0], L, dp[0], c->np[0]) * c->np[1] + bin_of(k2[1], L, dp[1], c->np[1]))
+                       * c->np[2] + bin_of(k2[2], L, dp[2], c->np[2]);
+    for (int ti = 0; ti < nterms; ++ti) {
+        const bzo_term* T = &terms[ti];
+        int sa = T->leg[0], sb = T->leg[1], sc = T->leg[2], sd = T->leg[3];
+        double ma2 = mdisp[mass_slot(sa)], mb2 = mdisp[mass_slot(sb)];
+        double mc2 = mdisp[mass_slot(sc)], md2 = mdisp[mass_slot(sd)];
+        double Ep = sqrt(pp + md2);
+        double E2 = sqrt(kk2 + mb2);
+        bzo_root rt[2];
+        int nr = solve_roots_k3(p, Ep, k2, E2, k1x, k1y, ma2, mc2, rt);
+        for (int ri = 0; ri < nr; ++ri) {
+            double z = rt[ri].z, E1 = rt[ri].E1, E3 = rt[ri].E2, J = rt[ri].J;
+            double k1[3] = {k1x, k1y, z};
+            double k3[3] = {(k1x + k2[0]) - p[0], (k1y + k2[1]) - p[1], z + (k2[2] - p[2])};
+            if (!in_box(z, L) || !in_box(k3[0], L) || !in_box(k3[1], L) || !in_box(k3[2], L)) continue;
+            double E = Ep + E3;
+            double PP = ((p[0] + k3[0]) * (p[0] + k3[0]) + (p[1] + k3[1]) * (p[1] + k3[1]))
+                        + (p[2] + k3[2]) * (p[2] + k3[2]);
+            double s = E * E - PP;
+            double k1k3 = (k1[0] * k3[0] + k1[1] * k3[1]) + k1[2] * k3[2];
+            double k1p = (k1[0] * p[0] + k1[1] * p[1]) + k1[2] * p[2];
+            double t = (ma2 + mc2) - 2.0 * (E1 * E3 - k1k3);
+            double uu = (ma2 + md2) - 2.0 * (E1 * Ep - k1p);
+            if (s <= 0.0 || t - mg2reg >= 0.0 || uu - mg2reg >= 0.0) {
+#pragma omp atomic
+                flags[0] += 1;
+                continue;
+            }
+            double M2 = msq(T->cls, mk, s, t, uu, mg2reg);
+            int64_t lin1 = ((int64_t)bin_of(k1[0], L, dp[0], c->np[0]) * c->np[1] + bin_of(k1[1], L, dp[1], c->np[1]))
+                               * c->np[2] + bin_of(k1[2], L, dp[2], c->np[2]);
+            int64_t lin3 = ((int64_t)bin_of(k3[0], L, dp[0], c->np[0]) * c->np[1] + bin_of(k3[1], L, dp[1], c->np[1]))
+                               * c->np[2] + bin_of(k3[2], L, dp[2], c->np[2]);
+            double f1, f2, f3, fp;
+            if (c->analytic) {
+                f1 = f_equilibrium(c, sa, E1);
+                f2 = f_equilibrium(c, sb, E2);
+                f3 = f_equilibrium(c, sc, E3);
+                fp = f_equilibrium(c, sd, Ep);
+            } else {
+                f1 = f_of_state(state[((int64_t)slot_of(c, sa) * nxc + x) * npc + lin1], sa);
+                f2 = f_of_state(state[((int64_t)slot_of(c, sb) * nxc + x) * npc + lin2], sb);
+                f3 = f_of_state(state[((int64_t)slot_of(c, sc) * nxc + x) * npc + lin3], sc);
+                fp = f_of_state(state[((int64_t)slot_of(c, sd) * nxc + x) * npc + linp], sd);
+            }
+            double F1 = is_quark(sa) ? 1.0 - f1 : 1.0 + f1;
+            double F2 = is_quark(sb) ? 1.0 - f2 : 1.0 + f2;
+            double F3 = is_quark(sc) ? 1.0 - f3 : 1.0 + f3;
+            double Fp = is_quark(sd) ? 1.0 - fp : 1.0 + fp;
+            double gain = f1 * f2 * F3 * Fp;
+            double W = gain - F1 * F2 * f3 * fp;
+            double den = fabs(J) * twopi5 * 16.0 * E1 * E2 * E3 * Ep;
+            double ct = T->sym * W * M2 / den;
+            double wq = ct * Kown;
+            if (!(fabs(wq) < 4611686018427387904.0)) {
+#pragma omp atomic
+                flags[1] += 1;
+                continue;
+            }
+            int64_t q = llrint(wq);
+            *c64 += ct * (Kq * 4.0) * (1.0 / TWO_POW_40);
+            *g64 += (T->sym * gain * M2 / den) * (Kq * 4.0) * (1.0 / TWO_POW_40);
+            {
+                int64_t idx = ((int64_t)slot_of(c, sd) * nxc + x) * npc + linp;
+#pragma omp atomic
+                A[idx] += q;
+            }
+            if (r->sampler != 1) {
+                int64_t i3 = ((int64_t)slot_of(c, sc) * nxc + x) * npc + lin3;
+                int64_t i1 = ((int64_t)slot_of(c, sa) * nxc + x) * npc + lin1;
+                int64_t i2 = ((int64_t)slot_of(c, sb) * nxc + x) * npc + lin2;
+#pragma omp atomic
+                A[i3] += q;
+#pragma omp atomic
+                A[i1] -= q;
+#pragma omp atomic
+                A[i2] -= q;
+            }
+            if (audit) {
+                double w = ct * Kq;
+                audit[0] += w * ((Ep + E3) - (E1 + E2));
+                audit[1] += w * ((p[0] + k3[0]) - (k1[0] + k2[0]));
+                audit[2] += w * ((p[1] + k3[1]) - (k1[1] + k2[1]));
+                audit[3] += w * ((p[2] + k3[2]) - (k1[2] + k2[2]));
+                audit[4] += fabs(w) * (Ep + E3 + E1 + E2);
+                audit[5] += 1.0;
+                audit[6] += fabs(w);
+            }
+        }
+    }
 }
 
 /* Samples the anchor (slot sl / species d, x-cell x, p-cell j).  Deposits
@@ -530,7 +687,12 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
         } else {
             k1x = -L + twoL * u[3];
             k1y = -L + twoL * u[4];
-            for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];
+            for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];  /* k2 when param == 1 */
+        }
+        if (r->param == 1) {
+            collide_sample_k3(c, r, state, mdisp, mg2reg, d, x, jv, p, k1x, k1y, k3, terms, nterms, mk, Kq, Kown,
+                              twopi5, A, &c64, &g64, audit, flags);
+            continue;
         }
         double pp = (p[0] * p[0] + p[1] * p[1]) + p[2] * p[2];
         double kk3 = (k3[0] * k3[0] + k3[1] * k3[1]) + k3[2] * k3[2];

@@ -35,6 +35,7 @@ class Run(C.Structure):
         ("anchor_stride", C.c_int64), ("anchor_offset", C.c_int64),
         ("u_explicit", C.POINTER(C.c_double)),
         ("prop", C.POINTER(C.c_double)),
+        ("param", C.c_int32),
     ]
 
 
@@ -143,8 +144,9 @@ def masses(cfg, state, m2_prev=None):
 
 
 def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=False,
-             anchor_stride=1, anchor_offset=0, u_explicit=None, prop=None):
+             anchor_stride=1, anchor_offset=0, u_explicit=None, prop=None, param=0):
     r = Run()
+    r.param = param
     r.nsamples = nsamples
     r.step = step
     r.dt = dt
@@ -168,15 +170,17 @@ def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=Fa
 
 def collision(cfg, state, m2, nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32,
               p_center=False, anchor_stride=1, anchor_offset=0, u_explicit=None,
-              want_c64=False, want_audit=False, prop=None):
-    """Returns dict with A (int64 [slot][x][p]), flags, and optionally C64/G64/audit."""
+              want_c64=False, want_audit=False, prop=None, param=0):
+    """Returns dict with A (int64 [slot][x][p]), flags, and optionally C64/G64/audit.
+    param 0: k2 eliminated (the paper's choice), 1: k3 eliminated."""
     ns, nxc, npc = ncells(cfg)
     state = np.ascontiguousarray(state, dtype=np.int64).reshape(-1)
     m2 = np.ascontiguousarray(m2, dtype=np.float64).reshape(nxc, 4)
     if sampler == LEARNED:
         assert prop is not None and np.asarray(prop).size == ns * nxc * npc * 8
+        assert param == 0, "the learned sampler draws (k1_perp, k3)"
     run = make_run(nsamples, step, dt, sampler, ubits, p_center, anchor_stride, anchor_offset,
-                   u_explicit, prop)
+                   u_explicit, prop, param)
     A = np.zeros(ns * nxc * npc, dtype=np.int64)
     C64 = np.zeros(ns * nxc * npc) if want_c64 else None
     G64 = np.zeros(ns * nxc * npc) if want_c64 else None

@@ -29,8 +29,13 @@ def _bin(k):
 
 def _k3_elimination(f, p, n, rng):
     """(2L)^5/n sum over samples and roots of c~ with k3 eliminated; per-batch means."""
+    return (2 * L) ** 5 * _k3_contrib(f, p, rng.random((n, 5))).reshape(20, -1).mean(1)
+
+
+def _k3_contrib(f, p, u):
+    """Per sample (uniforms u[:, 0:2] -> k1_perp, u[:, 2:5] -> k2): sum over roots of c~."""
     inb = lambda v: (v >= -L) & (v < L)
-    u = rng.random((n, 5))
+    n = u.shape[0]
     k1x, k1y = -L + 2 * L * u[:, 0], -L + 2 * L * u[:, 1]
     k2 = -L + 2 * L * u[:, 2:5]
     a2 = k1x ** 2 + k1y ** 2 + M2G
@@ -74,7 +79,7 @@ def _k3_elimination(f, p, n, rng):
         W = f1 * f2 * (1 + f3) * (1 + fp) - (1 + f1) * (1 + f2) * f3 * fp
         ct = 0.5 * W * M2 / (J[idx] * (2 * np.pi) ** 5 * 16 * E1[idx] * E2[idx] * E3[idx] * Ep)
         contrib[idx] += ct
-    return (2 * L) ** 5 * contrib.reshape(20, -1).mean(1)
+    return contrib
 
 
 @pytest.mark.parametrize("anchor", [(1, 1, 1), (2, 1, 3), (0, 2, 2)])
@@ -100,3 +105,46 @@ def test_k3_elimination_agrees_with_oracle(anchor):
     # while a wrong Jacobian or root leaves a heavy-tailed estimate whose own error
     # exceeds its value
     assert err < 0.2 * abs(m2_)
+
+
+def test_oracle_k3_parameterisation_equals_this_one_sample_by_sample():
+    """The oracle's selectable k3-eliminating form (run param 1) on explicit
+    uniforms equals the estimate above on the same uniforms (different code,
+    same mathematics): per anchor to 1e-9."""
+    cfg, st = _setup()
+    m2 = np.full((1, 4), M2G)
+    f = I.decode(st, 0x01)[0, 0]
+    n = 4000
+    rng = np.random.default_rng(5)
+    u = rng.random((NP ** 3, n, 8))
+    r = O.collision(cfg, st, m2, n, dt=0.01, sampler=O.PLAIN, p_center=True, u_explicit=u,
+                    want_c64=True, param=1)
+    got = r["C64"].reshape(-1) * HBARC / 0.01
+    for anchor in [(1, 1, 1), (2, 1, 3), (0, 2, 2), (3, 3, 0)]:
+        a = (anchor[0] * NP + anchor[1]) * NP + anchor[2]
+        p = -L + (np.array(anchor) + 0.5) * (2 * L / NP)
+        want = (2 * L) ** 5 * _k3_contrib(f, p, u[a, :, 3:8]).mean()
+        assert got[a] == pytest.approx(want, rel=1e-9, abs=1e-12)
+
+
+def test_oracle_k3_parameterisation_agrees_with_k2_and_conserves():
+    """Symmetric deposits of the k3 form sum to zero exactly, and its plain
+    estimate agrees with the k2 form's within their errors (3 anchors)."""
+    cfg, st = _setup()
+    m2 = np.full((1, 4), M2G)
+    r = O.collision(cfg, st, m2, 256, dt=0.01, param=1)
+    assert int(r["A"].sum()) == 0 and np.abs(r["A"]).sum() > 0
+    for anchor in [(1, 1, 1), (0, 2, 2)]:
+        a = (anchor[0] * NP + anchor[1]) * NP + anchor[2]
+        est = {0: [], 1: []}
+        for prm in (0, 1):
+            for sd in range(20):
+                cfg.seed = 300 + sd
+                rr = O.collision(cfg, st, m2, 1 << 16, step=0, dt=0.01, sampler=O.PLAIN, p_center=True,
+                                 anchor_stride=NP ** 3, anchor_offset=a, want_c64=True, param=prm)
+                est[prm].append(rr["C64"].reshape(-1)[a])
+        m0, m1 = np.mean(est[0]), np.mean(est[1])
+        err = np.sqrt(np.var(est[0], ddof=1) / 20 + np.var(est[1], ddof=1) / 20)
+        assert abs(m0 - m1) < 5 * err
+        assert err < 0.2 * abs(m0)
+        assert np.std(est[1]) > np.std(est[0])     # the "less stable" choice has the larger spread
