@@ -602,6 +602,47 @@ def run_batch(args):
     return 0
 
 
+def run_stability(args):
+    """The stability comparison of Sec. III.A (Fig. 2): 40^3 gluons on
+    [-2, 2) GeV, f uniform in [0, 1] (seeded), alpha_s = 0.3, 100 samples per
+    cell, dt = 0.01 fm/c, the plain (own-cell) estimator on the FP64 path;
+    the gluon number after one step over independent evaluations, with k2
+    (the paper's choice) or k3 eliminated.  Prints one JSON report."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1912_04457_gb300 import build as B
+    B.build()
+    from paper_1912_04457_gb300 import bz
+    from paper_1912_04457_gb300 import inputs as I
+    n, L, N, dt, evals = 40, 2.0, 100, 0.01, 20
+    st = I.encode(I.random_f((n, n, n), 1, 1, 11, 0.0, 1.0), 0x01)
+    dev = torch.from_numpy(st.reshape(-1)).cuda()
+    number0 = float(dev.double().sum().item())
+    out = {"workload": "stability_gluon_40cube_N100", "evaluations": evals, "sampler": "plain (own cell)",
+           "precision": "f64", "data": "synthetic: f uniform in [0, 1], seed 11"}
+    for param, name in ((0, "k2_eliminated"), (1, "k3_eliminated")):
+        numbers, ms = [], []
+        for e in range(evals):
+            h = bz.Handle(np_=(n, n, n), L=L, seed=500 + e, species_mask=0x01, alpha_s=0.3)
+            h.set_parameterisation(param)
+            A = torch.empty_like(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            h.collision_term(dev, A, N, 0, dt, bz.PREC_F64, bz.SAMPLER_PLAIN)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            numbers.append((number0 + float(A.double().sum().item())) / number0)
+            h.close()
+        v = np.array(numbers)
+        out[name] = {"relative_number_mean": float(v.mean()), "relative_number_std": float(v.std(ddof=1)),
+                     "ms_per_evaluation_median": float(np.median(ms))}
+    out["std_ratio_k3_over_k2"] = out["k3_eliminated"]["relative_number_std"] / out["k2_eliminated"]["relative_number_std"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_tts(args):
     """Time to solution of the collision term at equal MC error on the 7-species
     32^3 box: FP64 uniform (symmetric and plain deposition) against FP32
@@ -753,7 +794,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bz", choices=["bz", "reference"])
-    ap.add_argument("--workload", default="qgp", choices=["qgp", "gluon_step", "gluon_bump", "batch", "tts"])
+    ap.add_argument("--workload", default="qgp",
+                    choices=["qgp", "gluon_step", "gluon_bump", "batch", "tts", "stability"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -767,6 +809,8 @@ def main():
         return run_batch(args)
     if args.workload == "tts":
         return run_tts(args)
+    if args.workload == "stability":
+        return run_stability(args)
     return run_bz(args)
 
 

@@ -197,6 +197,17 @@ int bz_clear_flags(bz_handle h);
  * Errors: BZ_EINVAL for other values. */
 int bz_set_uniform_bits(bz_handle h, int32_t bits);
 
+/* Which momentum the delta function of Eq. (delta function) eliminates
+ * (Sec. III.A): which = 0 (default, the paper's choice) k2 = k3 + p - k1,
+ * with (k1x, k1y, k3) sampled and k1z from E1 + E2 = E3 + Ep; which = 1
+ * k3 = k1 + k2 - p, with (k1x, k1y, k2) sampled and k1z from E1 - E3 =
+ * Ep - E2 (the paper's "less stable" choice, for its stability comparison):
+ * same box, volume (2L)^5, deposits and weights, the Jacobian of the
+ * solved equation.  which = 1 is for the FP64 path with uniform samples;
+ * collision calls with the FP32 path or the learned sampler then fail with
+ * BZ_EINVAL.  Errors: BZ_EINVAL for other values. */
+int bz_set_parameterisation(bz_handle h, int32_t which);
+
 /* Force term -div_p[(grad_x E) f] of Eq. (left handside) (dp/dt = -grad_x E,
  * Eq. (boltzmann equation general form)), added to the drift of bz_drift and
  * bz_step when enable = 1 (default 0).  Along p_i the p cells of an x cell

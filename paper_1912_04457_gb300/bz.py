@@ -62,6 +62,7 @@ SIGNATURES = {
     "bz_get_state_flags": (C.c_int, [_P, _P]),
     "bz_set_uniform_bits": (C.c_int, [_P, _I32]),
     "bz_set_force_term": (C.c_int, [_P, _I32]),
+    "bz_set_parameterisation": (C.c_int, [_P, _I32]),
     "bz_energy_source": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
@@ -179,6 +180,10 @@ class Handle:
 
     def set_uniform_bits(self, bits):
         self._check(self.lib.bz_set_uniform_bits(self.h, bits))
+
+    def set_parameterisation(self, which):
+        """0: k2 eliminated (default), 1: k3 eliminated (FP64 path, uniform samples)."""
+        self._check(self.lib.bz_set_parameterisation(self.h, which))
 
     def set_force_term(self, enable=True):
         self._check(self.lib.bz_set_force_term(self.h, 1 if enable else 0))

@@ -40,6 +40,7 @@ struct bz_handle_s {
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
     double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
     bool force = false;            // the drift includes the force term -div_p[(grad_x E) f]
+    int param = 0;                 // FP64 collision: 0 k2 eliminated, 1 k3 eliminated
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
     long long* d_sflags = nullptr; // state warnings (2): f < 0 cells, fermion f > 1 cells
     int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
@@ -360,6 +361,14 @@ extern "C" int bz_set_uniform_bits(bz_handle h, int32_t bits)
     return BZ_OK;
 }
 
+extern "C" int bz_set_parameterisation(bz_handle h, int32_t which)
+{
+    if (!h) return BZ_EINVAL;
+    if (which != 0 && which != 1) return fail(h, BZ_EINVAL, "parameterisation must be 0 (k2) or 1 (k3)");
+    h->param = which;
+    return BZ_OK;
+}
+
 extern "C" int bz_set_force_term(bz_handle h, int32_t enable)
 {
     if (!h) return BZ_EINVAL;
@@ -640,6 +649,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.mass_mode = h->mass_mode;
     a.analytic = h->analytic;
     a.p_center = 0;
+    a.param = sizeof(R) == sizeof(double) ? h->param : 0;
     a.T = (R)h->T;
     for (int s = 0; s < NSPEC; ++s) a.mu[s] = (R)h->mu[s];
     a.Kq = (R)Kq;
@@ -798,6 +808,8 @@ static int check_common(bz_handle h, int nsamples, int step, double dt, int prec
         return fail(h, BZ_EINVAL, "bad sampler %d", sampler);
     if (sampler == BZ_SAMPLER_LEARNED && !h->anchor_prm_ready)
         return fail(h, BZ_EINVAL, "the learned sampler needs per-anchor proposal parameters (bz_proposal_infer)");
+    if (h->param == 1 && (prec != BZ_PREC_F64 || sampler == BZ_SAMPLER_LEARNED))
+        return fail(h, BZ_EINVAL, "the k3-eliminating parameterisation runs on the FP64 path with uniform samples");
     return BZ_OK;
 }
 

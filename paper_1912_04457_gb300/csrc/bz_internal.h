@@ -89,6 +89,7 @@ struct CollideArgs {
     int nsamples, step;
     int64_t n_sel, a_stride, a_offset;
     int sampler, mass_mode, analytic, p_center;
+    int param;              // FP64 path: 0 k2 eliminated (the paper's choice), 1 k3 eliminated
     R T, mu[NSPEC];
     R Kq, Kown, twopi5;
     R A1, A2, A3, A4, A5;

@@ -327,6 +327,130 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
     return own;
 }
 
+// The second parameterisation of Sec. III.A (param 1): k3 = k1 + k2 - p
+// eliminated, (k1_perp, k2) sampled (G.k3 and G.kk3 hold k2 and |k2|^2).
+// E1 - E3 = Ep - E2 = dl squared twice gives (K^2 - dl^2) z^2
+// - K (A0 + 2 dl^2) z + A0^2/4 - dl^2 (c2 + K^2) = 0, K = k2z - pz,
+// A0 = a2 - c2 - K^2 - dl^2; a root is one of the original equation iff
+// A0 - 2 K z has the sign of dl and E3 + dl > 0; |J| = |z/E1 - (z + K)/E3|.
+// Deposits, weights and flags as eval_term.  FP64 only.
+template <typename R>
+__device__ __forceinline__ long long eval_term_k3(const CollideArgs<R>& P, const Geom<R>& G, int64_t a, int ti)
+{
+    using O = Ops<R>;
+    const R L = P.L;
+    const int64_t nxc = P.nxc, npc = P.npc;
+    const TermDev& T = P.terms[G.d][ti];
+    const R ma2 = G.mdisp[T.mslot[0]], mb2 = G.mdisp[T.mslot[1]];
+    const R mc2 = G.mdisp[T.mslot[2]], md2 = G.mdisp[T.mslot[3]];
+    const R* k2 = G.k3;
+    const R Ep = O::sqrt_(G.pp + md2);
+    const R E2 = O::sqrt_(G.kk3 + mb2);
+    const R k1x = G.k1x, k1y = G.k1y;
+    const R cx = (k1x + k2[0]) - G.p[0], cy = (k1y + k2[1]) - G.p[1], K = k2[2] - G.p[2];
+    const R a2 = G.a2m + ma2;
+    const R c2 = (cx * cx + cy * cy) + mc2;
+    const R dl = Ep - E2;
+    const R A0 = ((a2 - c2) - K * K) - dl * dl;
+    const R qa = K * K - dl * dl;
+    const R qb = -K * (A0 + R(2) * dl * dl);
+    const R qc = R(0.25) * A0 * A0 - dl * dl * (c2 + K * K);
+    if (qa == R(0) || dl == R(0)) return 0;
+    const R disc = qb * qb - R(4) * qa * qc;
+    if (disc < R(0)) return 0;
+    const R sq = O::sqrt_(disc);
+    const R Q = R(-0.5) * (qb >= R(0) ? qb + sq : qb - sq);
+    if (Q == R(0)) return 0;
+    R zc[2];
+    zc[0] = Q / qa;
+    zc[1] = qc / Q;
+    const int64_t lin2 = ((int64_t)bin_of(k2[0], L, P.dp[0], P.np[0]) * P.np[1] + bin_of(k2[1], L, P.dp[1], P.np[1]))
+                             * P.np[2]
+                         + bin_of(k2[2], L, P.dp[2], P.np[2]);
+    long long own = 0;
+#pragma unroll
+    for (int ri = 0; ri < 2; ++ri) {
+        const R z = zc[ri];
+        const R w = A0 - R(2) * K * z;
+        if (!(dl > R(0) ? w > R(0) : w < R(0))) continue;
+        const R zk = z + K;
+        const R E3 = O::sqrt_(c2 + zk * zk);
+        if (!(E3 + dl > R(0))) continue;
+        const R E1 = O::sqrt_(a2 + z * z);
+        const R J = z / E1 - zk / E3;
+        if (J == R(0)) continue;
+        const R k3[3] = {cx, cy, z + (k2[2] - G.p[2])};
+        if (!in_box(z, L) || !in_box(k3[0], L) || !in_box(k3[1], L) || !in_box(k3[2], L)) continue;
+        const R E = Ep + E3;
+        const R PP = ((G.p[0] + k3[0]) * (G.p[0] + k3[0]) + (G.p[1] + k3[1]) * (G.p[1] + k3[1]))
+                     + (G.p[2] + k3[2]) * (G.p[2] + k3[2]);
+        const R s = E * E - PP;
+        const R k1k3 = (k1x * k3[0] + k1y * k3[1]) + z * k3[2];
+        const R k1p = (k1x * G.p[0] + k1y * G.p[1]) + z * G.p[2];
+        const R t = (ma2 + mc2) - R(2) * (E1 * E3 - k1k3);
+        const R uu = (ma2 + md2) - R(2) * (E1 * Ep - k1p);
+        const R mg2 = G.mg2;
+        if (s <= R(0) || t - mg2 >= R(0) || uu - mg2 >= R(0)) {
+            red_add(&P.flags[0], 1);
+            continue;
+        }
+        const R M2 = msq<R>(T.cls, P, s, t, uu, mg2);
+        const int64_t lin1 = ((int64_t)bin_of(k1x, L, P.dp[0], P.np[0]) * P.np[1] + bin_of(k1y, L, P.dp[1], P.np[1]))
+                                 * P.np[2]
+                             + bin_of(z, L, P.dp[2], P.np[2]);
+        const int64_t lin3 = ((int64_t)bin_of(k3[0], L, P.dp[0], P.np[0]) * P.np[1] + bin_of(k3[1], L, P.dp[1], P.np[1]))
+                                 * P.np[2]
+                             + bin_of(k3[2], L, P.dp[2], P.np[2]);
+        const int64_t i1 = (int64_t)T.slot[0] * nxc * npc + G.xoff + lin1;
+        const int64_t i2 = (int64_t)T.slot[1] * nxc * npc + G.xoff + lin2;
+        const int64_t i3 = (int64_t)T.slot[2] * nxc * npc + G.xoff + lin3;
+        R f1, f2, f3, fp;
+        if (P.analytic) {
+            f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
+            f2 = f_equilibrium(P, P.slot_species[T.slot[1]], E2);
+            f3 = f_equilibrium(P, P.slot_species[T.slot[2]], E3);
+            fp = f_equilibrium(P, P.slot_species[T.slot[3]], Ep);
+        } else {
+            f1 = load_f(P, i1);
+            f2 = load_f(P, i2);
+            f3 = load_f(P, i3);
+            fp = load_f(P, a);
+        }
+        const R F1 = T.quark[0] ? R(1) - f1 : R(1) + f1;
+        const R F2 = T.quark[1] ? R(1) - f2 : R(1) + f2;
+        const R F3 = T.quark[2] ? R(1) - f3 : R(1) + f3;
+        const R Fp = T.quark[3] ? R(1) - fp : R(1) + fp;
+        const R gain = f1 * f2 * F3 * Fp;
+        const R W = gain - F1 * F2 * f3 * fp;
+        const R den = O::fabs_(J) * P.twopi5 * R(16) * E1 * E2 * E3 * Ep;
+        const R ct = (R)T.sym * W * M2 / den;
+        const R wq = ct * P.Kown;
+        if (!(O::fabs_(wq) < O::LIM)) {
+            red_add(&P.flags[1], 1);
+            continue;
+        }
+        if (P.audit) {
+            const double wa = (double)(ct * P.Kq);
+            atomicAdd(&P.audit[0], wa * (double)((Ep + E3) - (E1 + E2)));
+            atomicAdd(&P.audit[1], wa * (double)((G.p[0] + k3[0]) - (k1x + k2[0])));
+            atomicAdd(&P.audit[2], wa * (double)((G.p[1] + k3[1]) - (k1y + k2[1])));
+            atomicAdd(&P.audit[3], wa * (double)((G.p[2] + k3[2]) - (z + k2[2])));
+            atomicAdd(&P.audit[4], fabs(wa) * (double)(Ep + E3 + E1 + E2));
+            atomicAdd(&P.audit[5], 1.0);
+            atomicAdd(&P.audit[6], fabs(wa));
+        }
+        const long long q = O::rint_(wq);
+        if (q == 0) continue;
+        own += q;
+        if (P.sampler != 1) {
+            red_add(&P.A[i3], q);
+            red_add(&P.A[i1], -q);
+            red_add(&P.A[i2], -q);
+        }
+    }
+    return own;
+}
+
 // FP64 kernel: grid-stride over (anchor, sample) items, 32 consecutive items
 // per warp.
 template <typename R>
@@ -347,7 +471,10 @@ __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ Collide
             Geom<R> G;
             make_geom(P, a, smp, G, P.step);
             const int nt = P.nterms[G.d];
-            for (int ti = 0; ti < nt; ++ti) own += eval_term<R>(P, G, a, smp, ti);
+            if (P.param == 1)
+                for (int ti = 0; ti < nt; ++ti) own += eval_term_k3<R>(P, G, a, ti);
+            else
+                for (int ti = 0; ti < nt; ++ti) own += eval_term<R>(P, G, a, smp, ti);
         }
         if (warp_anchor) {
             own = warp_sum_ll(own);

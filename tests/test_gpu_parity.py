@@ -386,3 +386,32 @@ def test_argument_errors():
     h2, _ = make_pair(np_=(4, 4, 4), mass_mode=2)
     with pytest.raises(bz.BzError):
         h2.collision_term(st, A, 4)   # fixed masses not set
+
+
+K3_CASES = [
+    # np, mask, N, mass_mode, sampler
+    ((8, 8, 8), 0x01, 64, 0, 0),
+    ((6, 6, 6), 0x7F, 32, 0, 0),
+    ((6, 10, 8), 0x13, 33, 1, 1),
+]
+
+
+@pytest.mark.parametrize("np_,mask,N,mass_mode,sampler", K3_CASES)
+def test_collision_k3_parameterisation_bit_exact(np_, mask, N, mass_mode, sampler):
+    """The k3-eliminating form (bz_set_parameterisation(1)) of the FP64 path
+    equals the oracle's (run param 1) bit for bit; symmetric deposits sum to 0."""
+    from paper_1912_04457_gb300 import bz
+    torch = torch_mod()
+    h, cfg = make_pair(np_=np_, mask=mask, mass_mode=mass_mode)
+    h.set_parameterisation(1)
+    st = random_state(mask, 1, np_, 21)
+    A = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    h.collision_term(to_dev(st), A, N, 3, 0.01, bz.PREC_F64, sampler)
+    m2 = O.masses(cfg, st)
+    ref = O.collision(cfg, st, m2, N, step=3, dt=0.01, sampler=sampler, param=1)["A"]
+    got = A.cpu().numpy().reshape(ref.shape)
+    assert np.array_equal(got, ref)
+    if sampler == 0:
+        assert int(got.sum()) == 0
+    with pytest.raises(bz.BzError):
+        h.collision_term(to_dev(st), A, N, 3, 0.01, bz.PREC_F32, sampler)   # FP64 only
