@@ -100,6 +100,8 @@ typedef struct {
     double T;               /* temperature for analytic f, GeV                 */
     double mu[NSPEC];       /* chemical potentials for analytic f, GeV         */
     int32_t force;          /* 1: the drift includes the force term -div_p[(grad_x E) f] */
+    const struct bzo_urow_s* user;  /* user-defined |M|^2 rows (see msq_user), or NULL */
+    uint32_t umask;         /* bit r set: row r of the |M|^2 table is user-defined */
 } bzo_config;
 
 static int is_quark(int s) { return s != 0; }
@@ -198,7 +200,34 @@ static int terms_for(const bzo_config* c, int d, bzo_term* out)
 /* |M|^2 of the Appendix table, with t and u denominators regulated by */
 /* m_g^2, written literally.  SU(3): d_F = C_A = 3, C_F = 4/3, d_A = 8. */
 /* ------------------------------------------------------------------ */
-typedef struct { double A1, A2, A3, A4, A5; } bzo_mconst;
+/* A user-defined |M|^2 row (the API of Sec. II for the user's own matrix    */
+/* elements): sum over its n <= 8 terms of coef s^a t^b u^c / (s^d          */
+/* (t - m_g^2)^e (u - m_g^2)^f), e = (a, b, c, d, e, f), each power a       */
+/* product of its factors from 1, left to right.                            */
+typedef struct { double coef; uint8_t e[6]; uint8_t pad[2]; } bzo_uterm;
+typedef struct bzo_urow_s { int32_t n; int32_t pad; bzo_uterm t[8]; } bzo_urow;
+
+typedef struct { double A1, A2, A3, A4, A5; const bzo_urow* user; uint32_t umask; } bzo_mconst;
+
+static double upow(double x, int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r = r * x;
+    return r;
+}
+
+static double msq_user(const bzo_urow* row, double s, double t, double u, double mg2)
+{
+    double tm = t - mg2, um = u - mg2;
+    double acc = 0.0;
+    for (int k = 0; k < row->n; ++k) {
+        const bzo_uterm* T = &row->t[k];
+        double num = (upow(s, T->e[0]) * upow(t, T->e[1])) * upow(u, T->e[2]);
+        double den = (upow(s, T->e[3]) * upow(tm, T->e[4])) * upow(um, T->e[5]);
+        acc = acc + T->coef * (num / den);
+    }
+    return acc;
+}
 
 static bzo_mconst mconst(double alpha_s)
 {
@@ -211,11 +240,14 @@ static bzo_mconst mconst(double alpha_s)
     k.A3 = 8.0 * g4 * dF * CF * CF;
     k.A4 = 8.0 * g4 * dF * CF * CA;
     k.A5 = 16.0 * g4 * dA * CA * CA;
+    k.user = NULL;
+    k.umask = 0;
     return k;
 }
 
 static double msq(int cls, const bzo_mconst* k, double s, double t, double u, double mg2)
 {
+    if (k->user && (k->umask >> cls & 1u)) return msq_user(&k->user[cls], s, t, u, mg2);
     double tm = t - mg2, um = u - mg2;
     switch (cls) {
     case M_QQP:
@@ -243,6 +275,12 @@ double bzo_msq(int cls, double alpha_s, double s, double t, double u, double mg2
 {
     bzo_mconst k = mconst(alpha_s);
     return msq(cls, &k, s, t, u, mg2);
+}
+
+/* Exported for the user-row pins: one user-defined row at (s, t, u). */
+double bzo_msq_user(const bzo_urow* row, double s, double t, double u, double mg2)
+{
+    return msq_user(row, s, t, u, mg2);
 }
 
 /* ------------------------------------------------------------------ */
@@ -822,6 +860,8 @@ int bzo_collision(const bzo_config* c, const bzo_run* r, const int64_t* state, c
     if (audit) memset(audit, 0, 8 * sizeof(double));
     flags[0] = flags[1] = 0;
     bzo_mconst mk = mconst(c->alpha_s);
+    mk.user = c->user;
+    mk.umask = c->umask;
     double twoL = 2.0 * c->L;
     double V = twoL * twoL * twoL * twoL * twoL;
     /* weight of one root per leg, in units of 2^-40 of N f:

@@ -25,6 +25,7 @@ class Config(C.Structure):
         ("mass_mode", C.c_int32), ("analytic", C.c_int32),
         ("T", C.c_double), ("mu", C.c_double * NSPEC),
         ("force", C.c_int32),
+        ("user", C.c_void_p), ("umask", C.c_uint32),
     ]
 
 
@@ -51,6 +52,8 @@ def lib():
         _lib.bzo_philox4x32_10.argtypes = [P, P, P]
         _lib.bzo_msq.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib.bzo_msq.restype = C.c_double
+        _lib.bzo_msq_user.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double]
+        _lib.bzo_msq_user.restype = C.c_double
         _lib.bzo_roots.argtypes = [P, C.c_double, P, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_double, P]
         _lib.bzo_two_body_sum.argtypes = [P, C.c_double, P, C.c_double, C.c_double, C.c_double,
@@ -75,8 +78,33 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+# user-defined |M|^2 rows: 7 rows of (n, pad, 8 x (coef, a, b, c, d, e, f, pad, pad))
+UTERM = np.dtype([("coef", "<f8"), ("e", "u1", (6,)), ("pad", "u1", (2,))])
+UROW = np.dtype([("n", "<i4"), ("pad", "<i4"), ("t", UTERM, (8,))])
+
+
+def user_table(rows):
+    """rows: {row index: [(coef, (a, b, c, d, e, f)), ...]} -> (structured array of 7 rows, mask)."""
+    tab = np.zeros(7, dtype=UROW)
+    mask = 0
+    for r, terms in rows.items():
+        assert 0 <= r < 7 and 0 < len(terms) <= 8
+        tab[r]["n"] = len(terms)
+        for k, (c, e) in enumerate(terms):
+            tab[r]["t"][k]["coef"] = c
+            tab[r]["t"][k]["e"] = e
+        mask |= 1 << r
+    return tab, mask
+
+
+def msq_user(terms, s, t, u, mg2):
+    tab, _ = user_table({0: terms})
+    return lib().bzo_msq_user(tab.ctypes.data_as(C.c_void_p), s, t, u, mg2)
+
+
 def make_config(nx=(1, 1, 1), dx=1.0, np_=(20, 20, 20), L=2.0, seed=1, box=0,
-                species_mask=1, alpha_s=0.3, mass_mode=0, analytic=False, T=0.5, mu=None, force=False):
+                species_mask=1, alpha_s=0.3, mass_mode=0, analytic=False, T=0.5, mu=None, force=False,
+                user_rows=None):
     c = Config()
     c.nx[:] = list(nx)
     c.dx = dx
@@ -91,6 +119,9 @@ def make_config(nx=(1, 1, 1), dx=1.0, np_=(20, 20, 20), L=2.0, seed=1, box=0,
     c.T = T
     c.mu[:] = list(mu) if mu is not None else [0.0] * NSPEC
     c.force = 1 if force else 0
+    if user_rows:
+        c._user_keep, c.umask = user_table(user_rows)
+        c.user = c._user_keep.ctypes.data
     return c
 
 
