@@ -197,6 +197,19 @@ int bz_clear_flags(bz_handle h);
  * Errors: BZ_EINVAL for other values. */
 int bz_set_uniform_bits(bz_handle h, int32_t bits);
 
+/* User-defined matrix elements (Sec. II: the API for the user's own |M|^2;
+ * the Appendix table is the default).  Replaces row `row` of the |M|^2
+ * table (0 q_a q_b -> q_a q_b, 1 q q -> q q, 2 q qb -> q qb, 3 q_a qb_a ->
+ * q_b qb_b, 4 q qb -> g g (and g g -> q qb), 5 q g -> q g, 6 g g -> g g) for
+ * every term that uses it, on the FP64 and FP32 paths, by
+ *   |M|^2 = sum_k coef[k] s^a t^b u^c / (s^d (t - m_g^2)^e (u - m_g^2)^f),
+ * (a, b, c, d, e, f) = exps[6k .. 6k+5], each in [0, 4]; 1 <= nterms <= 8
+ * (host arrays, copied).  nterms = 0 restores the default row.  The FP32
+ * path uses the FP32 rounding of each coefficient.  The batched ensemble
+ * always uses the default table.  Errors: BZ_EINVAL for a bad row, count,
+ * exponent or a non-finite coefficient. */
+int bz_set_matrix_element(bz_handle h, int32_t row, int32_t nterms, const double* coef, const int32_t* exps);
+
 /* Which momentum the delta function of Eq. (delta function) eliminates
  * (Sec. III.A): which = 0 (default, the paper's choice) k2 = k3 + p - k1,
  * with (k1x, k1y, k3) sampled and k1z from E1 + E2 = E3 + Ep; which = 1

@@ -63,6 +63,7 @@ SIGNATURES = {
     "bz_set_uniform_bits": (C.c_int, [_P, _I32]),
     "bz_set_force_term": (C.c_int, [_P, _I32]),
     "bz_set_parameterisation": (C.c_int, [_P, _I32]),
+    "bz_set_matrix_element": (C.c_int, [_P, _I32, _I32, _P, _P]),
     "bz_energy_source": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "bz_set_equilibrium": (C.c_int, [_P, C.c_int, _D, _P]),
     "bz_profile": (C.c_int, [_P, C.c_int]),
@@ -180,6 +181,14 @@ class Handle:
 
     def set_uniform_bits(self, bits):
         self._check(self.lib.bz_set_uniform_bits(self.h, bits))
+
+    def set_matrix_element(self, row, terms):
+        """terms: [(coef, (a, b, c, d, e, f)), ...] (empty: default row)."""
+        coef = np.ascontiguousarray([c for c, _ in terms], dtype=np.float64)
+        exps = np.ascontiguousarray([e for _, e in terms], dtype=np.int32).reshape(-1)
+        self._check(self.lib.bz_set_matrix_element(self.h, row, len(terms),
+                                                   coef.ctypes.data_as(C.c_void_p) if len(terms) else None,
+                                                   exps.ctypes.data_as(C.c_void_p) if len(terms) else None))
 
     def set_parameterisation(self, which):
         """0: k2 eliminated (default), 1: k3 eliminated (FP64 path, uniform samples)."""

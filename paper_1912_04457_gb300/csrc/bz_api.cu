@@ -41,6 +41,9 @@ struct bz_handle_s {
     double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
     bool force = false;            // the drift includes the force term -div_p[(grad_x E) f]
     int param = 0;                 // FP64 collision: 0 k2 eliminated, 1 k3 eliminated
+    UserRow h_urows[MSQ_ROWS] = {};  // user-defined |M|^2 rows (host copy)
+    uint32_t umask = 0;
+    UserRow* d_urows = nullptr;
     double* d_audit = nullptr;     // bz_collision_audit sums (8)
     long long* d_sflags = nullptr; // state warnings (2): f < 0 cells, fermion f > 1 cells
     int f64_ubits = 32;            // uniform resolution of the FP64 path (32 or 23 bits)
@@ -161,6 +164,8 @@ static void free_scratch(bz_handle h)
     h->d_gforce = nullptr;
     cudaFree(h->d_m2prev);
     h->d_m2prev = nullptr;
+    cudaFree(h->d_urows);
+    h->d_urows = nullptr;
     cudaFree(h->d_audit);
     h->d_audit = nullptr;
     cudaFree(h->d_sflags);
@@ -358,6 +363,36 @@ extern "C" int bz_set_uniform_bits(bz_handle h, int32_t bits)
     if (!h) return BZ_EINVAL;
     if (bits != 32 && bits != 23) return fail(h, BZ_EINVAL, "uniform bits must be 32 or 23");
     h->f64_ubits = bits;
+    return BZ_OK;
+}
+
+extern "C" int bz_set_matrix_element(bz_handle h, int32_t row, int32_t nterms, const double* coef,
+                                     const int32_t* exps)
+{
+    if (!h) return BZ_EINVAL;
+    if (row < 0 || row >= MSQ_ROWS) return fail(h, BZ_EINVAL, "|M|^2 row must be in [0, %d)", MSQ_ROWS);
+    if (nterms < 0 || nterms > 8) return fail(h, BZ_EINVAL, "a user row has 0 to 8 terms");
+    if (nterms > 0 && (!coef || !exps)) return fail(h, BZ_EINVAL, "null coefficients or exponents");
+    UserRow r{};
+    r.n = nterms;
+    for (int k = 0; k < nterms; ++k) {
+        if (!std::isfinite(coef[k])) return fail(h, BZ_EINVAL, "coefficient %d is not finite", k);
+        r.t[k].coef = coef[k];
+        r.t[k].coef32 = (float)coef[k];
+        for (int i = 0; i < 6; ++i) {
+            const int e = exps[6 * k + i];
+            if (e < 0 || e > 4) return fail(h, BZ_EINVAL, "exponent %d of term %d outside [0, 4]", i, k);
+            r.t[k].e[i] = (uint8_t)e;
+        }
+    }
+    if (!h->d_urows && cudaMalloc(&h->d_urows, sizeof(UserRow) * MSQ_ROWS) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the |M|^2 table");
+    h->h_urows[row] = r;
+    if (nterms > 0)
+        h->umask |= 1u << row;
+    else
+        h->umask &= ~(1u << row);
+    CK(h, cudaMemcpy(h->d_urows, h->h_urows, sizeof(UserRow) * MSQ_ROWS, cudaMemcpyHostToDevice));
     return BZ_OK;
 }
 
@@ -650,6 +685,8 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.analytic = h->analytic;
     a.p_center = 0;
     a.param = sizeof(R) == sizeof(double) ? h->param : 0;
+    a.urows = h->d_urows;
+    a.umask = h->d_urows ? h->umask : 0u;
     a.T = (R)h->T;
     for (int s = 0; s < NSPEC; ++s) a.mu[s] = (R)h->mu[s];
     a.Kq = (R)Kq;

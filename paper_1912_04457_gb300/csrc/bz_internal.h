@@ -70,6 +70,21 @@ __host__ __device__ __forceinline__ uint32_t udiv(uint32_t n, DivMagic dm)
     return (uint32_t)(((unsigned long long)n * dm.m) >> dm.s);
 }
 
+// User-defined |M|^2 row: sum over n <= 8 terms of coef s^a t^b u^c /
+// (s^d (t - m_g^2)^e (u - m_g^2)^f), e = (a, b, c, d, e, f) in [0, 4]
+// (coef32: its FP32 rounding, used by the FP32 path).
+struct UserTerm {
+    double coef;
+    float coef32;
+    uint8_t e[6];
+    uint8_t pad[2];
+};
+struct UserRow {
+    int n, pad;
+    UserTerm t[8];
+};
+constexpr int MSQ_ROWS = 7;
+
 template <typename R>
 struct CollideArgs {
     const void* f;          // f per cell [slot][x][p] (unused in equilibrium mode)
@@ -90,6 +105,8 @@ struct CollideArgs {
     int64_t n_sel, a_stride, a_offset;
     int sampler, mass_mode, analytic, p_center;
     int param;              // FP64 path: 0 k2 eliminated (the paper's choice), 1 k3 eliminated
+    const UserRow* urows;   // [MSQ_ROWS] device table of user-defined |M|^2 rows, or null
+    uint32_t umask;         // bit r: row r of the |M|^2 table is user-defined
     R T, mu[NSPEC];
     R Kq, Kown, twopi5;
     R A1, A2, A3, A4, A5;

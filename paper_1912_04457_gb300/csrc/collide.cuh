@@ -77,9 +77,36 @@ __device__ __forceinline__ int bin_of(R k, R L, R dp, int n)
 template <typename R>
 __device__ __forceinline__ bool in_box(R k, R L) { return k >= -L && k < L; }
 
+// A user-defined row: terms in order, each power a product of its factors
+// from 1 left to right.
+template <typename R>
+__device__ __forceinline__ R upow(R x, int n)
+{
+    R r = R(1);
+    for (int i = 0; i < n; ++i) r = r * x;
+    return r;
+}
+
+template <typename R>
+__device__ __forceinline__ R msq_user(const UserRow* row, R s, R t, R u, R mg2)
+{
+    const R tm = t - mg2, um = u - mg2;
+    R acc = R(0);
+    const int n = row->n;
+    for (int k = 0; k < n; ++k) {
+        const UserTerm& T = row->t[k];
+        const R num = (upow(s, T.e[0]) * upow(t, T.e[1])) * upow(u, T.e[2]);
+        const R den = (upow(s, T.e[3]) * upow(tm, T.e[4])) * upow(um, T.e[5]);
+        const R c = sizeof(R) == sizeof(double) ? (R)T.coef : (R)T.coef32;
+        acc = acc + c * (num / den);
+    }
+    return acc;
+}
+
 template <typename R>
 __device__ __forceinline__ R msq(int cls, const CollideArgs<R>& P, R s, R t, R u, R mg2)
 {
+    if ((P.umask >> cls) & 1u) return msq_user<R>(P.urows + cls, s, t, u, mg2);
     R tm = t - mg2, um = u - mg2;
     switch (cls) {
     case M_QQP:
