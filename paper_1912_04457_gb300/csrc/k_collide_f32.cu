@@ -629,17 +629,22 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
 }
 
 // ---------------------------------------------------------------------------
-// Re-evaluation of a queued (anchor, sample, term) of the uniform sampler.
-// What made the term ill-conditioned, or put a solved coordinate on a bin
-// edge, is redone in FP64: the sample point from the same Philox words, E,
-// D, kappa, H, the roots and their validity, box and bin decisions (the
-// sampled legs' bins are the exact integer ones).  From the accepted roots
-// on (s, t, u in FP64; |M|^2, W and c~ in FP32) it is an ordinary term of
-// the FP32 path.  Returns the anchor's +q.
+// Re-evaluation of a queued (anchor, sample, term).  What made the term
+// ill-conditioned, or put a solved coordinate on a bin edge, is redone in
+// float-float arithmetic (about 48 bits, FP32 instructions only; FP64 issues
+// at 1/64 of the FP32 rate here): the sample point from the same Philox
+// words (the uniform sampler's exactly; the learned one's inverse-CDF
+// transform and weight in FP64), E, D, kappa, H, the roots and
+// their validity, box and bin decisions (the uniform sampler's sampled legs
+// take the exact integer bins), E1, s, t and u.  From the accepted roots on
+// (|M|^2, W and c~ in FP32) it is an ordinary term of the FP32 path.
+// Returns the anchor's +q.  Not inlined: the single-box and the batch fixup
+// kernels call one compiled body, so a queued term gives the same bits in
+// both.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int bin64(double k, double L, double dp, int n)
+__device__ __forceinline__ int bin_ff(ff k, ff L, ff dp, int n)
 {
-    int j = (int)floor((k + L) / dp);
+    int j = ff_floor(ff_div(ff_add(k, L), dp));
     j = j < 0 ? 0 : j;
     return j >= n ? n - 1 : j;
 }
@@ -653,187 +658,8 @@ struct PropCache {
 };
 
 template <bool LEARNED>
-__device__ long long fixup_term(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step, PropCache& pc)
-{
-    const int64_t nxc = P.nxc, npc = P.npc;
-    const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
-    const uint32_t rem = (uint32_t)a - sl_u * (uint32_t)(nxc * npc);
-    const uint32_t x_u = udiv(rem, P.dv_npc);
-    const int sl = (int)sl_u;
-    const int64_t x = x_u;
-    const int j = (int)(rem - x_u * (uint32_t)npc);
-    const int d = P.slot_species[sl];
-    const uint32_t jx_u = udiv((uint32_t)j, P.dv_yz);
-    const uint32_t ryz = (uint32_t)j - jx_u * (uint32_t)(P.np[1] * P.np[2]);
-    const uint32_t jy_u = udiv(ryz, P.dv_z);
-    const int jx = (int)jx_u, jy = (int)jy_u, jz = (int)(ryz - jy_u * (uint32_t)P.np[2]);
-    const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
-    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-    auto u23 = [](uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); };
-    const double L = P.L64, twoL = 2.0 * P.L64;
-    const double p0 = (-L + ((double)jx + 0.5) * P.dp64[0]) + P.dp64[0] * (u23(r0.x) - 0.5);
-    const double p1 = (-L + ((double)jy + 0.5) * P.dp64[1]) + P.dp64[1] * (u23(r0.y) - 0.5);
-    const double p2 = (-L + ((double)jz + 0.5) * P.dp64[2]) + P.dp64[2] * (u23(r0.z) - 0.5);
-    double k1x, k1y, k30, k31, k32, wfac = 1.0;
-    int b1xy, lin3;
-    if (LEARNED) {
-        // the learned sample point in FP64: y = mu + sigma logit(Fa + u (Fb - Fa)) on logistic draws
-        // (F(y) = v there, so the density needs no exponential), y = 2u - 1 on uniform draws
-        if (pc.a != a) {
-            const float* pr = P.prop + a * 8;
-            for (int i = 0; i < 3; ++i) pc.mu[i] = pr[i];
-            pc.s3 = pr[3];
-            pc.s1 = pr[4];
-            pc.alpha = pr[5];
-            for (int c = 0; c < 4; ++c) {
-                const double mu = c == 0 ? 0.0 : pc.mu[c - 1], sg = c == 0 ? pc.s1 : pc.s3;
-                pc.Fa[c] = 1.0 / (1.0 + exp((1.0 + mu) / sg));
-                pc.cFb[c] = 1.0 / (1.0 + exp((1.0 - mu) / sg));
-                pc.D[c] = 1.0 / (1.0 + exp(-(1.0 - mu) / sg)) - pc.Fa[c];
-            }
-            pc.a = a;
-        }
-        const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
-                                       P.key0, P.key1);
-        const double uv[5] = {u23(r0.w), u23(r1.x), u23(r1.y), u23(r1.z), u23(r1.w)};
-        const bool uni = u23(r2.x) < pc.alpha;
-        double y[5], G = 1.0;
-        for (int i = 0; i < 5; ++i) {
-            const int c = i < 2 ? 0 : i - 1;
-            const double mu = i < 2 ? 0.0 : pc.mu[i - 2], sg = i < 2 ? pc.s1 : pc.s3;
-            double F, cF;
-            if (uni) {
-                y[i] = 2.0 * uv[i] - 1.0;
-                const double zz = (y[i] - mu) / sg, e = exp(-fabs(zz)), inv = 1.0 / (1.0 + e);
-                F = zz >= 0.0 ? inv : e * inv;
-                cF = zz >= 0.0 ? e * inv : inv;
-            } else {
-                F = pc.Fa[c] + uv[i] * pc.D[c];
-                cF = pc.cFb[c] + (1.0 - uv[i]) * pc.D[c];
-                y[i] = mu + sg * log(F / cF);
-                y[i] = y[i] < -1.0 ? -1.0 : (y[i] >= 1.0 ? 0.99999994 : y[i]);
-            }
-            G *= F * cF / (sg * pc.D[c]);
-        }
-        wfac = 1.0 / (32.0 * (pc.alpha / 32.0 + (1.0 - pc.alpha) * G));
-        k1x = L * y[0];
-        k1y = L * y[1];
-        k30 = L * y[2];
-        k31 = L * y[3];
-        k32 = L * y[4];
-        b1xy = bin64(k1x, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(k1y, L, P.dp64[1], P.np[1]);
-        lin3 = (bin64(k30, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(k31, L, P.dp64[1], P.np[1])) * P.np[2]
-               + bin64(k32, L, P.dp64[2], P.np[2]);
-    } else {
-        k1x = -L + twoL * u23(r0.w);
-        k1y = -L + twoL * u23(r1.x);
-        k30 = -L + twoL * u23(r1.y);
-        k31 = -L + twoL * u23(r1.z);
-        k32 = -L + twoL * u23(r1.w);
-        b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
-        lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
-    }
-    const double Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
-    const double bx = Px - k1x, by = Py - k1y;
-    if (!(bx >= -L && bx < L && by >= -L && by < L)) return 0;
-    const TermDev& T = P.terms[d][ti];
-    double mv[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) mv[i] = P.mass_mode == 1 ? 0.0 : P.m2[x * 4 + i];
-    const double mg2 = P.m2[x * 4];
-    const double ma2 = mv[T.mslot[0]], mb2 = mv[T.mslot[1]], mc2 = mv[T.mslot[2]], md2 = mv[T.mslot[3]];
-    const double Ep = sqrt(((p0 * p0 + p1 * p1) + p2 * p2) + md2);
-    const double E3 = sqrt(((k30 * k30 + k31 * k31) + k32 * k32) + mc2);
-    const double E = Ep + E3;
-    const double a2 = (k1x * k1x + k1y * k1y) + ma2;
-    const double b2 = (bx * bx + by * by) + mb2;
-    const double D = E * E - Pz * Pz;
-    const double kap = (E * E + a2 - b2 - Pz * Pz) * 0.5;
-    const double H = kap * kap - a2 * D;
-    if (!(D > 0.0) || !(H > 0.0)) return 0;
-    const double sqH = sqrt(H);
-    const double kp = kap * Pz, sq = E * sqH;
-    const double Q = kp >= 0.0 ? kp + sq : kp - sq;
-    if (Q == 0.0) return 0;
-    const double zr[2] = {Q / D, (E * E * a2 - kap * kap) / Q};
-    const double s = E * E - ((Px * Px + Py * Py) + Pz * Pz);
-    const double k13 = k1x * k30 + k1y * k31, k1p = k1x * p0 + k1y * p1;
-    const unsigned slot_stride = (unsigned)(nxc * npc), xoff = (unsigned)(x * npc);
-    const int b2xy = bin64(bx, L, P.dp64[0], P.np[0]) * P.np[1] + bin64(by, L, P.dp64[1], P.np[1]);
-    const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
-    long long own = 0;
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const double z = zr[r], dz = Pz - z;
-        const double e2E = kap + Pz * z;  // E2 E at a root: valid iff 0 < E2 < E
-        if (!(e2E > 0.0 && e2E < E * E)) continue;
-        if (!(z >= -L && z < L && dz >= -L && dz < L)) continue;
-        const double E1 = sqrt(a2 + z * z);
-        const double t = (ma2 + mc2) - 2.0 * (E1 * E3 - (k13 + z * k32));
-        const double uu = (ma2 + md2) - 2.0 * (E1 * Ep - (k1p + z * p2));
-        if (s <= 0.0 || t - mg2 >= 0.0 || uu - mg2 >= 0.0) {
-            red_add(&P.flags[0], 1);
-            continue;
-        }
-        const float M2 = msq<float>(T.cls, P, (float)s, (float)t, (float)uu, (float)mg2);
-        const int lin1 = b1xy * P.np[2] + bin64(z, L, P.dp64[2], P.np[2]);
-        const int lin2 = b2xy * P.np[2] + bin64(dz, L, P.dp64[2], P.np[2]);
-        const unsigned i1 = (unsigned)T.slot[0] * slot_stride + xoff + lin1;
-        const unsigned i2 = (unsigned)T.slot[1] * slot_stride + xoff + lin2;
-        const unsigned i3 = (unsigned)T.slot[2] * slot_stride + xoff + lin3;
-        float f1, f2, f3, fpp;
-        if (P.analytic) {
-            f1 = f_equilibrium(P, P.slot_species[T.slot[0]], (float)E1);
-            f2 = f_equilibrium(P, P.slot_species[T.slot[1]], (float)(E - E1));
-            f3 = f_equilibrium(P, P.slot_species[T.slot[2]], (float)E3);
-            fpp = f_equilibrium(P, d, (float)Ep);
-        } else {
-            const float* F = static_cast<const float*>(P.f);
-            f1 = __ldg(F + i1);
-            f2 = __ldg(F + i2);
-            f3 = __ldg(F + i3);
-            fpp = fp;
-        }
-        const float F1 = T.quark[0] ? 1.0f - f1 : 1.0f + f1;
-        const float F2 = T.quark[1] ? 1.0f - f2 : 1.0f + f2;
-        const float F3 = T.quark[2] ? 1.0f - f3 : 1.0f + f3;
-        const float Fp = T.quark[3] ? 1.0f - fpp : 1.0f + fpp;
-        const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
-        // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
-        const float den = (float)((double)P.twopi5 * 16.0 * sqH * E3 * Ep);
-        const float ct = (float)T.sym * W * M2 / den;
-        const float wq = ct * P.Kown * (LEARNED ? (float)wfac : 1.0f);
-        if (!(fabsf(wq) < 4611686018427387904.0f)) {
-            red_add(&P.flags[1], 1);
-            continue;
-        }
-        const long long q = rint_ll(wq);
-        if (q == 0) continue;
-        own += q;
-        if (P.sampler != 1) {
-            red_add(&P.A[i3], q);
-            red_add(&P.A[i1], -q);
-            red_add(&P.A[i2], -q);
-        }
-    }
-    return own;
-}
-
-// The same re-evaluation for the uniform sampler in float-float arithmetic
-// (about 48 bits, FP32 instructions only) instead of FP64: the sample point,
-// energies, D, kappa, H, the roots, validity, box and bin decisions, E1, s, t
-// and u.  Returns the anchor's +q.  Not inlined: the single-box and the batch
-// fixup kernels call one compiled body, so a queued term gives the same bits
-// in both.
-__device__ __forceinline__ int bin_ff(ff k, ff L, ff dp, int n)
-{
-    int j = ff_floor(ff_div(ff_add(k, L), dp));
-    j = j < 0 ? 0 : j;
-    return j >= n ? n - 1 : j;
-}
-
-__device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step)
+__device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int64_t a, int smp, int ti, int step,
+                                                PropCache& pc)
 {
     const int64_t nxc = P.nxc, npc = P.npc;
     const uint32_t sl_u = udiv((uint32_t)a, P.dv_slot);
@@ -860,13 +686,67 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
 #pragma unroll
     for (int i = 0; i < 3; ++i)
         p[i] = ff_add(ff_add(nL, ff_mul_f(dp[i], (float)jv[i] + 0.5f)), ff_mul_f(dp[i], uj[i] - 0.5f));
-    const ff k1x = ff_add(nL, ff_mul_f(twoL, u23(r0.w)));
-    const ff k1y = ff_add(nL, ff_mul_f(twoL, u23(r1.x)));
-    const ff k30 = ff_add(nL, ff_mul_f(twoL, u23(r1.y)));
-    const ff k31 = ff_add(nL, ff_mul_f(twoL, u23(r1.z)));
-    const ff k32 = ff_add(nL, ff_mul_f(twoL, u23(r1.w)));
-    const int b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
-    const int lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+    ff k1x, k1y, k30, k31, k32;
+    int b1xy, lin3;
+    float wfac = 1.0f;
+    if (LEARNED) {
+        // the learned sample point to FP64 accuracy (the integrand of a queued term is
+        // sensitive to it): y = mu + sigma logit(Fa + u (Fb - Fa)) on logistic draws (F(y) = v
+        // there, so the density needs no exponential), y = 2u - 1 on uniform draws
+        if (pc.a != a) {
+            const float* pr = P.prop + a * 8;
+            for (int i = 0; i < 3; ++i) pc.mu[i] = pr[i];
+            pc.s3 = pr[3];
+            pc.s1 = pr[4];
+            pc.alpha = pr[5];
+            for (int c = 0; c < 4; ++c) {
+                const double mu = c == 0 ? 0.0 : pc.mu[c - 1], sg = c == 0 ? pc.s1 : pc.s3;
+                pc.Fa[c] = 1.0 / (1.0 + exp((1.0 + mu) / sg));
+                pc.cFb[c] = 1.0 / (1.0 + exp((1.0 - mu) / sg));
+                pc.D[c] = 1.0 / (1.0 + exp(-(1.0 - mu) / sg)) - pc.Fa[c];
+            }
+            pc.a = a;
+        }
+        const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
+                                       P.key0, P.key1);
+        const double uv[5] = {u23(r0.w), u23(r1.x), u23(r1.y), u23(r1.z), u23(r1.w)};
+        const bool uni = (double)u23(r2.x) < pc.alpha;
+        double y[5], G = 1.0;
+        for (int i = 0; i < 5; ++i) {
+            const int c = i < 2 ? 0 : i - 1;
+            const double mu = i < 2 ? 0.0 : pc.mu[i - 2], sg = i < 2 ? pc.s1 : pc.s3;
+            double F, cF;
+            if (uni) {
+                y[i] = 2.0 * uv[i] - 1.0;
+                const double zz = (y[i] - mu) / sg, e = exp(-fabs(zz)), inv = 1.0 / (1.0 + e);
+                F = zz >= 0.0 ? inv : e * inv;
+                cF = zz >= 0.0 ? e * inv : inv;
+            } else {
+                F = pc.Fa[c] + uv[i] * pc.D[c];
+                cF = pc.cFb[c] + (1.0 - uv[i]) * pc.D[c];
+                y[i] = mu + sg * log(F / cF);
+                y[i] = y[i] < -1.0 ? -1.0 : (y[i] >= 1.0 ? 0.99999994 : y[i]);
+            }
+            G *= F * cF / (sg * pc.D[c]);
+        }
+        wfac = (float)(1.0 / (32.0 * (pc.alpha / 32.0 + (1.0 - pc.alpha) * G)));
+        k1x = ff_from_double(P.L64 * y[0]);
+        k1y = ff_from_double(P.L64 * y[1]);
+        k30 = ff_from_double(P.L64 * y[2]);
+        k31 = ff_from_double(P.L64 * y[3]);
+        k32 = ff_from_double(P.L64 * y[4]);
+        b1xy = bin_ff(k1x, L, dp[0], P.np[0]) * P.np[1] + bin_ff(k1y, L, dp[1], P.np[1]);
+        lin3 = (bin_ff(k30, L, dp[0], P.np[0]) * P.np[1] + bin_ff(k31, L, dp[1], P.np[1])) * P.np[2]
+               + bin_ff(k32, L, dp[2], P.np[2]);
+    } else {
+        k1x = ff_add(nL, ff_mul_f(twoL, u23(r0.w)));
+        k1y = ff_add(nL, ff_mul_f(twoL, u23(r1.x)));
+        k30 = ff_add(nL, ff_mul_f(twoL, u23(r1.y)));
+        k31 = ff_add(nL, ff_mul_f(twoL, u23(r1.z)));
+        k32 = ff_add(nL, ff_mul_f(twoL, u23(r1.w)));
+        b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+        lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2] + bin_word(r1.w, P.np[2]);
+    }
     const ff Px = ff_add(p[0], k30), Py = ff_add(p[1], k31), Pz = ff_add(p[2], k32);
     const ff bx = ff_sub(Px, k1x), by = ff_sub(Py, k1y);
     if (!(ff_ge(bx, nL) && ff_lt(bx, L) && ff_ge(by, nL) && ff_lt(by, L))) return 0;
@@ -940,7 +820,7 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
                                   __fmul_rn(__fmul_rn(__fmul_rn(F1, F2), f3), fpp));
         // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
         const float ct = __fdiv_rn(__fmul_rn(__fmul_rn((float)T.sym, W), M2), den0);
-        const float wq = __fmul_rn(ct, P.Kown);
+        const float wq = LEARNED ? __fmul_rn(__fmul_rn(ct, P.Kown), wfac) : __fmul_rn(ct, P.Kown);
         if (!(fabsf(wq) < 4611686018427387904.0f)) {
             red_add(&P.flags[1], 1);
             continue;
@@ -975,11 +855,7 @@ __global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ Colli
         const unsigned long long it = qitems[seg * qcap + i];
         const int64_t a = (int64_t)(it >> 24);
         const int smp = (int)((it >> 4) & 0xFFFFFu), ti = (int)(it & 0xFu);
-        long long own;
-        if constexpr (LEARNED)
-            own = fixup_term<true>(P, a, smp, ti, P.step, pc);
-        else
-            own = fixup_term_ff(P, a, smp, ti, P.step);
+        const long long own = fixup_term_ff<LEARNED>(P, a, smp, ti, P.step, pc);
         if (own != 0) red_add(&P.A[a], own);
     }
 }
@@ -998,7 +874,8 @@ __global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float
         const unsigned long long it = qitems[seg * qcap + i];
         const CollideArgs<float>& P = boxes[(int)(it >> 48)];
         const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
-        const long long own = fixup_term_ff(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step);
+        PropCache pc;
+        const long long own = fixup_term_ff<false>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step, pc);
         if (own != 0) red_add(&P.A[a], own);
     }
 }
