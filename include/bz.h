@@ -385,8 +385,11 @@ int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, int32_t step,
  * float [nparams], device float loss), forward and backward on the tensor
  * cores.  Synchronises (to read sum w). */
 int bz_proposal_grad(bz_handle h, const void* records, int64_t n, float* grad, float* loss, void* stream);
-/* steps Adam steps (lr, beta 0.9/0.999) on consecutive batches of `batch`
- * records (wrapping); losses_host (may be NULL) receives each step's loss. */
+/* steps Adam steps (lr, beta 0.9/0.999), each on a minibatch of `batch`
+ * records drawn independently and uniformly from records [0, n) (index
+ * SplitMix64(key_step + i) mod n, key_step from the handle's Adam step
+ * count), so the minibatches do not follow the arrival order of the
+ * records; losses_host (may be NULL) receives each step's loss. */
 int bz_proposal_train(bz_handle h, const void* records, int64_t n, int32_t steps, int32_t batch, double lr,
                       float* losses_host, void* stream);
 /* Runs the network for every anchor of h (8 floats each: mu3 x3, sigma3,

@@ -1600,18 +1600,18 @@ extern "C" int bz_proposal_train(bz_handle h, const void* records, int64_t n, in
     const ProposalArgs A = prop_args(h);
     const int np = mlp_nparam();
     CK(h, cudaMemsetAsync(h->d_prop_g, 0, sizeof(float) * np, s));
-    int64_t off = 0;
+    // each step's minibatch: b records drawn independently and uniformly from all n
+    // (the record buffer is in arrival order, i.e. clustered by anchor)
     for (int k = 0; k < steps; ++k) {
-        int64_t b = std::min<int64_t>(batch, n);
-        if (off + b > n) off = 0;
+        const int64_t b = batch;
         CK(h, cudaMemsetAsync(h->d_loss, 0, sizeof(float), s));
         const int64_t nch = (b + 63) / 64;
         const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
-        CK(h, launch_mlp_grad(h->d_prop, A, rec + off, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss,
-                              grid, s));
+        const uint64_t key = ((uint64_t)(h->adam_step + 1) << 32) * 0x9E3779B97F4A7C15ull;
+        CK(h, launch_mlp_grad(h->d_prop, A, rec, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss, grid,
+                              s, n, key));
         CK(h, launch_adam(h->d_prop, h->d_prop_g, h->d_prop_m, h->d_prop_v, np, (float)lr, ++h->adam_step, s));
         if (losses_host) CK(h, cudaMemcpyAsync(&losses_host[k], h->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-        off += b;
     }
     if (losses_host) CK(h, cudaStreamSynchronize(s));
     h->anchor_prm_ready = false;

@@ -239,8 +239,11 @@ __host__ __device__ inline int64_t f32_units(int64_t n_sel, int nsamples)
     return n_sel * ((nchunk + F32_GROUP - 1) / F32_GROUP);
 }
 int mlp_nparam();
+// ntot > 0: minibatch position r reads record splitmix64(key + r) mod ntot of rec
+// (i.i.d. draws from all ntot records); ntot = 0: records [0, n) in order
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
-                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s);
+                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s, int64_t ntot = 0,
+                            uint64_t key = 0);
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
 cudaError_t launch_mlp_infer(const float* params, const ProposalArgs& A, int64_t nanchor, float* out, int grid,
                              cudaStream_t s);

@@ -190,9 +190,20 @@ struct TrainSmem {
 // One gradient evaluation over records [0, n): grad (FP32, NPARAM) += dL/dtheta
 // with L = -sum w log q / wsum, and loss_sum += L.  Each block walks chunks of
 // CH records and keeps its weight-gradient tiles in registers.
+// SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mix.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ params, const ProposalArgs A,
                                                      const ProposalRecord* __restrict__ rec, int64_t n, float inv_wsum,
-                                                     float* __restrict__ grad, float* loss_sum)
+                                                     float* __restrict__ grad, float* loss_sum, int64_t ntot,
+                                                     uint64_t key)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -216,7 +227,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ p
             const int64_t r = c * CH + threadIdx.x;
             float f[NIN];
             if (r < n) {
-                const ProposalRecord R = rec[r];
+                const int64_t ri = ntot > 0 ? (int64_t)(splitmix64(key + (uint64_t)r) % (uint64_t)ntot) : r;
+                const ProposalRecord R = rec[ri];
                 anchor_features(A, R.a, f);
                 for (int i = 0; i < 5; ++i) S.yv[threadIdx.x * 5 + i] = R.y[i];
                 S.wv[threadIdx.x] = R.w * inv_wsum;
@@ -480,7 +492,8 @@ cudaError_t launch_sum_weights(const ProposalRecord* rec, int64_t n, double* out
 int mlp_nparam() { return NPARAM; }
 
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
-                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s)
+                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s, int64_t ntot,
+                            uint64_t key)
 {
     const size_t smem = sizeof(TrainSmem);
     static bool attr = false;
@@ -489,7 +502,7 @@ cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const Pr
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_mlp_grad<<<grid, 256, smem, s>>>(params, A, rec, n, inv_wsum, grad, loss);
+    k_mlp_grad<<<grid, 256, smem, s>>>(params, A, rec, n, inv_wsum, grad, loss, ntot, key);
     return cudaGetLastError();
 }
 
