@@ -3,7 +3,7 @@
 
 One step = one pass of the whole hot path on the workload: thermal masses,
 drift (+ f for the lookups), collision sampling and deposition (FP32
-integrand with FP64 re-evaluation of ill-conditioned terms), moments.
+integrand with float-float re-evaluation of ill-conditioned terms), moments.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bz|reference]
                   [--workload qgp|gluon_step|gluon_bump]

@@ -181,7 +181,7 @@ int bz_reset_masses(bz_handle h);
 /* Counters (host int64 [4], synchronising): [0] roots dropped because a
  * regulated denominator t - m_g^2 or u - m_g^2 was >= 0 or s <= 0, [1]
  * deposits whose fixed-point weight exceeded 2^62, [2] mass fixed-point
- * overflows, [3] FP32-path terms that found the FP64 re-evaluation queue
+ * overflows, [3] FP32-path terms that found the re-evaluation queue
  * full (kept in FP32).  bz_clear_flags zeroes them and the state warnings. */
 int bz_get_flags(bz_handle h, int64_t* flags_host);
 /* State warnings (host int64 [2], synchronising), added up by every moments

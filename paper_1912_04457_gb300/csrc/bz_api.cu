@@ -723,8 +723,9 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         CK(h, launch_collide_f64(a, (int)blocks, s));
         return BZ_OK;
     }
-    // FP32 integrand, one warp per (anchor, 32 samples) unit; ill-conditioned
-    // terms queued per warp for FP64.  Cell indices are 32-bit there.
+    // FP32 integrand, one warp per unit (an anchor and up to 256 of its samples);
+    // ill-conditioned terms queued per warp for the float-float re-evaluation.
+    // Cell indices are 32-bit there.
     if (h->ncell >= (int64_t)1 << 31)
         return fail(h, BZ_EINVAL, "the FP32 path needs fewer than 2^31 cells (has %lld)", (long long)h->ncell);
     const int64_t units = f32_units(n_sel, nsamples);
@@ -760,7 +761,7 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         ProfScope ps(h, BZ_K_COLLIDE, s);
         CK(h, launch_collide_f32(a, (int)blocks, s));
     }
-    {  // FP64 sample point and root solve, FP32 integrand
+    {  // float-float sample point and root solve, FP32 integrand
         ProfScope ps(h, BZ_K_FIXUP, s);
         CK(h, launch_fixup_f32(a, (int)warps, s));
     }
@@ -1087,7 +1088,7 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
 // set, coupling and sample count, stepped together.  Per step: thermal
 // masses of every box (one launch), f of the concatenated state (one
 // launch), collision of every (box, anchor, 32 samples) unit in one
-// persistent launch with dynamic work distribution, FP64 fixup of queued
+// persistent launch with dynamic work distribution, float-float fixup of queued
 // terms, moments, and the end-of-step bookkeeping; the step is captured
 // once as a CUDA graph and replayed, the step index living in device memory.
 // The collision increment is deposited into the state in place: the kernels

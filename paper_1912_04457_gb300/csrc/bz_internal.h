@@ -120,7 +120,7 @@ struct CollideArgs {
     unsigned long long* rec_count;
     long long rec_cap;
     int rec_stride;  // 0: off; else units with index % rec_stride == 0 are recorded
-    // FP32 path: terms with |H| < tau kappa^2 are queued per warp for FP64
+    // FP32 path: terms with |H| < tau kappa^2 are queued per warp for re-evaluation
     // FP64 path: continuous-leg audit sums per accepted root, or null:
     // [0] sum w (Ep + E3 - E1 - E2), [1..3] sum w (p + k3 - k1 - k2), [4] sum |w| (Ep + E3 + E1 + E2),
     // [5] roots, [6] sum |w|; w = c~ Kq (unquantised)
@@ -223,7 +223,7 @@ cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, 
 #ifndef BZ_DEFER_TAU
 #define BZ_DEFER_TAU 2e-3
 #endif
-constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2 are re-evaluated in FP64
+constexpr double DEFER_TAU = BZ_DEFER_TAU;  // FP32 terms with |H| < tau kappa^2 are re-evaluated (float-float)
 #ifndef BZ_DEFER_CAP_DIV
 #define BZ_DEFER_CAP_DIV 50
 #endif

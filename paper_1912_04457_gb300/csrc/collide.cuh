@@ -20,8 +20,8 @@
 // of the inputs alone gives O(eps kappa^2 / H) relative error.  The FP32
 // kernel therefore queues every term with |H| < tau kappa^2 (about 0.3% of
 // the in-box terms at tau = 2e-3) and k_fixup_f32 redoes their sample point
-// and root solve in FP64 from the same Philox counter; deposits are still
-// exact integers.
+// and root solve in float-float arithmetic (about 48 bits) from the same
+// Philox counter; deposits are still exact integers.
 #pragma once
 #include <cstdint>
 #include "bz_internal.h"

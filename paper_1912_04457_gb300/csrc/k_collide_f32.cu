@@ -313,7 +313,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 bool v0 = false, v1 = false, defer = false;
                 z0 = z1 = sqH = 0.0f;
                 if (act && D > 0.0f) {
-                    // FP64 re-evaluation when the term is ill-conditioned
+                    // float-float re-evaluation when the term is ill-conditioned
                     // (|H| < tau kappa^2) or a solved coordinate sits on an edge
                     defer = may_defer && fabsf(H) < P.tau * (kap * kap);
                     if (H > 0.0f) {
@@ -344,7 +344,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 z0 = S.gz0[lane]; z1 = S.gz1[lane]; E3 = S.gE3[lane]; sqH = S.gsq[lane]; gfl = S.gfl[lane];
             }
             bool v0 = gfl & 1, v1 = (gfl >> 1) & 1;
-            if (gfl & 4) {  // queued for FP64; when the queue is full the FP32 roots stand
+            if (gfl & 4) {  // queued for re-evaluation; when the queue is full the FP32 roots stand
                 const int qs = atomicAdd(dq.s_count, 1);
                 if (qs < dq.cap) {
                     dq.seg[qs] = box_tag | ((unsigned long long)a << 24)
