@@ -415,3 +415,31 @@ def test_collision_k3_parameterisation_bit_exact(np_, mask, N, mass_mode, sample
         assert int(got.sum()) == 0
     with pytest.raises(bz.BzError):
         h.collision_term(to_dev(st), A, N, 3, 0.01, bz.PREC_F32, sampler)   # FP64 only
+
+
+def test_option_argument_errors():
+    """Option setters refuse values outside their domain."""
+    from paper_1912_04457_gb300 import bz
+    h, _ = make_pair(np_=(4, 4, 4))
+    for bad in (2, -1):
+        with pytest.raises(bz.BzError):
+            h._check(h.lib.bz_set_force_term(h.h, bad))   # the binding passes 0 or 1 only
+        with pytest.raises(bz.BzError):
+            h.set_parameterisation(bad)
+    with pytest.raises(bz.BzError):
+        h.set_uniform_bits(16)
+
+
+def test_f32_step_with_force_conserves_number():
+    """An FP32 step of an inhomogeneous box with the force term and thermal
+    masses: drift, force, collisions and the fixup together keep sum n exact."""
+    from paper_1912_04457_gb300 import bz
+    nx, np_, mask = (4, 3, 2), (8, 8, 8), 0x13
+    h, _ = make_pair(nx=nx, dx=0.2, np_=np_, mask=mask, mass_mode=0)
+    h.set_force_term(True)
+    st = random_state(mask, 24, np_, 31, 0.0, 0.5)
+    dev = to_dev(st)
+    h.step(dev, 0.01, 3, 64, bz.PREC_F32)
+    got = dev.cpu().numpy()
+    assert int(got.sum()) == int(st.sum())
+    assert not np.array_equal(got.reshape(st.shape), st)
