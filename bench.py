@@ -122,7 +122,7 @@ def ncu_traffic(workload):
 
 
 def term_counts(w):
-    """(term evaluations, terms per anchor averaged) of one step."""
+    """Term evaluations of one step: every sample of every anchor times its equation's terms."""
     from paper_1912_04457_gb300 import inputs as I
     per_species = []
     for s in I.slots(w.species_mask):
@@ -422,6 +422,8 @@ def run_bz(args):
             "dtype": "f32" if prec == bz.PREC_F32 else "f64", "data": "synthetic",
             "config": describe(w),
             "cell_updates_per_s": cell_updates,
+            "term_evaluations_per_s": whole_job_rate(terms, args.steps, world, t_max),
+            "accepted_roots_per_s": whole_job_rate(terms * rpt, args.steps, world, t_max),
             "wall_s_timed_loop": wall,
             "kernel_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
