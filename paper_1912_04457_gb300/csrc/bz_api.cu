@@ -39,6 +39,8 @@ struct bz_handle_s {
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
     double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
+    long long* d_mom_part = nullptr;  // moments: exact partial sums of the p-cell chunks
+    int64_t mom_part_cap = 0;
     bool force = false;            // the drift includes the force term -div_p[(grad_x E) f]
     int param = 0;                 // FP64 collision: 0 k2 eliminated, 1 k3 eliminated
     UserRow h_urows[MSQ_ROWS] = {};  // user-defined |M|^2 rows (host copy)
@@ -164,6 +166,9 @@ static void free_scratch(bz_handle h)
     h->d_gforce = nullptr;
     cudaFree(h->d_m2prev);
     h->d_m2prev = nullptr;
+    cudaFree(h->d_mom_part);
+    h->d_mom_part = nullptr;
+    h->mom_part_cap = 0;
     cudaFree(h->d_urows);
     h->d_urows = nullptr;
     cudaFree(h->d_audit);
@@ -808,7 +813,7 @@ static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long*
     return BZ_OK;
 }
 
-static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, double* out)
+static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, double* out, bool chunked = true)
 {
     a.state = state;
     a.out = out;
@@ -833,6 +838,24 @@ static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, doub
         const int sp = sl < h->nslots ? h->slot_species[sl] : 0;
         a.pauli[sl] = is_quark(sp) ? (long long)(kDeg[sp] * TWO_POW_40) : 0x7fffffffffffffffLL;
     }
+    // few (x cell, slot) rows: split each over blocks of >= 256 p cells so that every SM works
+    const int64_t rows = h->nxc * h->nslots;
+    int64_t nch = 1;
+    if (chunked && rows < 2 * (int64_t)h->nsm)
+        nch = std::min<int64_t>((2 * (int64_t)h->nsm + rows - 1) / rows, std::max<int64_t>(1, h->npc / 256));
+    if (nch > 1) {
+        const int64_t need = rows * nch * 10;
+        if (need > h->mom_part_cap) {
+            cudaFree(h->d_mom_part);
+            h->d_mom_part = nullptr;
+            h->mom_part_cap = 0;
+            if (cudaMalloc(&h->d_mom_part, sizeof(long long) * need) != cudaSuccess)
+                return fail(h, BZ_ENOMEM, "cannot allocate the moments scratch");
+            h->mom_part_cap = need;
+        }
+        a.part = h->d_mom_part;
+    }
+    a.nchunk = (int)nch;
     return BZ_OK;
 }
 
@@ -1008,7 +1031,7 @@ extern "C" int bz_moments(bz_handle h, const int64_t* state, double* out, void* 
     if (!h->have_masses && h->mass_mode == BZ_MASS_THERMAL)
         if ((rc = compute_masses(h, reinterpret_cast<const long long*>(state), s))) return rc;
     MomentArgs a{};
-    fill_moments(h, a, reinterpret_cast<const long long*>(state), out);
+    if ((rc = fill_moments(h, a, reinterpret_cast<const long long*>(state), out))) return rc;
     {
         ProfScope ps(h, BZ_K_MOMENTS, s);
         CK(h, launch_moments(a, s));
@@ -1028,7 +1051,7 @@ extern "C" int bz_energy_source(bz_handle h, const int64_t* state, const double*
     if (!h->have_masses && h->mass_mode == BZ_MASS_FIXED)
         return fail(h, BZ_EINVAL, "mass mode FIXED needs bz_set_masses first");
     MomentArgs a{};  // with the massless dispersion the masses are not read
-    fill_moments(h, a, reinterpret_cast<const long long*>(state), out);
+    fill_moments(h, a, reinterpret_cast<const long long*>(state), out, false);
     a.sflags = nullptr;
     a.dt = dt;
     if (m2_prev_host) {
@@ -1070,7 +1093,7 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
         if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, h->step_sampler, s))) return rc;
         if (moments_out) {
             MomentArgs m{};
-            fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5);
+            if ((rc = fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5))) return rc;
             ProfScope ps(h, BZ_K_MOMENTS, s);
             CK(h, launch_moments(m, s));
         }
@@ -1348,7 +1371,7 @@ static int batch_fill_args(bz_batch b, long long* state, double dt, cudaStream_t
         b->a32[i].tau = (float)DEFER_TAU;
         fill_masses(h, b->mass[i], st, b->d_acc + 4 * i, b->d_m2_cur + 4 * i,
                     h->mass_mode == BZ_MASS_MASSLESS ? nullptr : b->d_m2_prev + 4 * i);
-        fill_moments(h, b->mom[i], st, nullptr);
+        fill_moments(h, b->mom[i], st, nullptr, false);
     }
     CKB(b, cudaMemcpyAsync(b->d_a32, b->a32.data(), sizeof(CollideArgs<float>) * n, cudaMemcpyHostToDevice, s));
     CKB(b, cudaMemcpyAsync(b->d_mass, b->mass.data(), sizeof(MassArgs) * n, cudaMemcpyHostToDevice, s));

@@ -143,6 +143,7 @@ struct MassArgs {
     int slot_of[NSPEC];     // -1 if inactive
     double pref_g, pref_q, meas;
     long long limit;
+    int64_t chunk;          // bins per block (set by launch_masses)
 };
 
 struct DriftArgs {
@@ -187,6 +188,10 @@ struct MomentArgs {
     // energy source (k_energy_source): out is [x][slot][3], masses of the previous evaluation, dt
     const double* m2_prev;
     double dt;
+    // k_moments: p-cell chunks per (x cell, slot), and their exact partial sums
+    // ([x][slot][chunk][5] 128-bit as (lo, hi) int64 pairs) when nchunk > 1
+    int nchunk;
+    long long* part;
 };
 
 // Per-slot scales of the f conversion: FP64 degeneracy, and the FP32

@@ -42,9 +42,11 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
 // f and summed exactly.  Grid: one block per (x cell, chunk of 2048 bins).
 // ---------------------------------------------------------------------------
 constexpr int MASS_CHUNK = 2048;
+static int device_sms();
 
-// Fixed-point partial sums of one (x cell, chunk of MASS_CHUNK bins) block.
-__device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64_t c0, bool use_prev)
+// Fixed-point partial sums of one (x cell, chunk of `chunk` bins) block; the
+// block sums add into exact integers, so the chunking does not change them.
+__device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64_t c0, int64_t chunk, bool use_prev)
 {
     __shared__ double s_p[3][MAX_NP];  // cell-centre momenta, -L + (j + 1/2) dp
     for (int d = 0; d < 3; ++d)
@@ -63,7 +65,7 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
     const int np1 = P.np[1], np2 = P.np[2], np12 = np1 * np2;
     long long sg = 0, sq[3] = {0, 0, 0};
     bool ovf = false;
-    for (int64_t j = c0 + threadIdx.x; j < c0 + MASS_CHUNK && j < P.npc; j += blockDim.x) {
+    for (int64_t j = c0 + threadIdx.x; j < c0 + chunk && j < P.npc; j += blockDim.x) {
         const int jj = (int)j;  // npc < 2^31
         const double px = s_p[0][jj / np12], py = s_p[1][(jj / np2) % np1], pz = s_p[2][jj % np2];
         const double pp = (px * px + py * py) + pz * pz;
@@ -115,8 +117,8 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
 
 __global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs P)
 {
-    const int64_t nchunk = (P.npc + MASS_CHUNK - 1) / MASS_CHUNK;
-    masses_block(P, blockIdx.x / nchunk, (blockIdx.x % nchunk) * MASS_CHUNK, true);
+    const int64_t nchunk = (P.npc + P.chunk - 1) / P.chunk;
+    masses_block(P, blockIdx.x / nchunk, (blockIdx.x % nchunk) * P.chunk, P.chunk, true);
 }
 
 __device__ __forceinline__ int find_box(const int64_t* prefix, int nboxes, int64_t v)
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) k_masses_batch(const MassArgs* __restrict
                                                       const int* have_prev)
 {
     const int b = find_box(chunk_prefix, nboxes, blockIdx.x);
-    masses_block(boxes[b], 0, (blockIdx.x - chunk_prefix[b]) * MASS_CHUNK, *have_prev != 0);
+    masses_block(boxes[b], 0, (blockIdx.x - chunk_prefix[b]) * MASS_CHUNK, MASS_CHUNK, *have_prev != 0);
 }
 
 __global__ void k_masses_finish_batch(const MassArgs* __restrict__ boxes, int nboxes)
@@ -162,8 +164,13 @@ cudaError_t launch_masses(const MassArgs& a, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * a.nxc, s);
     if (e != cudaSuccess) return e;
-    const int64_t nchunk = (a.npc + MASS_CHUNK - 1) / MASS_CHUNK;
-    k_masses<<<(unsigned)(nchunk * a.nxc), 256, 0, s>>>(a);
+    // chunks of 256 to 2048 bins, enough blocks for every SM on small grids
+    MassArgs b = a;
+    const int64_t per_x = ((int64_t)4 * device_sms() + a.nxc - 1) / a.nxc;
+    int64_t chunk = ((a.npc + per_x - 1) / per_x + 255) / 256 * 256;
+    b.chunk = chunk < 256 ? 256 : (chunk > MASS_CHUNK ? MASS_CHUNK : chunk);
+    const int64_t nchunk = (a.npc + b.chunk - 1) / b.chunk;
+    k_masses<<<(unsigned)(nchunk * a.nxc), 256, 0, s>>>(b);
     k_masses_finish<<<(unsigned)((a.nxc + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -696,8 +703,18 @@ __device__ __forceinline__ double i128_to_double(__int128 v)
 #define BZ_MOM_MINB 4    // resident blocks per SM (register budget)
 #endif
 
-// Exact sums of one (x cell, slot); writes 5 doubles at o.
-__device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, int sl, double* o)
+// The 5 doubles of one (x cell, slot) from its exact sums.
+__device__ __forceinline__ void moments_out(const MomentArgs& P, const __int128* t, double* o)
+{
+    o[0] = i128_to_double(t[0]) * P.pref;
+    o[1] = i128_to_double(t[1]) * P.pref * (1.0 / 16777216.0);
+    for (int d = 0; d < 3; ++d) o[2 + d] = i128_to_double(t[2 + d]) * P.pref * P.half_dp[d];
+}
+
+// Exact sums of the cells [jlo, jhi) of one (x cell, slot): 5 doubles at o,
+// or, with part set, the 5 exact 128-bit sums (lo, hi words) at part.
+__device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, int sl, int jlo, int jhi, double* o,
+                                              long long* part)
 {
     __shared__ float s_pf[3][MAX_NP];  // cell-centre momenta (lanes index them at different cells)
     for (int d = 0; d < 3; ++d)
@@ -722,24 +739,24 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     long long kh[3] = {0, 0, 0};              // sum k_d nh
     __int128 e_wide = 0;                      // sum E_fx n of cells with E_fx >= 2^31 (exact, rare)
     constexpr int U = BZ_MOM_UNROLL;          // cells in flight per thread
-    for (int j0 = threadIdx.x; j0 < npc; j0 += U * (int)blockDim.x) {
+    for (int j0 = jlo + (int)threadIdx.x; j0 < jhi; j0 += U * (int)blockDim.x) {
         long long nv[U];
         int jpv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * (int)blockDim.x;
-            nv[u] = j < npc ? __ldg(&st[j]) : 0;
+            nv[u] = j < jhi ? __ldg(&st[j]) : 0;
             if (P.jtab) {
-                jpv[u] = j < npc ? __ldg(P.jtab + j) : 0;
+                jpv[u] = j < jhi ? __ldg(P.jtab + j) : 0;
             } else {
-                const int jj = j < npc ? j : 0, jxy = jj / np2;
+                const int jj = j < jhi ? j : 0, jxy = jj / np2;
                 jpv[u] = (jxy / np1) | ((jxy % np1) << 8) | ((jj % np2) << 16);
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = j0 + u * (int)blockDim.x;
-            if (j >= npc) break;
+            if (j >= jhi) break;
             const long long n = nv[u];
             const int jv[3] = {jpv[u] & 0xff, (jpv[u] >> 8) & 0xff, jpv[u] >> 16};
             const float pf0 = s_pf[0][jv[0]], pf1 = s_pf[1][jv[1]], pf2 = s_pf[2][jv[2]];
@@ -797,22 +814,52 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
         __int128 t[5] = {0, 0, 0, 0, 0};
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
             for (int i = 0; i < 5; ++i) t[i] += red[i][w];
-        o[0] = i128_to_double(t[0]) * P.pref;
-        o[1] = i128_to_double(t[1]) * P.pref * (1.0 / 16777216.0);
-        for (int d = 0; d < 3; ++d) o[2 + d] = i128_to_double(t[2 + d]) * P.pref * P.half_dp[d];
+        if (part) {  // exact partial sums of this chunk, combined by k_moments_finish
+            for (int i = 0; i < 5; ++i) {
+                part[2 * i] = (long long)(unsigned long long)t[i];
+                part[2 * i + 1] = (long long)(t[i] >> 64);
+            }
+        } else {
+            moments_out(P, t, o);
+        }
     }
 }
 
+// Block = (x cell, slot, chunk of the p cells); with one chunk the block
+// writes the moments, else its exact partial sums for k_moments_finish.
 __global__ void __launch_bounds__(256, BZ_MOM_MINB) k_moments(const __grid_constant__ MomentArgs P)
 {
-    const int64_t x = blockIdx.x / P.nslots;
-    const int sl = blockIdx.x % P.nslots;
-    moments_block(P, x, sl, P.out + (x * P.nslots + sl) * 5);
+    const int nch = P.nchunk > 1 ? P.nchunk : 1;
+    const int64_t row = blockIdx.x / nch;
+    const int c = (int)(blockIdx.x % nch);
+    const int64_t x = row / P.nslots;
+    const int sl = (int)(row % P.nslots);
+    const int jlo = (int)((int64_t)c * P.npc / nch), jhi = (int)((int64_t)(c + 1) * P.npc / nch);
+    moments_block(P, x, sl, jlo, jhi, P.out + (x * P.nslots + sl) * 5,
+                  nch > 1 ? P.part + (int64_t)blockIdx.x * 10 : nullptr);
+}
+
+// Adds the chunks' partial sums of each (x cell, slot) in chunk order.
+__global__ void k_moments_finish(const __grid_constant__ MomentArgs P)
+{
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= P.nxc * P.nslots) return;
+    __int128 t[5] = {0, 0, 0, 0, 0};
+    for (int c = 0; c < P.nchunk; ++c) {
+        const long long* q = P.part + (row * P.nchunk + c) * 10;
+        for (int i = 0; i < 5; ++i)
+            t[i] += (__int128)(((unsigned __int128)(unsigned long long)q[2 * i + 1] << 64) | (unsigned long long)q[2 * i]);
+    }
+    moments_out(P, t, P.out + row * 5);
 }
 
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s)
 {
-    k_moments<<<(unsigned)(a.nxc * a.nslots), 256, 0, s>>>(a);
+    const int nch = a.nchunk > 1 && a.part ? a.nchunk : 1;
+    MomentArgs b = a;
+    b.nchunk = nch;
+    k_moments<<<(unsigned)(a.nxc * a.nslots * nch), 256, 0, s>>>(b);
+    if (nch > 1) k_moments_finish<<<(unsigned)((a.nxc * a.nslots + 127) / 128), 128, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -936,7 +983,8 @@ __global__ void __launch_bounds__(256, BZ_MOM_MINB) k_moments_batch(const Moment
         const int mid = (lo + hi + 1) >> 1;
         if (slot_prefix[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    moments_block(boxes[lo], 0, (int)blockIdx.x - slot_prefix[lo], out + (int64_t)(*kidx) * per_step + 5 * (int64_t)blockIdx.x);
+    moments_block(boxes[lo], 0, (int)blockIdx.x - slot_prefix[lo], 0, (int)boxes[lo].npc,
+                  out + (int64_t)(*kidx) * per_step + 5 * (int64_t)blockIdx.x, nullptr);
 }
 
 cudaError_t launch_moments_batch(const MomentArgs* boxes, const int* slot_prefix, int nboxes, int nblocks,
