@@ -23,7 +23,8 @@
  *                                    elimination and the k1z root (Sec. III.A)
  *   Eqs. (MC C_gg), (ca), (small c relation) -- MC estimator and symmetrical
  *                                    sampling (Sec. III.B)
- *   Eq. (left handside)           -- conservative (flux) form of the drift (Sec. III)
+ *   Eq. (left handside)           -- conservative (flux) form of the drift and the force term (Sec. III)
+ *   Eq. (current conservation)    -- the energy source S_ex of a varying mass (Sec. II)
  *   Table (Matrix elements squared) -- |M|^2 (Appendix)
  *
  * Readings of the paper where it is silent (all listed in the design notes):
@@ -40,7 +41,9 @@
  *   - the mass integrals are summed exactly in 2^-30 fixed point, so their
  *     value does not depend on summation order.
  * Parity of the physical evolution curves (the paper's figures) is
- * unpinned: the figures are not available.
+ * unpinned: the figures are not available.  The -(1/4) m^2 I term of
+ * T_total (bzo_energy_source) is the product of the pinned I and the
+ * masses; beyond that its parity is unpinned.
  */
 #include <math.h>
 #include <stdint.h>
