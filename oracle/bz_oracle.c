@@ -32,7 +32,10 @@
  *   - each k1z root deposits to its own legs;
  *   - the anchor momentum p is jittered uniformly inside its cell;
  *   - the integration box is (k1x,k1y,k3) in [-L,L)^5; a root whose k1z or
- *     k2 leaves the box is rejected;
+ *     k2 leaves the box is rejected (run param 1: k3 eliminated instead,
+ *     (k1x,k1y,k2) sampled, the paper's second choice of Sec. III.A);
+ *   - user-defined |M|^2 rows are sums of terms c s^a t^b u^c /
+ *     (s^d (t - m_g^2)^e (u - m_g^2)^f) replacing rows of the table;
  *   - the drift is first-order upwind in flux form, periodic in x;
  *   - the optional force term is upwind in p with dE/dx = (dm^2/dx)/(2E),
  *     dm^2/dx a central difference, and no flux through the momentum-box
