@@ -362,7 +362,7 @@ def run_bz(args):
         drift_kernels = 2 if w.nxc > 1 else 1   # k_inv_energy + the drift kernel on inhomogeneous grids
         nsm_ = torch.cuda.get_device_properties(local).multi_processor_count
         # k_moments + k_moments_finish when few (x cell, slot) rows are split into p-cell chunks
-        mom_kernels = 2 if (w.nxc * w.nslots < 2 * nsm_ and w.npc // 256 > 1) else 1
+        mom_kernels = 2 if (w.nxc * w.nslots < 2 * nsm_ and w.npc // 1024 > 1) else 1
         launches = (2 * prof["masses"][1] + drift_kernels * prof["drift"][1] + prof["collide"][1]
                     + prof["fixup"][1] + mom_kernels * prof["moments"][1] + prof["convert"][1])
         # algorithmic work of one collision launch

@@ -838,11 +838,11 @@ static int fill_moments(bz_handle h, MomentArgs& a, const long long* state, doub
         const int sp = sl < h->nslots ? h->slot_species[sl] : 0;
         a.pauli[sl] = is_quark(sp) ? (long long)(kDeg[sp] * TWO_POW_40) : 0x7fffffffffffffffLL;
     }
-    // few (x cell, slot) rows: split each over blocks of >= 256 p cells so that every SM works
+    // few (x cell, slot) rows: split each over blocks of >= 1024 p cells so that every SM works
     const int64_t rows = h->nxc * h->nslots;
     int64_t nch = 1;
     if (chunked && rows < 2 * (int64_t)h->nsm)
-        nch = std::min<int64_t>((2 * (int64_t)h->nsm + rows - 1) / rows, std::max<int64_t>(1, h->npc / 256));
+        nch = std::min<int64_t>((2 * (int64_t)h->nsm + rows - 1) / rows, std::max<int64_t>(1, h->npc / 1024));
     if (nch > 1) {
         const int64_t need = rows * nch * 10;
         if (need > h->mom_part_cap) {
