@@ -572,7 +572,7 @@ static double uniform_of(uint32_t x, int ubits)
 /* |M|^2, W and the four deposits as in the k2 form, with the Jacobian   */
 /* of this root.                                                         */
 static void collide_sample_k3(const bzo_config* c, const bzo_run* r, const int64_t* state, const double* mdisp,
-                              double mg2reg, int d, int64_t x, const int jv[3], const double p[3], double k1x,
+                              double mg2reg, int64_t x, const int jv[3], const double p[3], double k1x,
                               double k1y, const double k2[3], const bzo_term* terms, int nterms, const bzo_mconst* mk,
                               double Kq, double Kown, double twopi5, int64_t* A, double* c64, double* g64,
                               double* audit, int64_t* flags)
@@ -734,7 +734,7 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
             for (int i = 0; i < 3; ++i) k3[i] = -L + twoL * u[5 + i];  /* k2 when param == 1 */
         }
         if (r->param == 1) {
-            collide_sample_k3(c, r, state, mdisp, mg2reg, d, x, jv, p, k1x, k1y, k3, terms, nterms, mk, Kq, Kown,
+            collide_sample_k3(c, r, state, mdisp, mg2reg, x, jv, p, k1x, k1y, k3, terms, nterms, mk, Kq, Kown,
                               twopi5, A, &c64, &g64, audit, flags);
             continue;
         }

@@ -191,12 +191,6 @@ constexpr int DRIFT_THREADS = 256;
 constexpr int DRIFT_PER_THREAD = 4;
 constexpr int DRIFT_TILE = DRIFT_THREADS * DRIFT_PER_THREAD;
 
-__device__ __forceinline__ long long courant_fx(float m, float pdf, float ppf, float dtdxf)
-{
-    const float inv = 1.0f / sqrtf(ppf + m);
-    const float cf = (pdf * inv) * dtdxf;
-    return rint_ll(cf * 1073741824.0f);
-}
 
 // floor((n C + 2^29) / 2^30) as an int64 (two's complement, like the exact
 // 128-bit product truncated to 64 bits).  For |C| < 2^31 the product splits
@@ -240,19 +234,9 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_inv_energy(const __grid_const
     }
 }
 
-// Narrow forms for |C| < 2^31 (every stable step: |c| <= dt/dx < 2): round to
-// int32, and n C split exactly into a signed 32 x 32 and an unsigned
-// 32 x 32 product, n = nh 2^32 + nl.
-__device__ __forceinline__ int rint_i32(float w)  // round half even, |w| < 2^31
-{
-    if (fabsf(w) < 4194304.0f) return __float_as_int(w + 12582912.0f) - 0x4B400000;
-    const unsigned b = __float_as_uint(w);
-    const int e = (int)((b >> 23) & 0xffu) - 150;  // w = m 2^e, e >= -1
-    const int m = (int)((b & 0x7fffffu) | 0x800000u);
-    const int v = e >= 0 ? m << e : (m >> 1) + ((m & 1) & ((m >> 1) & 1));
-    return (b >> 31) ? -v : v;
-}
-
+// Narrow form for |C| < 2^31 (every stable step: |c| <= dt/dx < 2): n C split
+// exactly into a signed 32 x 32 and an unsigned 32 x 32 product,
+// n = nh 2^32 + nl.
 __device__ __forceinline__ long long flux32(int nh, unsigned nl, int C)
 {
     const long long hi = (long long)nh * C;
@@ -351,7 +335,6 @@ __device__ __forceinline__ long long force_acc(const DriftArgs& P, const float* 
 template <bool NARROW>
 __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__ DriftArgs P)
 {
-    __shared__ float s_m[7];          // mass of this row's x cell, then (lower, upper) neighbour per axis
     __shared__ long long s_off[6];    // cell offsets of the (lower, upper) neighbour rows per axis
     __shared__ float s_pf[3][MAX_NP]; // cell-centre momenta (lanes index them at different cells)
     for (int d = 0; d < 3; ++d)
@@ -360,20 +343,14 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
     const int sl = (int)(row / P.nxc);
     const int64_t x = row - (int64_t)sl * P.nxc;
     const int ms = P.slot_mslot[sl];
-    if (threadIdx.x < 7) {
-        int64_t xn = x;
-        if (threadIdx.x > 0) {
-            const int d = (threadIdx.x - 1) >> 1, up = (threadIdx.x - 1) & 1;
-            const int64_t xs = d == 0 ? (int64_t)P.nx[1] * P.nx[2] : (d == 1 ? (int64_t)P.nx[2] : 1);
-            const int xi = (int)((x / xs) % P.nx[d]);
-            const int64_t step = up ? (xi == P.nx[d] - 1 ? 1 - P.nx[d] : 1) : (xi == 0 ? P.nx[d] - 1 : -1);
-            xn = x + step * xs;
-            s_off[threadIdx.x - 1] = (xn - x) * P.npc;
-        }
-        s_m[threadIdx.x] = P.mass_mode == 1 ? 0.0f : (float)P.m2[xn * 4 + ms];
+    if (threadIdx.x < 6) {
+        const int d = threadIdx.x >> 1, up = threadIdx.x & 1;
+        const int64_t xs = d == 0 ? (int64_t)P.nx[1] * P.nx[2] : (d == 1 ? (int64_t)P.nx[2] : 1);
+        const int xi = (int)((x / xs) % P.nx[d]);
+        const int64_t step = up ? (xi == P.nx[d] - 1 ? 1 - P.nx[d] : 1) : (xi == 0 ? P.nx[d] - 1 : -1);
+        s_off[threadIdx.x] = step * xs * P.npc;
     }
     __syncthreads();
-    const float m_own = s_m[0];
     const long long* in_row = P.in + row * P.npc;
     long long* out_row = P.out + row * P.npc;
     const int npc = (int)P.npc;
@@ -385,7 +362,6 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
         const long long ncj = __ldg(in_row + j);
         const int jp = __ldg(P.jtab + j);
         const float pf[3] = {s_pf[0][jp & 0xff], s_pf[1][(jp >> 8) & 0xff], s_pf[2][jp >> 16]};
-        const float ppf = (pf[0] * pf[0] + pf[1] * pf[1]) + pf[2] * pf[2];
         long long acc = 0;
         if (NARROW && P.inv_e) {
             const float* ie_row = P.inv_e + row * P.npc;
@@ -395,10 +371,10 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (P.nx[d] == 1) continue;
-                const int own_C = rint_i32(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
+                const int own_C = rint_split(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
                 const long long off = s_off[2 * d + (pf[d] > 0.0f ? 0 : 1)];  // the upwind neighbour
                 const long long nn = __ldg(in_row + off + j);
-                const int nb_C = rint_i32(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
+                const int nb_C = rint_split(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
                 const long long f_own = flux32(nh, nl, own_C), f_nb = flux32((int)(nn >> 32), (unsigned)nn, nb_C);
                 // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down
                 acc += pf[d] > 0.0f ? f_own - f_nb : f_nb - f_own;
@@ -418,27 +394,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
                 acc += pf[d] > 0.0f ? flux_fx(ncj, own_C) - flux_fx(nn, nb_C) : flux_fx(nn, nb_C) - flux_fx(ncj, own_C);
             }
             if (P.force) acc += force_acc(P, P.gforce + (x * 4 + ms) * 3, jp, j, in_row, ie_row, ncj, inv);
-        } else {
-            bool own_done = false;
-            long long own_C[3] = {0, 0, 0};
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (P.nx[d] == 1) continue;
-                if (!own_done) {
-                    const float inv = 1.0f / sqrtf(ppf + m_own);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) own_C[e] = rint_ll(((pf[e] * inv) * P.dtdxf) * 1073741824.0f);
-                    own_done = true;
-                }
-                if (pf[d] > 0.0f) {  // inflow through the lower face from the lower neighbour
-                    const long long nn = __ldg(in_row + s_off[2 * d] + j);
-                    acc += flux_fx(ncj, own_C[d]) - flux_fx(nn, courant_fx(s_m[1 + 2 * d], pf[d], ppf, P.dtdxf));
-                } else {             // inflow through the upper face from the upper neighbour
-                    const long long nn = __ldg(in_row + s_off[2 * d + 1] + j);
-                    acc += flux_fx(nn, courant_fx(s_m[2 + 2 * d], pf[d], ppf, P.dtdxf)) - flux_fx(ncj, own_C[d]);
-                }
-            }
-        }
+        }  // without inverse energies (one x cell) nothing moves: n^{n+1} = n^n
         out_row[j] = ncj - acc;
         if (P.freal) {
             const int64_t cell = row * P.npc + j;
@@ -583,7 +539,8 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
     const int64_t tiles = (a.npc + DRIFT_TILE - 1) / DRIFT_TILE;
     if (rows < 1 || rows > 2147483647LL || tiles > 65535) return cudaErrorInvalidConfiguration;
     const bool moving = a.nx[0] > 1 || a.nx[1] > 1 || a.nx[2] > 1;
-    if (a.inv_e && moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
+    if (moving && !a.inv_e) return cudaErrorInvalidValue;  // the drift kernels read the inverse energies
+    if (moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
     if (a.force && !(a.inv_e && a.gforce && moving)) return cudaErrorInvalidValue;
     if (a.force) k_force_grad<<<(unsigned)((a.nxc * 4 + 127) / 128), 128, 0, s>>>(a);
     const int64_t nslots = rows / a.nxc;
@@ -722,7 +679,7 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
     __syncthreads();
     const float m = P.mass_mode == 1 ? 0.0f : (float)P.m2[x * 4 + P.slot_mslot[sl]];
     const long long* st = P.state + ((int64_t)sl * P.nxc + x) * P.npc;
-    const int npc = (int)P.npc, np1 = P.np[1], np2 = P.np[2];
+    const int np1 = P.np[1], np2 = P.np[2];
     const long long pauli = P.pauli[sl];
     int neg = 0, over = 0;  // state warnings: f < 0 anywhere, f > 1 for fermions (Pauli)
     // n = nh 2^32 + nl (nl unsigned): every product below is 32 x 32 bits and
