@@ -67,7 +67,8 @@ __device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)
 // float-to-int conversion instruction; those issue on the FP64 pipe here).
 __device__ __forceinline__ int binf(float k, float L, float inv_dp, int n)
 {
-    const float t = fminf(fmaxf((k + L) * inv_dp, 0.0f), (float)n - 0.5f);
+    const float nf = __uint_as_float(0x4B000000u | (unsigned)n) - 8388608.0f;  // (float)n exactly, n < 2^23
+    const float t = fminf(fmaxf((k + L) * inv_dp, 0.0f), nf - 0.5f);
     const int j = __float_as_int(__fadd_rd(t, 8388608.0f)) - 0x4B000000;
     return j >= n ? n - 1 : j;
 }
@@ -655,6 +656,12 @@ struct PropCache {
     int64_t a = -1;
     double mu[3], s1, s3, alpha;
     double Fa[4], cFb[4], D[4];  // components: k1 (centre 0, sigma1), k3x, k3y, k3z
+    // float-float constants of the last box and x cell a thread saw, so that an item
+    // converts no doubles (FP64 instructions issue at 1/64 of the FP32 rate)
+    const void* box = nullptr;
+    int64_t x = -1;
+    ff L, nL, twoL, dp[3];
+    ff m2[4], mg2;
 };
 
 template <bool LEARNED>
@@ -677,15 +684,29 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
     const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
     const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
     // 23-bit uniforms (x + 1/2) 2^-23 are exact in FP32, and so is u - 1/2
-    auto u23 = [](uint32_t w) { return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f); };
-    const ff L = ff_from_double(P.L64), nL = ff_neg(L), twoL = ff_from_double(2.0 * P.L64);
-    const ff dp[3] = {ff_from_double(P.dp64[0]), ff_from_double(P.dp64[1]), ff_from_double(P.dp64[2])};
+    auto u23 = [](uint32_t w) { return unif23(w); };  // exact, without a conversion instruction
+    if (pc.box != (const void*)&P) {
+        pc.box = &P;
+        pc.x = -1;
+        pc.L = ff_from_double(P.L64);
+        pc.nL = ff_neg(pc.L);
+        pc.twoL = ff_from_double(2.0 * P.L64);
+        for (int i = 0; i < 3; ++i) pc.dp[i] = ff_from_double(P.dp64[i]);
+    }
+    if (pc.x != x) {
+        pc.x = x;
+        for (int i = 0; i < 4; ++i) pc.m2[i] = P.mass_mode == 1 ? ff{0.0f, 0.0f} : ff_from_double(P.m2[x * 4 + i]);
+        pc.mg2 = ff_from_double(P.m2[x * 4]);
+    }
+    const ff L = pc.L, nL = pc.nL, twoL = pc.twoL;
+    const ff dp[3] = {pc.dp[0], pc.dp[1], pc.dp[2]};
     const int jv[3] = {jx, jy, jz};
     const float uj[3] = {u23(r0.x), u23(r0.y), u23(r0.z)};
     ff p[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-        p[i] = ff_add(ff_add(nL, ff_mul_f(dp[i], (float)jv[i] + 0.5f)), ff_mul_f(dp[i], uj[i] - 0.5f));
+        p[i] = ff_add(ff_add(nL, ff_mul_f(dp[i], (__uint_as_float(0x4B000000u | (unsigned)jv[i]) - 8388608.0f) + 0.5f)),
+                      ff_mul_f(dp[i], uj[i] - 0.5f));  // the bin index as a float, exactly (< 2^23)
     ff k1x, k1y, k30, k31, k32;
     int b1xy, lin3;
     float wfac = 1.0f;
@@ -751,9 +772,8 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
     const ff bx = ff_sub(Px, k1x), by = ff_sub(Py, k1y);
     if (!(ff_ge(bx, nL) && ff_lt(bx, L) && ff_ge(by, nL) && ff_lt(by, L))) return 0;
     const TermDev& T = P.terms[d][ti];
-    auto mass = [&](int i) { return P.mass_mode == 1 ? ff{0.0f, 0.0f} : ff_from_double(P.m2[x * 4 + i]); };
-    const ff mg2 = ff_from_double(P.m2[x * 4]);
-    const ff ma2 = mass(T.mslot[0]), mb2 = mass(T.mslot[1]), mc2 = mass(T.mslot[2]), md2 = mass(T.mslot[3]);
+    const ff mg2 = pc.mg2;
+    const ff ma2 = pc.m2[T.mslot[0]], mb2 = pc.m2[T.mslot[1]], mc2 = pc.m2[T.mslot[2]], md2 = pc.m2[T.mslot[3]];
     const ff Ep = ff_sqrt(ff_add(ff_add(ff_add(ff_sqr(p[0]), ff_sqr(p[1])), ff_sqr(p[2])), md2));
     const ff E3 = ff_sqrt(ff_add(ff_add(ff_add(ff_sqr(k30), ff_sqr(k31)), ff_sqr(k32)), mc2));
     const ff E = ff_add(Ep, E3), EE = ff_sqr(E);
@@ -870,11 +890,11 @@ __global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float
     if (seg >= nseg) return;
     const int n = qcount[seg];
     const int step = *step_dev;
+    PropCache pc;
     for (int i = threadIdx.x & 31; i < n; i += 32) {
         const unsigned long long it = qitems[seg * qcap + i];
         const CollideArgs<float>& P = boxes[(int)(it >> 48)];
         const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
-        PropCache pc;
         const long long own = fixup_term_ff<false>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step, pc);
         if (own != 0) red_add(&P.A[a], own);
     }
