@@ -354,8 +354,9 @@ int bz_collision_term_static(const bz_grid* g, uint32_t species_mask, double alp
  * accumulation) gives the parameters of a density over the normalised box
  * y = (k1x, k1y, k3)/L in [-1, 1)^5:
  *   q(y) = alpha/32 + (1 - alpha) prod_i g_i(y_i),  alpha >= 0.1,
- * g_i logistic densities truncated to [-1, 1) (k1 components centred at 0
- * with scale sigma1, k3 components centred at mu3 with scale sigma3).  A
+ * g_i Student-t densities with two degrees of freedom truncated to [-1, 1)
+ * (k1 components centred at 0 with scale sigma1, k3 components centred at
+ * mu3 with scale sigma3; their CDF inverts with square roots only).  A
  * sample drawn from q carries the weight c~ L^5 / q(y) instead of c~ (2L)^5,
  * and its four legs still receive +-w/4, so the estimator stays unbiased
  * for any q > 0 and Sum A = 0 exactly.  Training maximises the |c~|-weighted

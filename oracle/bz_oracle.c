@@ -532,12 +532,21 @@ typedef struct {
 } bzo_run;
 
 /* Learned-proposal sample: defensive mixture q(y) = alpha/32 + (1 - alpha)
- * prod_i g_i(y_i) on y = (k1x, k1y, k3)/L in [-1, 1)^5, g_i the logistic
- * density truncated to [-1, 1) (centre 0 and scale sigma1 for the k1
- * components, centre mu3 and scale sigma3 for k3); pr = (mu3 x3, sigma3,
- * sigma1, alpha).  usel < alpha picks the uniform component (y = 2u - 1),
- * else y_i = mu + sigma logit(Fa + u (Fb - Fa)).  Returns 1/(32 q(y)), the
- * factor that turns the uniform weight V/N into 1/(N q_x). */
+ * prod_i g_i(y_i) on y = (k1x, k1y, k3)/L in [-1, 1)^5, g_i the Student-t
+ * density with two degrees of freedom, f(z) = (2 + z^2)^(-3/2), truncated to
+ * [-1, 1) (centre 0 and scale sigma1 for the k1 components, centre mu3 and
+ * scale sigma3 for k3); pr = (mu3 x3, sigma3, sigma1, alpha).  Its CDF is
+ * F(z) = 1/2 + z / (2 sqrt(2 + z^2)), so with v = Fa + u (Fb - Fa) and
+ * cv = 1 - v the inverse is z = (v - cv) / sqrt(2 v cv) and the density
+ * there is f(z) = (2 v cv)^(3/2): square roots only.  usel < alpha picks the
+ * uniform component (y = 2u - 1).  Returns 1/(32 q(y)), the factor that
+ * turns the uniform weight V/N into 1/(N q_x). */
+static double t2_tail(double z) /* F(-|z|) without cancellation */
+{
+    double s = sqrt(2.0 + z * z);
+    return 1.0 / (s * (s + fabs(z)));
+}
+
 double bzo_proposal_sample(const double* pr, double usel, const double* u5, double* y)
 {
     int uni = usel < pr[5];
@@ -545,17 +554,22 @@ double bzo_proposal_sample(const double* pr, double usel, const double* u5, doub
     for (int i = 0; i < 5; ++i) {
         double mu = i < 2 ? 0.0 : pr[i - 2];
         double sg = i < 2 ? pr[4] : pr[3];
-        double Fa = 1.0 / (1.0 + exp((1.0 + mu) / sg)), Fb = 1.0 / (1.0 + exp(-(1.0 - mu) / sg));
+        double Fa = t2_tail((-1.0 - mu) / sg);  /* F(za), za < 0 */
+        double cFb = t2_tail((1.0 - mu) / sg);  /* 1 - F(zb), zb > 0 */
+        double D = (1.0 - cFb) - Fa;
         if (uni) {
             y[i] = 2.0 * u5[i] - 1.0;
+            double z = (y[i] - mu) / sg;
+            double s = sqrt(2.0 + z * z);
+            G *= 1.0 / (s * s * s * sg * D);
         } else {
-            double v = Fa + u5[i] * (Fb - Fa);
-            y[i] = mu + sg * log(v / (1.0 - v));
+            double v = Fa + u5[i] * D, cv = cFb + (1.0 - u5[i]) * D;
+            double t = 2.0 * v * cv;
+            y[i] = mu + sg * ((v - cv) / sqrt(t));
             if (y[i] < -1.0) y[i] = -1.0;
             if (y[i] >= 1.0) y[i] = 0.99999994;
+            G *= t * sqrt(t) / (sg * D);
         }
-        double F = 1.0 / (1.0 + exp(-(y[i] - mu) / sg));
-        G *= F * (1.0 - F) / (sg * (Fb - Fa));
     }
     return 1.0 / (32.0 * (pr[5] / 32.0 + (1.0 - pr[5]) * G));
 }

@@ -13,9 +13,11 @@ Proposal (defensive mixture):
   mu3 = tanh(o0..2), sigma3 = 0.02 + 0.5 sigmoid(o3), sigma1 = 0.02 + 0.5 sigmoid(o4),
   alpha = 0.1 + 0.9 sigmoid(o5),
   q(y) = alpha / 32 + (1 - alpha) prod_i g_i(y_i),
-g_i the logistic density with centre 0 (k1 components) or mu3 (k3
-components) truncated to [-1, 1).  Loss over records (anchor a, weight w,
-sample y): L = -sum_i w_i log q(y_i | a_i) / sum_i w_i.
+g_i the Student-t density with two degrees of freedom, f(z) = (2 + z^2)^(-3/2)
+(z = (y - centre)/scale), with centre 0 (k1 components) or mu3 (k3
+components), truncated to [-1, 1): its CDF, inverse CDF and density need
+only square roots, F(z) = 1/2 + z / (2 sqrt(2 + z^2)).  Loss over records
+(anchor a, weight w, sample y): L = -sum_i w_i log q(y_i | a_i) / sum_i w_i.
 """
 import numpy as np
 
@@ -106,15 +108,26 @@ def head(O):
     return prm
 
 
+def t2_pdf(z):
+    """Student-t density with two degrees of freedom."""
+    return (2.0 + z * z) ** -1.5
+
+
+def t2_cdf(z):
+    """Its CDF, 1/2 + z / (2 sqrt(2 + z^2)), written without cancellation in the tails."""
+    s = np.sqrt(2.0 + z * z)
+    tail = 1.0 / (s * (s + np.abs(z)))         # F(-|z|)
+    return np.where(z < 0, tail, 1.0 - tail)
+
+
 def proposal_density(prm, y):
     """q(y) for rows of per-sample parameters prm [n, 8] and samples y [n, 5]."""
     G = np.ones(len(y))
     for i in range(5):
         mu = np.zeros(len(y)) if i < 2 else prm[:, i - 2]
         s = prm[:, 4] if i < 2 else prm[:, 3]
-        Fa, Fb = _sig((-1.0 - mu) / s), _sig((1.0 - mu) / s)
-        F = _sig((y[:, i] - mu) / s)
-        G = G * F * (1.0 - F) / (s * (Fb - Fa))
+        Z = t2_cdf((1.0 - mu) / s) - t2_cdf((-1.0 - mu) / s)
+        G = G * t2_pdf((y[:, i] - mu) / s) / (s * Z)
     al = prm[:, 5]
     return al / 32.0 + (1.0 - al) * G
 
@@ -132,12 +145,12 @@ def logq_grad(O, y):
         mu = prm[:, i - 2] if k3 else np.zeros(n)
         s = prm[:, 3] if k3 else prm[:, 4]
         z, za, zb = (y[:, i] - mu) / s, (-1.0 - mu) / s, (1.0 - mu) / s
-        F, Fa, Fb = _sig(z), _sig(za), _sig(zb)
-        Z = Fb - Fa
-        pa, pb = Fa * (1 - Fa), Fb * (1 - Fb)
-        G = G * F * (1 - F) / (s * Z)
-        dm = -(1 - 2 * F) / s + (pb - pa) / (s * Z)
-        dsg = -(1 - 2 * F) * z / s - 1.0 / s + (pb * zb - pa * za) / (s * Z)
+        Z = t2_cdf(zb) - t2_cdf(za)
+        pa, pb = t2_pdf(za), t2_pdf(zb)
+        G = G * t2_pdf(z) / (s * Z)
+        dlf = -3.0 * z / (2.0 + z * z)            # d log f / dz
+        dm = -dlf / s + (pb - pa) / (s * Z)
+        dsg = -dlf * z / s - 1.0 / s + (pb * zb - pa * za) / (s * Z)
         if k3:
             dmu[:, i - 2] = dm
             ds3 += dsg

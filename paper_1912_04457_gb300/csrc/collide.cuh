@@ -190,26 +190,36 @@ __device__ __forceinline__ void make_geom(const CollideArgs<R>& P, int64_t a, in
     }
     G.wfac = R(1);
     if (P.sampler == SAMPLER_LEARNED) {
-        // defensive mixture of the uniform density and truncated logistics (per-anchor parameters)
+        // defensive mixture of the uniform density and truncated Student-t densities with two
+        // degrees of freedom (per-anchor parameters): F(z) = 1/2 + z / (2 sqrt(2 + z^2)), so the
+        // inverse CDF and the density need square roots only
         const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0,
                                        P.key1);
         R prm[6];
         for (int i = 0; i < 6; ++i) prm[i] = (R)P.prop[a * 8 + i];
         const bool uni = O::unif(r2.x, P.ubits) < prm[5];
         R y[5], Gd = R(1);
+        auto tail = [](R z) {  // F(-|z|)
+            const R r = O::sqrt_(R(2) + z * z);
+            return R(1) / (r * (r + O::fabs_(z)));
+        };
         for (int i = 0; i < 5; ++i) {
             const R mu = i < 2 ? R(0) : prm[i - 2];
             const R sg = i < 2 ? prm[4] : prm[3];
-            const R Fa = R(1) / (R(1) + O::exp_((R(1) + mu) / sg)), Fb = R(1) / (R(1) + O::exp_(-(R(1) - mu) / sg));
+            const R Fa = tail((R(-1) - mu) / sg), cFb = tail((R(1) - mu) / sg);
+            const R D = (R(1) - cFb) - Fa;
             if (uni) {
                 y[i] = R(2) * u[3 + i] - R(1);
+                const R z = (y[i] - mu) / sg;
+                const R r = O::sqrt_(R(2) + z * z);
+                Gd *= R(1) / (r * r * r * sg * D);
             } else {
-                const R v = Fa + u[3 + i] * (Fb - Fa);
-                y[i] = mu + sg * log(v / (R(1) - v));
+                const R v = Fa + u[3 + i] * D, cv = cFb + (R(1) - u[3 + i]) * D;
+                const R t = R(2) * v * cv;
+                y[i] = mu + sg * ((v - cv) / O::sqrt_(t));
                 y[i] = y[i] < R(-1) ? R(-1) : (y[i] >= R(1) ? R(0.99999994) : y[i]);
+                Gd *= t * O::sqrt_(t) / (sg * D);
             }
-            const R F = R(1) / (R(1) + O::exp_(-(y[i] - mu) / sg));
-            Gd *= F * (R(1) - F) / (sg * (Fb - Fa));
         }
         G.wfac = R(1) / (R(32) * (prm[5] * (R(1) / R(32)) + (R(1) - prm[5]) * Gd));
         G.k1x = L * y[0];

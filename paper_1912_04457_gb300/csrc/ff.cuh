@@ -139,6 +139,16 @@ __host__ __device__ __forceinline__ bool ff_lt(ff a, ff b) { return ff_gt0(ff_su
 __host__ __device__ __forceinline__ bool ff_ge(ff a, ff b) { return ff_ge0(ff_sub(a, b)); }
 __host__ __device__ __forceinline__ float ff_to_float(ff a) { return FF_ADD(a.hi, a.lo); }
 
+__host__ __device__ __forceinline__ ff ff_abs(ff a) { return a.hi < 0.0f ? ff_neg(a) : a; }
+
+// F(-|z|) of the Student-t distribution with two degrees of freedom,
+// 1 / (r (r + |z|)) with r = sqrt(2 + z^2) (no cancellation in the tails)
+__host__ __device__ __forceinline__ ff ff_t2_tail(ff z)
+{
+    const ff r = ff_sqrt(ff_add_f(ff_sqr(z), 2.0f));
+    return ff_div(ff_from(1.0f), ff_mul(r, ff_add(r, ff_abs(z))));
+}
+
 // floor of a normalised float-float as an int (|a| < 2^22), without a
 // conversion instruction: the integer-valued float f plus 1.5 2^23 holds f
 // in its low mantissa bits

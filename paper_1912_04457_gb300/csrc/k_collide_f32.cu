@@ -38,7 +38,7 @@ struct WarpSmem {
     int b1xy[SBUF], b2xy[SBUF], lin3[SBUF];           // bins of k1perp, k2perp and k3
     int meta[SBUF];               // sample index | k2perp inside << 24 | on an edge << 25
     float wfac[SBUF];             // learned: 1/(32 q(y)); record mode: sum of |c~| of the sample
-    float3 tlc[4];                // learned: tlog_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
+    float3 tlc[4];                // learned: t2_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
     // pending roots
     float z[RING], E3[RING], sqH[RING];
     int tag[RING];                // live-sample sequence number | term << 24
@@ -94,27 +94,20 @@ __device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float 
     return r < nu || r > 1.0f - nu;
 }
 
-// e^x accurate to a few ulp for any |x|: x log2(e) is split exactly into
-// t + r (t = fl(x log2e_hi), r from the FMA residual of that product plus
-// x log2e_lo, i.e. Dekker's exact product), so the rounding of the argument
-// no longer grows with |x|; then e^x = 2^t (1 + r ln 2) to second order in r.
-__device__ __forceinline__ float exp_split(float x)
+// Student-t with two degrees of freedom, truncated to [-1, 1), centre mu and
+// scale s (|mu| < 1): Fa = F(-1), cFb = 1 - F(1) and D = F(1) - F(-1), the
+// tails F(-|z|) = 1 / (r (r + |z|)), r = sqrt(2 + z^2), without cancellation.
+__device__ __forceinline__ float t2_tail(float z)
 {
-    const float L2E_HI = 1.44269502162933349609375f;  // log2(e) rounded to FP32
-    const float L2E_LO = 1.92596299e-08f;             // log2(e) - L2E_HI
-    const float t = x * L2E_HI;
-    const float r = fmaf(x, L2E_HI, -t) + x * L2E_LO;
-    return exp2f(t) * fmaf(r, 0.6931471805599453f, 1.0f);
+    const float r = sqrtf(2.0f + z * z);
+    return 1.0f / (r * (r + fabsf(z)));
 }
 
-// Truncated logistic on [-1, 1) with centre mu and scale s: Fa = F(-1),
-// cFb = 1 - F(1) and D = F(1) - F(-1), each without cancellation.
-__device__ __forceinline__ float3 tlog_consts(float mu, float s)
+__device__ __forceinline__ float3 t2_consts(float mu, float s)
 {
-    const float Fa = 1.0f / (1.0f + exp_split((1.0f + mu) / s));
-    const float cFb = 1.0f / (1.0f + exp_split((1.0f - mu) / s));
-    const float Fb = 1.0f / (1.0f + exp_split(-(1.0f - mu) / s));
-    return make_float3(Fa, cFb, Fb - Fa);
+    const float Fa = t2_tail((-1.0f - mu) / s);
+    const float cFb = t2_tail((1.0f - mu) / s);
+    return make_float3(Fa, cFb, (1.0f - cFb) - Fa);
 }
 
 }  // namespace
@@ -186,8 +179,8 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         ps3 = __shfl_sync(0xffffffffu, v, 3);
         ps1 = __shfl_sync(0xffffffffu, v, 4);
         pa = __shfl_sync(0xffffffffu, v, 5);
-        if (lane < 4) S.tlc[lane] = tlog_consts(lane == 0 ? 0.0f : (lane == 1 ? pm0 : (lane == 2 ? pm1 : pm2)),
-                                               lane == 0 ? ps1 : ps3);
+        if (lane < 4) S.tlc[lane] = t2_consts(lane == 0 ? 0.0f : (lane == 1 ? pm0 : (lane == 2 ? pm1 : pm2)),
+                                             lane == 0 ? ps1 : ps3);
     }
     const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
     const float pc0 = -L + ((float)jx + 0.5f) * P.dp[0];
@@ -440,9 +433,10 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
                 const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
                                                P.key0, P.key1);
-                // Component i: y = mu + s logit(v), v = Fa + u D, so F(y) = v and
-                // 1 - F(y) = cFb + (1 - u) D: the density v (1 - v)/(s D) needs no
-                // exponential.  A uniform draw y = 2u - 1 takes F(y) from exp_split.
+                // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
+                // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
+                // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
+                // (2 + z^2)^(-3/2) / (s D).  Square roots only.
                 const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
                 float y[5];
                 const bool uni = unif23(r2.x) < pa;
@@ -452,20 +446,19 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
                     const float sg = i < 2 ? ps1 : ps3;
                     const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
-                    float F, cF;
                     if (uni) {
                         y[i] = 2.0f * uv[i] - 1.0f;
                         const float zz = (y[i] - mu) / sg;
-                        const float e = exp_split(-fabsf(zz));
-                        const float inv = 1.0f / (1.0f + e);
-                        F = zz >= 0.0f ? inv : e * inv;
-                        cF = zz >= 0.0f ? e * inv : inv;
+                        const float r = rsqrtf(2.0f + zz * zz);
+                        G *= r * r * r / (sg * tc.z);
                     } else {
-                        F = tc.x + uv[i] * tc.z;
-                        cF = tc.y + (1.0f - uv[i]) * tc.z;
-                        y[i] = fminf(fmaxf(mu + sg * __logf(F / cF), -1.0f), 0.99999994f);
+                        const float v = tc.x + uv[i] * tc.z;
+                        const float cv = tc.y + (1.0f - uv[i]) * tc.z;
+                        const float t = 2.0f * v * cv;
+                        const float rt = rsqrtf(t);
+                        y[i] = fminf(fmaxf(mu + sg * ((v - cv) * rt), -1.0f), 0.99999994f);
+                        G *= t * t * rt / (sg * tc.z);
                     }
-                    G *= F * cF / (sg * tc.z);
                 }
                 wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
                 k1x = L * y[0];
@@ -634,8 +627,8 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
 // ill-conditioned, or put a solved coordinate on a bin edge, is redone in
 // float-float arithmetic (about 48 bits, FP32 instructions only; FP64 issues
 // at 1/64 of the FP32 rate here): the sample point from the same Philox
-// words (the uniform sampler's exactly; the learned one's inverse-CDF
-// transform and weight in FP64), E, D, kappa, H, the roots and
+// words (the uniform sampler's exactly, the learned one's Student-t inverse
+// CDF too; its weight in FP32), E, D, kappa, H, the roots and
 // their validity, box and bin decisions (the uniform sampler's sampled legs
 // take the exact integer bins), E1, s, t and u.  From the accepted roots on
 // (|M|^2, W and c~ in FP32) it is an ordinary term of the FP32 path.
@@ -654,8 +647,8 @@ __device__ __forceinline__ int bin_ff(ff k, ff L, ff dp, int n)
 // (consecutive queue items mostly come from one anchor).
 struct PropCache {
     int64_t a = -1;
-    double mu[3], s1, s3, alpha;
-    double Fa[4], cFb[4], D[4];  // components: k1 (centre 0, sigma1), k3x, k3y, k3z
+    float mu[3], s1, s3, alpha;
+    ff Fa[4], cFb[4], D[4];  // components: k1 (centre 0, sigma1), k3x, k3y, k3z
     // float-float constants of the last box and x cell a thread saw, so that an item
     // converts no doubles (FP64 instructions issue at 1/64 of the FP32 rate)
     const void* box = nullptr;
@@ -711,9 +704,10 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
     int b1xy, lin3;
     float wfac = 1.0f;
     if (LEARNED) {
-        // the learned sample point to FP64 accuracy (the integrand of a queued term is
-        // sensitive to it): y = mu + sigma logit(Fa + u (Fb - Fa)) on logistic draws (F(y) = v
-        // there, so the density needs no exponential), y = 2u - 1 on uniform draws
+        // the learned sample point in float-float (the integrand of a queued term is
+        // sensitive to it): v = Fa + u D, cv = cFb + (1 - u) D, y = mu + s (v - cv) /
+        // sqrt(2 v cv) on Student-t draws, y = 2u - 1 on uniform ones; its weight 1/(32 q)
+        // in FP32 from the same values
         if (pc.a != a) {
             const float* pr = P.prop + a * 8;
             for (int i = 0; i < 3; ++i) pc.mu[i] = pr[i];
@@ -721,41 +715,45 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
             pc.s1 = pr[4];
             pc.alpha = pr[5];
             for (int c = 0; c < 4; ++c) {
-                const double mu = c == 0 ? 0.0 : pc.mu[c - 1], sg = c == 0 ? pc.s1 : pc.s3;
-                pc.Fa[c] = 1.0 / (1.0 + exp((1.0 + mu) / sg));
-                pc.cFb[c] = 1.0 / (1.0 + exp((1.0 - mu) / sg));
-                pc.D[c] = 1.0 / (1.0 + exp(-(1.0 - mu) / sg)) - pc.Fa[c];
+                const ff mu = ff_from(c == 0 ? 0.0f : pc.mu[c - 1]), sg = ff_from(c == 0 ? pc.s1 : pc.s3);
+                pc.Fa[c] = ff_t2_tail(ff_div(ff_sub(ff_from(-1.0f), mu), sg));
+                pc.cFb[c] = ff_t2_tail(ff_div(ff_sub(ff_from(1.0f), mu), sg));
+                pc.D[c] = ff_sub(ff_sub(ff_from(1.0f), pc.cFb[c]), pc.Fa[c]);
             }
             pc.a = a;
         }
         const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
                                        P.key0, P.key1);
-        const double uv[5] = {u23(r0.w), u23(r1.x), u23(r1.y), u23(r1.z), u23(r1.w)};
-        const bool uni = (double)u23(r2.x) < pc.alpha;
-        double y[5], G = 1.0;
+        const float uv[5] = {u23(r0.w), u23(r1.x), u23(r1.y), u23(r1.z), u23(r1.w)};
+        const bool uni = u23(r2.x) < pc.alpha;
+        ff y[5];
+        float G = 1.0f;
         for (int i = 0; i < 5; ++i) {
             const int c = i < 2 ? 0 : i - 1;
-            const double mu = i < 2 ? 0.0 : pc.mu[i - 2], sg = i < 2 ? pc.s1 : pc.s3;
-            double F, cF;
+            const float mu = i < 2 ? 0.0f : pc.mu[i - 2], sg = i < 2 ? pc.s1 : pc.s3;
+            const float Dh = ff_to_float(pc.D[c]);
             if (uni) {
-                y[i] = 2.0 * uv[i] - 1.0;
-                const double zz = (y[i] - mu) / sg, e = exp(-fabs(zz)), inv = 1.0 / (1.0 + e);
-                F = zz >= 0.0 ? inv : e * inv;
-                cF = zz >= 0.0 ? e * inv : inv;
+                y[i] = ff_from(2.0f * uv[i] - 1.0f);  // exact
+                const float zz = (y[i].hi - mu) / sg;
+                const float r = rsqrtf(2.0f + zz * zz);
+                G *= r * r * r / (sg * Dh);
             } else {
-                F = pc.Fa[c] + uv[i] * pc.D[c];
-                cF = pc.cFb[c] + (1.0 - uv[i]) * pc.D[c];
-                y[i] = mu + sg * log(F / cF);
-                y[i] = y[i] < -1.0 ? -1.0 : (y[i] >= 1.0 ? 0.99999994 : y[i]);
+                const ff v = ff_add(pc.Fa[c], ff_mul_f(pc.D[c], uv[i]));
+                const ff cv = ff_add(pc.cFb[c], ff_mul_f(pc.D[c], 1.0f - uv[i]));  // 1 - u exact
+                const ff t = ff_mul_f(ff_mul(v, cv), 2.0f);
+                y[i] = ff_add(ff_from(mu), ff_mul_f(ff_div(ff_sub(v, cv), ff_sqrt(t)), sg));
+                if (ff_lt(y[i], ff_from(-1.0f))) y[i] = ff_from(-1.0f);
+                if (ff_ge(y[i], ff_from(1.0f))) y[i] = ff_from(0.99999994f);
+                const float th = ff_to_float(t);
+                G *= th * sqrtf(th) / (sg * Dh);
             }
-            G *= F * cF / (sg * pc.D[c]);
         }
-        wfac = (float)(1.0 / (32.0 * (pc.alpha / 32.0 + (1.0 - pc.alpha) * G)));
-        k1x = ff_from_double(P.L64 * y[0]);
-        k1y = ff_from_double(P.L64 * y[1]);
-        k30 = ff_from_double(P.L64 * y[2]);
-        k31 = ff_from_double(P.L64 * y[3]);
-        k32 = ff_from_double(P.L64 * y[4]);
+        wfac = 1.0f / (32.0f * (pc.alpha * (1.0f / 32.0f) + (1.0f - pc.alpha) * G));
+        k1x = ff_mul(L, y[0]);
+        k1y = ff_mul(L, y[1]);
+        k30 = ff_mul(L, y[2]);
+        k31 = ff_mul(L, y[3]);
+        k32 = ff_mul(L, y[4]);
         b1xy = bin_ff(k1x, L, dp[0], P.np[0]) * P.np[1] + bin_ff(k1y, L, dp[1], P.np[1]);
         lin3 = (bin_ff(k30, L, dp[0], P.np[0]) * P.np[1] + bin_ff(k31, L, dp[1], P.np[1])) * P.np[2]
                + bin_ff(k32, L, dp[2], P.np[2]);

@@ -15,8 +15,9 @@
 // [-1, 1)^5): mu3 = tanh(o0..2), sigma3 = 0.02 + 0.5 sigmoid(o3), sigma1 =
 // 0.02 + 0.5 sigmoid(o4), alpha = 0.1 + 0.9 sigmoid(o5);
 //   q(y) = alpha / 32 + (1 - alpha) prod_i g_i(y_i),
-// g_i the logistic density truncated to [-1, 1) with centre 0 (k1 components,
-// scale sigma1) or mu3 (k3 components, scale sigma3).
+// g_i the Student-t density with two degrees of freedom, f(z) = (2 + z^2)^(-3/2),
+// truncated to [-1, 1), with centre 0 (k1 components, scale sigma1) or mu3
+// (k3 components, scale sigma3); its CDF is 1/2 + z / (2 sqrt(2 + z^2)).
 // Training loss over records (y, w = sum over terms and roots of |c~|, taken
 // with the uniform sampler): L = -sum w log q(y) / sum w  (q -> |c~| / int|c~|).
 #include <cuda_bf16.h>
@@ -137,6 +138,18 @@ __device__ __forceinline__ void head(const float o[6], float prm[8])
     prm[7] = 0.0f;
 }
 
+// truncated Student-t (two degrees of freedom): density and the tail F(-|z|)
+__device__ __forceinline__ float t2_pdf(float z)
+{
+    const float r = rsqrtf(2.0f + z * z);
+    return r * r * r;
+}
+__device__ __forceinline__ float t2_tail(float z)
+{
+    const float s = sqrtf(2.0f + z * z);
+    return 1.0f / (s * (s + fabsf(z)));
+}
+
 // log q(y) and d log q / d o (6) for one record
 __device__ void logq_grad(const float o[6], const float y[5], float& logq, float g[6])
 {
@@ -149,13 +162,14 @@ __device__ void logq_grad(const float o[6], const float y[5], float& logq, float
         const float mu = k3 ? prm[i - 2] : 0.0f;
         const float s = k3 ? prm[3] : prm[4];
         const float z = (y[i] - mu) / s, za = (-1.0f - mu) / s, zb = (1.0f - mu) / s;
-        const float F = sigm(z), Fa = sigm(za), Fb = sigm(zb);
-        const float Z = Fb - Fa;
-        const float pa = Fa * (1.0f - Fa), pb = Fb * (1.0f - Fb);
-        G *= F * (1.0f - F) / (s * Z);
-        // d log g / d mu and d log g / d s
-        const float dm = -(1.0f - 2.0f * F) / s + (pb - pa) / (s * Z);
-        const float ds = -(1.0f - 2.0f * F) * z / s - 1.0f / s + (pb * zb - pa * za) / (s * Z);
+        // za < 0 < zb: Z = F(zb) - F(za) = 1 - tail(zb) - tail(za)
+        const float Z = (1.0f - t2_tail(zb)) - t2_tail(za);
+        const float pa = t2_pdf(za), pb = t2_pdf(zb);
+        G *= t2_pdf(z) / (s * Z);
+        // d log g / d mu and d log g / d s, with d log f / dz = -3 z / (2 + z^2)
+        const float dlf = -3.0f * z / (2.0f + z * z);
+        const float dm = -dlf / s + (pb - pa) / (s * Z);
+        const float ds = -dlf * z / s - 1.0f / s + (pb * zb - pa * za) / (s * Z);
         if (k3) {
             dmu[i - 2] = dm;
             dsig3 += ds;

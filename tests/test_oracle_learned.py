@@ -37,14 +37,15 @@ def test_oracle_sampler_draws_from_the_density():
         ys[i], wf[i] = O.proposal_sample(prm, rng.uniform(), rng.uniform(size=5))
     q = mlp.proposal_density(np.tile(prm, (n, 1)), ys)
     assert np.allclose(wf, 1.0 / (32.0 * q), rtol=1e-10)
-    # marginal histograms vs the density's marginals (mixture of uniform and truncated logistic)
+    # marginal histograms vs the density's marginals (mixture of uniform and truncated Student-t with
+    # two degrees of freedom, whose CDF is 1/2 + z / (2 sqrt(2 + z^2)))
     edges = np.linspace(-1, 1, 21)
     for i in range(5):
         mu = 0.0 if i < 2 else prm[i - 2]
         s = prm[4] if i < 2 else prm[3]
-        sig = lambda z: 1.0 / (1.0 + np.exp(-z))
-        Fa, Fb = sig((-1 - mu) / s), sig((1 - mu) / s)
-        cdf = (sig((edges - mu) / s) - Fa) / (Fb - Fa)
+        cdf2 = lambda z: 0.5 + z / (2.0 * np.sqrt(2.0 + z * z))
+        Fa, Fb = cdf2((-1 - mu) / s), cdf2((1 - mu) / s)
+        cdf = (cdf2((edges - mu) / s) - Fa) / (Fb - Fa)
         p = prm[5] * np.diff(edges) / 2.0 + (1 - prm[5]) * np.diff(cdf)
         counts, _ = np.histogram(ys[:, i], edges)
         chi2 = ((counts - n * p) ** 2 / (n * p)).sum()
