@@ -359,7 +359,7 @@ def run_bz(args):
     result = None
     if rank == 0:
         coll_ms, coll_n = prof["collide"]
-        drift_kernels = 2 if w.nxc > 1 else 1   # k_inv_energy + the drift kernel on inhomogeneous grids
+        drift_kernels = 2 if w.nxc > 1 else 1   # k_mass_table + the drift kernel on inhomogeneous grids
         nsm_ = torch.cuda.get_device_properties(local).multi_processor_count
         # k_moments + k_moments_finish when few (x cell, slot) rows are split into p-cell chunks
         mom_kernels = 2 if (w.nxc * w.nslots < 2 * nsm_ and w.npc // 1024 > 1) else 1
@@ -477,7 +477,7 @@ def measured_hbm_gbs():
 
 
 def transport_rooflines(h, w, state, mom, prof, steps, stream, barrier):
-    """Drift (k_inv_energy + drift kernel; algorithmic bytes 8 B read + 8 B
+    """Drift (k_mass_table + drift kernel; algorithmic bytes 8 B read + 8 B
     write + 4 B f per cell) and moments (8 B read per cell) of the timed steps
     against the HBM peak, and the drift with the force term switched on,
     timed over separate calls."""

@@ -38,6 +38,7 @@ struct bz_handle_s {
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
+    float* d_m2f = nullptr;        // drift scratch: FP32 m^2 per (x cell, mass slot)
     double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
     long long* d_mom_part = nullptr;  // moments: exact partial sums of the p-cell chunks
     int64_t mom_part_cap = 0;
@@ -164,6 +165,8 @@ static void free_scratch(bz_handle h)
     h->d_inv_e = nullptr;
     cudaFree(h->d_gforce);
     h->d_gforce = nullptr;
+    cudaFree(h->d_m2f);
+    h->d_m2f = nullptr;
     cudaFree(h->d_m2prev);
     h->d_m2prev = nullptr;
     cudaFree(h->d_mom_part);
@@ -212,6 +215,8 @@ static int alloc_scratch(bz_handle h)
         return fail(h, BZ_ENOMEM, "cannot allocate %lld bytes for the drift", (long long)(4 * h->ncell));
     if (h->nxc > 1 && !h->d_gforce && cudaMalloc(&h->d_gforce, sizeof(float) * 12 * h->nxc) != cudaSuccess)
         return fail(h, BZ_ENOMEM, "cannot allocate the force-term scratch");
+    if (h->nxc > 1 && !h->d_m2f && cudaMalloc(&h->d_m2f, sizeof(float) * 4 * h->nxc) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the drift's mass table");
     return BZ_OK;
 }
 
@@ -805,6 +810,7 @@ static int fill_drift(bz_handle h, DriftArgs& a, const long long* in, long long*
     }
     a.jtab = h->d_jtab;
     a.inv_e = h->d_inv_e;
+    a.m2f = h->d_m2f;
     // the force needs a mass gradient: none with one x cell or the massless dispersion
     a.force = h->force && h->nxc > 1 && h->mass_mode != BZ_MASS_MASSLESS;
     a.gforce = h->d_gforce;

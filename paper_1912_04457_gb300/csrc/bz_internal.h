@@ -162,6 +162,7 @@ struct DriftArgs {
     float fscale[NSPEC];    // per slot: FP32 rounding of 2^-40 / N_s (the FP32 f is n_fp32 * fscale)
     const int* jtab;        // [npc] jx | jy << 8 | jz << 16
     float* inv_e;           // [ncell] scratch: 1/sqrt(p^2 + m^2) of every cell, written by k_inv_energy
+    float* m2f;             // [nxc][4] scratch: FP32 rounding of m^2 per x cell and mass slot (0: massless)
     // force term -div_p[(grad_x E) f] (off: force = 0): per (x cell, mass slot, axis) the FP32
     // g_i = (m^2(x + e_i) - m^2(x - e_i)) / (4 dx), written by k_force_grad into gforce
     int force;

@@ -258,17 +258,19 @@ __device__ __forceinline__ int rint_split(float w)
     return (int)(((unsigned)(__float_as_int(hs) - 0x4B400000) << 16) + (unsigned)(__float_as_int(ls) - 0x4B400000));
 }
 
-// Courant integer of the narrow form, rint((p_d inv) K) with K = dt/dx 2^30:
-// the exact power-of-two factor folded into K gives the same float as
-// ((p_d inv) dt/dx) 2^30 wherever the rounded value can be nonzero.
-__device__ __forceinline__ int courant_i32(float pd, float inv, float K)
-{
-    return rint_split((pd * inv) * K);
-}
 
 __device__ __forceinline__ long long flux_n(long long n, int C)
 {
     return flux32((int)(n >> 32), (unsigned)n, C);
+}
+
+// Courant integer of the narrow form, rint((p_d inv) K) with K = dt/dx 2^30,
+// round half even by the hardware conversion (|w| < 2^31 in the narrow form):
+// the exact power-of-two factor folded into K gives the same float as
+// ((p_d inv) dt/dx) 2^30 wherever the rounded value can be nonzero.
+__device__ __forceinline__ int courant_cvt(float pd, float inv, float K)
+{
+    return __float2int_rn((pd * inv) * K);
 }
 
 // Force term of Eq. (left handside), -div_p[(grad_x E) f]: along p_i the p
@@ -406,14 +408,6 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
     }
 }
 
-// Drift by (y, z) planes, the same integer fluxes as k_drift with every face
-// flux of the two inner x axes computed once: a thread owns one p cell of one
-// (slot, x index ix) and walks a segment of y rows in the upwind order of its
-// p_y, and each row in ascending z.  The y-face flux of the row upwind of the
-// current one is kept per z cell in shared memory; the z-face fluxes of cells
-// z - 1, z, z + 1 in registers (the next cell's state is loaded one step
-// ahead).  Only the x axis reads its upwind neighbour.  Face fluxes per cell:
-// 4 + 1/n_z + 1/(rows per segment), against 6 in k_drift.
 constexpr int PLANE_THREADS = 128;
 constexpr int PLANE_MAX_NZ = 40;  // y-face buffer: n_z x PLANE_THREADS int64 of dynamic shared memory
 #ifndef BZ_PLANE_THREADS_PER_SM
@@ -426,11 +420,83 @@ constexpr int PLANE_MAX_NZ = 40;  // y-face buffer: n_z x PLANE_THREADS int64 of
 #define BZ_HW_CVT 0       // 1: f conversion with the hardware int64 -> float instruction (slower here)
 #endif
 
-template <bool FORCE>
-__global__ void __launch_bounds__(PLANE_THREADS) k_drift_plane(const __grid_constant__ DriftArgs P, int nseg, float K)
+// Asynchronous global -> shared copies (cp.async): the streaming drift keeps
+// its state loads BZ_DPIPE cells ahead of their use without holding registers.
+// Each thread copies and later reads only its own words, so completion of its
+// own groups (wait_group) is the only ordering needed.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
 {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+#ifndef BZ_DPIPE
+#define BZ_DPIPE 2  // cells in flight per thread (cp.async groups)
+#endif
+
+// FP32 m^2 of every (x cell, mass slot) for the streaming drift, the same
+// rounding as k_inv_energy's per-row value.
+__global__ void k_mass_table(const __grid_constant__ DriftArgs P)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < P.nxc * 4) P.m2f[t] = P.mass_mode == 1 ? 0.0f : (float)P.m2[t];
+}
+
+// Force-term part of the update of cell j of one (slot, x) row, as
+// force_acc, with the inverse energy of the cell behind computed in place:
+// it differs from cell j only in its p_i, and shares the x cell's m^2.
+__device__ __forceinline__ long long force_acc_inline(const DriftArgs& P, const float* g3, int jp, int j,
+                                                      const long long* in_row, long long n, float inv,
+                                                      const float (*pf)[MAX_NP], float m)
+{
+    const int jv[3] = {jp & 0xff, (jp >> 8) & 0xff, jp >> 16};
+    const int stride[3] = {P.np[1] * P.np[2], P.np[2], 1};
+    long long acc = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (P.nx[i] == 1) continue;
+        const float g = __ldg(g3 + i);
+        const bool up = (-g) > 0.0f;  // towards larger p_i
+        const int jo = jv[i] + (up ? 1 : -1), jb = jv[i] + (up ? -1 : 1);
+        long long own = 0, behind = 0;
+        if (jo >= 0 && jo < P.np[i]) own = force_flux(n, g, inv, P.Kp[i]);
+        if (jb >= 0 && jb < P.np[i]) {
+            const int jj = j + (up ? -stride[i] : stride[i]);
+            const float q0 = pf[0][i == 0 ? jb : jv[0]], q1 = pf[1][i == 1 ? jb : jv[1]], q2 = pf[2][i == 2 ? jb : jv[2]];
+            const float invb = 1.0f / sqrtf((q0 * q0 + q1 * q1) + q2 * q2 + m);
+            behind = force_flux(__ldg(in_row + jj), g, invb, P.Kp[i]);
+        }
+        acc += up ? own - behind : behind - own;
+    }
+    return acc;
+}
+
+// Drift by (y, z) planes, streaming: the integer fluxes of k_drift with every
+// face flux of the two inner x axes computed once per step.  A thread owns
+// one p cell of one (slot, x index ix) and walks a segment of y rows and each
+// row's z cells in the upwind order of its own p_y and p_z, so the flux into
+// the current cell is the one it computed for the previous cell (z, in a
+// register) or for the previous row (y, per z cell in shared memory); each
+// row starts with its periodic wrap cell.  The x axis reads the upwind
+// neighbour.  1/E = 1/sqrt(p^2 + m^2(x)) is computed in place (IEEE FP32, as
+// k_inv_energy) from the p cell's p^2 and the x cell's FP32 m^2, and the
+// state is streamed through a cp.async ring BZ_DPIPE cells ahead, so a step
+// reads the state once (the x neighbours from L2) and writes it and f once.
+// Face fluxes per cell: 4 + 1/n_z + 1/(rows per segment), against 6 in
+// k_drift.  Integer sums do not depend on their order: the result is the
+// bits of k_drift.
+template <bool FORCE>
+__global__ void __launch_bounds__(PLANE_THREADS) k_drift_stream(const __grid_constant__ DriftArgs P, int nseg, float K)
+{
+    constexpr int D = BZ_DPIPE;
     __shared__ float s_pf[3][MAX_NP];
-    extern __shared__ long long s_fy[];  // [n_z][PLANE_THREADS]
+    extern __shared__ long long s_dyn[];  // y-face buffer [n_z][PLANE_THREADS], then the ring [D][2][PLANE_THREADS]
     for (int d = 0; d < 3; ++d)
         for (int i = threadIdx.x; i < P.np[d]; i += blockDim.x) s_pf[d][i] = P.pf[d][i];
     __syncthreads();
@@ -444,81 +510,110 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_drift_plane(const __grid_cons
     const int ix = rest % nx0, sl = rest / nx0;
     const int jp = __ldg(P.jtab + j);
     const float p0 = s_pf[0][jp & 0xff], p1 = s_pf[1][(jp >> 8) & 0xff], p2 = s_pf[2][jp >> 16];
+    const float pp = (p0 * p0 + p1 * p1) + p2 * p2;
     const bool sx = p0 > 0.0f, sy = p1 > 0.0f, sz = p2 > 0.0f;  // p_d > 0: the upwind neighbour is the lower one
     const int ixu = sx ? (ix == 0 ? nx0 - 1 : ix - 1) : (ix == nx0 - 1 ? 0 : ix + 1);
     const int64_t plane = (int64_t)ny * nz * P.npc;  // cells of one x index
     const int64_t zs = P.npc;                         // cells between z neighbours
     const int64_t b_own = (int64_t)sl * P.nxc * P.npc + (int64_t)ix * plane + j;
-    const int64_t b_up = (int64_t)sl * P.nxc * P.npc + (int64_t)ixu * plane + j;
+    const int64_t dup = (int64_t)(ixu - ix) * plane;  // to the x-upwind cell
+    const int ms = P.slot_mslot[sl];
+    const float* m2f = P.m2f + ms;                    // [x * 4]
+    const int xo = ix * ny * nz, xuo = ixu * ny * nz;   // x cell = (ix n_y + iy) n_z + iz
     const long long* in = P.in;
-    const float* ie = P.inv_e;
-    long long* fy = s_fy + threadIdx.x;
+    long long* fy = s_dyn + threadIdx.x;
+    long long* ring = s_dyn + (size_t)nz * PLANE_THREADS + threadIdx.x;
     const bool mx = nx0 > 1, my = ny > 1, mz = nz > 1;
     const int t0 = (int)((int64_t)seg * ny / nseg), t1 = (int)((int64_t)(seg + 1) * ny / nseg);
+    const int W = mz ? 1 : 0, per_row = nz + W, nr = t1 - t0;
     if (my) {  // y-face fluxes of the row upwind of the segment's first row
         const int tw = t0 == 0 ? ny - 1 : t0 - 1;
-        const int64_t rw = b_own + (int64_t)(sy ? tw : ny - 1 - tw) * nz * zs;
+        const int iy = sy ? tw : ny - 1 - tw;
+        const int64_t rw = b_own + (int64_t)iy * nz * zs;
         for (int iz = 0; iz < nz; ++iz) {
-            const int64_t o = rw + iz * zs;
-            fy[iz * PLANE_THREADS] = flux_n(__ldg(in + o), courant_i32(p1, __ldg(ie + o), K));
+            const float inv = 1.0f / sqrtf(pp + __ldg(m2f + (xo + iy * nz + iz) * 4));
+            fy[iz * PLANE_THREADS] = flux_n(__ldg(in + rw + iz * zs), courant_cvt(p1, inv, K));
         }
     }
-#pragma unroll 1
-    for (int t = t0; t < t1; ++t) {
-        const int64_t rb = b_own + (int64_t)(sy ? t : ny - 1 - t) * nz * zs;
-        const int64_t ru = b_up + (rb - b_own);
-        long long n_cur = __ldg(in + rb);
-        float i_cur = __ldg(ie + rb);
-        long long fz_cur = 0, fz_prev = 0, fz_first = 0;
-        if (mz) {
-            fz_cur = flux_n(n_cur, courant_i32(p2, i_cur, K));
-            fz_first = fz_cur;
-            const int64_t ol = rb + (int64_t)(nz - 1) * zs;
-            fz_prev = flux_n(__ldg(in + ol), courant_i32(p2, __ldg(ie + ol), K));
-        }
-#pragma unroll 1
-        for (int iz = 0; iz < nz; ++iz) {
-            const int64_t oc = rb + iz * zs;
-            long long n_nx = 0, fz_next = fz_first;
-            float i_nx = 0.0f;
-            if (iz + 1 < nz) {
-                n_nx = __ldg(in + oc + zs);
-                i_nx = __ldg(ie + oc + zs);
-                fz_next = flux_n(n_nx, courant_i32(p2, i_nx, K));
+    // item i of a row: i < W the wrap cell, else the (i - W)-th cell in upwind order
+    int pr = 0, pi = 0, ps = 0;  // next item to copy and its ring slot
+    auto issue = [&]() {
+        if (pr < nr) {
+            const int iy = sy ? t0 + pr : ny - 1 - t0 - pr;
+            int k = pi - W;
+            const bool wrap = k < 0;
+            if (wrap) k = nz - 1;
+            const int iz = sz ? k : nz - 1 - k;
+            const long long* src = in + b_own + ((int64_t)iy * nz + iz) * zs;
+            cp_async8(ring + (2 * ps) * PLANE_THREADS, src);
+            if (mx && !wrap) cp_async8(ring + (2 * ps + 1) * PLANE_THREADS, src + dup);
+            if (++pi == per_row) {
+                pi = 0;
+                ++pr;
             }
+        }
+        cp_async_commit();
+        ps = ps + 1 == D ? 0 : ps + 1;
+    };
+#pragma unroll
+    for (int q = 0; q < D - 1; ++q) issue();
+    long long fz_up = 0;  // z flux of the previous cell of the walk (the upwind one)
+    int cr = 0, ci = 0, cs = 0;
+#pragma unroll 1
+    for (int g = 0, G = nr * per_row; g < G; ++g) {
+        issue();
+        cp_async_wait<D - 1>();
+        const long long n = ring[(2 * cs) * PLANE_THREADS];
+        const int iy = sy ? t0 + cr : ny - 1 - t0 - cr;
+        int k = ci - W;
+        const bool wrap = k < 0;
+        if (wrap) k = nz - 1;
+        const int iz = sz ? k : nz - 1 - k;
+        const int xr = iy * nz + iz;
+        const float m = __ldg(m2f + (xo + xr) * 4);
+        const float inv = 1.0f / sqrtf(pp + m);
+        if (wrap) {
+            fz_up = flux_n(n, courant_cvt(p2, inv, K));
+        } else {
             long long acc = 0;
             // p_d > 0: outflow through the upper face, inflow from below; else the mirror
-            if (mz) acc += sz ? fz_cur - fz_prev : fz_next - fz_cur;
+            if (mz) {
+                const long long f2 = flux_n(n, courant_cvt(p2, inv, K));
+                acc += sz ? f2 - fz_up : fz_up - f2;
+                fz_up = f2;
+            }
             if (my) {
-                const long long f1 = flux_n(n_cur, courant_i32(p1, i_cur, K));
+                const long long f1 = flux_n(n, courant_cvt(p1, inv, K));
                 const long long fu = fy[iz * PLANE_THREADS];
                 acc += sy ? f1 - fu : fu - f1;
                 fy[iz * PLANE_THREADS] = f1;
             }
             if (mx) {
-                const long long f0 = flux_n(n_cur, courant_i32(p0, i_cur, K));
-                const int64_t ou = ru + iz * zs;
-                const long long fu = flux_n(__ldg(in + ou), courant_i32(p0, __ldg(ie + ou), K));
+                const long long nu = ring[(2 * cs + 1) * PLANE_THREADS];
+                const float invu = 1.0f / sqrtf(pp + __ldg(m2f + (xuo + xr) * 4));
+                const long long f0 = flux_n(n, courant_cvt(p0, inv, K));
+                const long long fu = flux_n(nu, courant_cvt(p0, invu, K));
                 acc += sx ? f0 - fu : fu - f0;
             }
-            if (FORCE) {
-                const int64_t xr = (oc - j) / P.npc;  // slot * nxc + x
-                const float* g3 = P.gforce + ((xr - (int64_t)sl * P.nxc) * 4 + P.slot_mslot[sl]) * 3;
-                acc += force_acc(P, g3, jp, j, in + (oc - j), ie + (oc - j), n_cur, i_cur);
-            }
-            P.out[oc] = n_cur - acc;
+            const int64_t oc = b_own + (int64_t)xr * zs;
+            if (FORCE)
+                acc += force_acc_inline(P, P.gforce + ((int64_t)(xo + xr) * 4 + ms) * 3, jp, j, in + (oc - j), n, inv,
+                                        s_pf, m);
+            P.out[oc] = n - acc;
             if (P.freal) {
                 if (P.freal_double)
-                    static_cast<double*>(P.freal)[oc] = (double)n_cur * TWO_POW_M40 / P.deg[sl];
+                    static_cast<double*>(P.freal)[oc] = (double)n * TWO_POW_M40 / P.deg[sl];
                 else
-                    static_cast<float*>(P.freal)[oc] = (BZ_HW_CVT ? __ll2float_rn(n_cur) : ll2float_rn(n_cur)) * P.fscale[sl];
+                    static_cast<float*>(P.freal)[oc] = (BZ_HW_CVT ? __ll2float_rn(n) : ll2float_rn(n)) * P.fscale[sl];
             }
-            fz_prev = fz_cur;
-            fz_cur = fz_next;
-            n_cur = n_nx;
-            i_cur = i_nx;
         }
+        if (++ci == per_row) {
+            ci = 0;
+            ++cr;
+        }
+        cs = cs + 1 == D ? 0 : cs + 1;
     }
+    cp_async_wait<0>();
 }
 
 static int device_sms()
@@ -539,12 +634,11 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
     const int64_t tiles = (a.npc + DRIFT_TILE - 1) / DRIFT_TILE;
     if (rows < 1 || rows > 2147483647LL || tiles > 65535) return cudaErrorInvalidConfiguration;
     const bool moving = a.nx[0] > 1 || a.nx[1] > 1 || a.nx[2] > 1;
-    if (moving && !a.inv_e) return cudaErrorInvalidValue;  // the drift kernels read the inverse energies
-    if (moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
-    if (a.force && !(a.inv_e && a.gforce && moving)) return cudaErrorInvalidValue;
+    if (moving && !(a.inv_e && a.m2f)) return cudaErrorInvalidValue;  // scratch of the moving forms
+    if (a.force && !(a.gforce && moving)) return cudaErrorInvalidValue;
     if (a.force) k_force_grad<<<(unsigned)((a.nxc * 4 + 127) / 128), 128, 0, s>>>(a);
     const int64_t nslots = rows / a.nxc;
-    if (a.inv_e && moving && a.dtdxf < 1.99f && a.nx[2] <= PLANE_MAX_NZ) {
+    if (moving && a.dtdxf < 1.99f && a.nx[2] <= PLANE_MAX_NZ) {
         // y segments: enough threads for every SM at full occupancy
         const int64_t base = nslots * a.nx[0] * a.npc;
         int64_t nseg = ((int64_t)device_sms() * BZ_PLANE_THREADS_PER_SM + base - 1) / base;
@@ -552,17 +646,26 @@ cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)
         const int64_t gs = nslots * a.nx[0] * nseg, gj = (a.npc + PLANE_THREADS - 1) / PLANE_THREADS;
         const int64_t gx = BZ_PLANE_XFAST ? gs : gj, gy = BZ_PLANE_XFAST ? gj : gs;
         if (gy <= 65535 && gx <= 2147483647LL) {
-            const size_t smem = sizeof(long long) * PLANE_THREADS * (size_t)a.nx[2];
+            const size_t smem = sizeof(long long) * PLANE_THREADS * ((size_t)a.nx[2] + 2 * BZ_DPIPE);
+            if (smem > 48 * 1024) {
+                const cudaError_t e =
+                    a.force ? cudaFuncSetAttribute(k_drift_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_drift_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
             const dim3 grid((unsigned)gx, (unsigned)gy);
+            const float K = a.dtdxf * 1073741824.0f;
+            k_mass_table<<<(unsigned)((a.nxc * 4 + 255) / 256), 256, 0, s>>>(a);
             if (a.force)
-                k_drift_plane<true><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, a.dtdxf * 1073741824.0f);
+                k_drift_stream<true><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, K);
             else
-                k_drift_plane<false><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, a.dtdxf * 1073741824.0f);
+                k_drift_stream<false><<<grid, PLANE_THREADS, smem, s>>>(a, (int)nseg, K);
             return cudaGetLastError();
         }
     }
     DriftArgs b = a;
     if (!moving) b.inv_e = nullptr;
+    if (moving) k_inv_energy<<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(a);
     if (a.dtdxf < 1.99f)  // |C| <= 2^30 dt/dx < 2^31
         k_drift<true><<<dim3((unsigned)rows, (unsigned)tiles), DRIFT_THREADS, 0, s>>>(b);
     else
