@@ -304,7 +304,7 @@ __global__ void k_force_grad(const __grid_constant__ DriftArgs P)
 __device__ __forceinline__ long long force_flux(long long n, float g, float inv, float K)
 {
     const float w = ((-g) * inv) * K;
-    if (fabsf(w) < 2147483648.0f) return flux32((int)(n >> 32), (unsigned)n, rint_split(w));
+    if (fabsf(w) < 2147483648.0f) return flux32((int)(n >> 32), (unsigned)n, __float2int_rn(w));
     return flux_fx(n, rint_ll(w));
 }
 
@@ -829,7 +829,7 @@ __device__ __forceinline__ void moments_block(const MomentArgs& P, int64_t x, in
             s_nl += nl;
             s_nh += nh;
             if (ew < 2147483648.0f) {  // E_fx < 2^31 (ew is >= 0 or NaN)
-                const unsigned Efx = (unsigned)rint_split(ew);
+                const unsigned Efx = (unsigned)__float2int_rn(ew);  // round half even
                 const unsigned long long tl = (unsigned long long)Efx * nl;
                 el_lo += tl;
                 el_hi += el_lo < tl;

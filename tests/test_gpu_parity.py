@@ -204,6 +204,8 @@ DRIFT_CASES = [
     ((2, 5, 3), (4, 6, 4), 0x11, 0.39, (-0.2, 0.6)),    # dt/dx = 1.95, narrow integer form
     ((2, 3, 2), (4, 4, 4), 0x01, 0.45, (0.0, 0.6)),     # dt/dx = 2.25, wide (128-bit) form
     ((1, 2, 41), (4, 4, 4), 0x01, 0.05, (0.0, 0.6)),    # n_z above the plane kernel's buffer
+    ((2, 2, 40), (4, 4, 4), 0x01, 0.1, (-0.2, 0.6)),    # n_z at the plane kernel's largest buffer
+    ((10, 16, 2), (16, 16, 16), 0x01, 0.1, (0.0, 0.6)),  # y segments of several rows (1.3 M cells)
     ((7, 6, 5), (6, 8, 10), 0x7F, 0.1, (-0.1, 0.6)),    # 7 species, ragged
     ((2, 3, 4), (4, 6, 4), 0x01, 0.3, (-1e4, 1e4)),     # |n| near 2^57: large high words in every flux
     ((2, 2, 3), (4, 4, 4), 0x01, 0.45, (-1e4, 1e4)),    # the same through the 128-bit (wide) form
