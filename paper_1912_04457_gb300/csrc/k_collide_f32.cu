@@ -5,7 +5,7 @@
 // warp-uniform.  Per term of d's equation (Eqs. C_gluon / C_quark):
 //   phase A (every lane): E3, D, kappa, H and the two k1z candidates of
 //     Eq. (work out delta E); ill-conditioned terms (|H| < tau kappa^2) go to
-//     the FP64 queue; each valid root inside the box is appended, as
+//     the float-float re-evaluation queue; each valid root inside the box is appended, as
 //     (lane, term, z, E3, sqrt H), to a per-warp ring in shared memory;
 //   phase B (whenever 32 roots are pending, and at the end): all 32 lanes
 //     take one root each and evaluate E1, s, t, u, |M|^2, the leg bins, W
@@ -82,7 +82,7 @@ __device__ __forceinline__ int bin_word(uint32_t x, int n)
 }
 
 // A solved coordinate within nu bin widths of a bin (or box) edge: FP32
-// rounding could put it on the other side, so the term goes to FP64.  k2x,
+// rounding could put it on the other side, so the term is re-evaluated in float-float.  k2x,
 // k2y carry a few ulps (EDGE_XY); a root's error grows with the
 // conditioning |kappa|/sqrt(H) of the quadratic (EDGE_Z per unit of it).
 constexpr float EDGE_XY = 1e-5f;
@@ -304,34 +304,28 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 const float D = E * E - Pz * Pz;
                 const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
                 const float H = kap * kap - a2 * D;
-                bool v0 = false, v1 = false, defer = false;
-                z0 = z1 = sqH = 0.0f;
-                if (act && D > 0.0f) {
-                    // float-float re-evaluation when the term is ill-conditioned
-                    // (|H| < tau kappa^2) or a solved coordinate sits on an edge
-                    defer = may_defer && fabsf(H) < P.tau * (kap * kap);
-                    if (H > 0.0f) {
-                        sqH = sqrtf(H);
-                        const float kp = kap * Pz;
-                        const float sq = E * sqH;
-                        const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-                        if (Q != 0.0f) {
-                            z0 = Q / D;
-                            z1 = (E * E * a2 - kap * kap) / Q;
-                            // kappa + Pz z = E E2 at a root: valid iff 0 < E2 < E
-                            const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
-                            const bool e0 = w0 > 0.0f && w0 < EE, e1v = w1 > 0.0f && w1 < EE;
-                            if (may_defer && !defer) {
-                                const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                                defer = (marg_xy && (e0 || e1v))
-                                        || (e0 && (near_edge(z0, L, inv_dp2, nu) || near_edge(Pz - z0, L, inv_dp2, nu)))
-                                        || (e1v && (near_edge(z1, L, inv_dp2, nu) || near_edge(Pz - z1, L, inv_dp2, nu)));
-                            }
-                            v0 = k2xy_in && e0 && in_box(z0, L) && in_box(Pz - z0, L);
-                            v1 = k2xy_in && e1v && in_box(z1, L) && in_box(Pz - z1, L);
-                        }
-                    }
-                }
+                // straight-line form (no divergent branches): every lane evaluates the
+                // roots, and the flags select; float-float re-evaluation when the term is
+                // ill-conditioned (|H| < tau kappa^2) or a solved coordinate sits on an edge
+                const bool ok = act & (D > 0.0f);
+                const bool hp = ok & (H > 0.0f);
+                bool defer = ok & may_defer & (fabsf(H) < P.tau * (kap * kap));
+                sqH = sqrtf(H);
+                const float kp = kap * Pz;
+                const float sq = E * sqH;
+                const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                const bool qv = hp & (Q != 0.0f);
+                z0 = Q / D;
+                z1 = (E * E * a2 - kap * kap) / Q;
+                const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
+                const bool e0 = qv & (w0 > 0.0f) & (w0 < EE), e1v = qv & (w1 > 0.0f) & (w1 < EE);
+                const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+                const bool edge = (marg_xy & (e0 | e1v))
+                                  | (e0 & (near_edge(z0, L, inv_dp2, nu) | near_edge(Pz - z0, L, inv_dp2, nu)))
+                                  | (e1v & (near_edge(z1, L, inv_dp2, nu) | near_edge(Pz - z1, L, inv_dp2, nu)));
+                defer = defer | (may_defer & edge);
+                const bool v0 = k2xy_in & e0 & in_box(z0, L) & in_box(Pz - z0, L);
+                const bool v1 = k2xy_in & e1v & in_box(z1, L) & in_box(Pz - z1, L);
                 gfl = (int)v0 | ((int)v1 << 1) | ((int)defer << 2);
                 S.gz0[lane] = z0; S.gz1[lane] = z1; S.gE3[lane] = E3; S.gsq[lane] = sqH; S.gfl[lane] = gfl;
             } else {
