@@ -41,14 +41,11 @@ struct WarpSmem {
     float3 tlc[4];                // learned: t2_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
     // pending roots
     float z[RING], E3[RING], sqH[RING];
-    int tag[RING];                // live-sample sequence number | term << 24
+    unsigned tag[RING];           // live-sample sequence number | first term << 24 | (terms - 1) << 28
     // this unit's terms: masses of the legs and sym, packed leg slots / flags / row
     float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
     int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
-    int tfirst[MAX_TERMS];        // the term opens a kinematic group (its roots are solved, not reused)
-    // the running kinematic group's roots, per lane
-    float gz0[32], gz1[32], gE3[32], gsq[32];
-    int gfl[32];                  // root 0 valid | root 1 valid << 1 | defer << 2
+    int tgn[MAX_TERMS];           // terms of the kinematic group the term opens (0: not a group's first)
 };
 
 __device__ __forceinline__ float unif23(uint32_t x)
@@ -161,13 +158,18 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     const float fp = P.analytic ? 0.0f : __ldg(static_cast<const float*>(P.f) + a);
 
     const int nt = P.nterms[d];
+    // kinematic groups: consecutive terms with equal leg masses (the first
+    // term of each is flagged); a group's size is the distance to the next first
+    const bool gfirst = lane < nt && P.terms[d][lane].gfirst;
+    const unsigned firsts = __ballot_sync(0xffffffffu, gfirst);
     if (lane < nt) {
         const TermDev& T = P.terms[d][lane];
         S.tm[lane] = make_float4(sel4(T.mslot[0], m0, m1, m2v, m3), sel4(T.mslot[1], m0, m1, m2v, m3),
                                  sel4(T.mslot[2], m0, m1, m2v, m3), (float)T.sym);
         S.tinfo[lane] = T.slot[0] | (T.slot[1] << 3) | (T.slot[2] << 6) | (T.quark[0] << 9) | (T.quark[1] << 10)
                         | (T.quark[2] << 11) | (T.quark[3] << 12) | (T.cls << 13);
-        S.tfirst[lane] = T.gfirst;
+        const unsigned after = firsts & ~((2u << lane) - 1u);
+        S.tgn[lane] = gfirst ? (after ? __ffs(after) - 1 : nt) - lane : 0;
     }
     const float md2 = sel4(P.terms[d][0].mslot[3], m0, m1, m2v, m3);
     float pm0 = 0.0f, pm1 = 0.0f, pm2 = 0.0f, ps3 = 1.0f, ps1 = 1.0f, pa = 1.0f;
@@ -198,12 +200,11 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     auto process = [&](int n) {
         if (lane < n) {
             const int ri = (head + lane) & (RING - 1);
-            const int tg = S.tag[ri];
-            const int src = tg & (SBUF - 1), ti = tg >> 24;
+            const unsigned tg = S.tag[ri];
+            const int src = tg & (SBUF - 1), t0 = (tg >> 24) & 15, tn = (int)(tg >> 28) + 1;
             const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
-            const float4 tmv = S.tm[ti];
-            const int info = S.tinfo[ti];
-            const float ma2 = tmv.x, mc2 = tmv.z;
+            const float4 tmv0 = S.tm[t0];  // leg masses shared by the group's terms
+            const float ma2 = tmv0.x, mc2 = tmv0.z;
             const float Ep = S.Ep[src];
             const float E = Ep + E3;
             const float a2 = S.a2m[src] + ma2;
@@ -215,49 +216,54 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
             const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
             if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
-                red_add(&P.flags[0], 1);
+                red_add(&P.flags[0], tn);
             } else {
-                const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
                 const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
                 const int lin2 = S.b2xy[src] * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
-                const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
-                const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
-                const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
-                float f1, f2, f3, fpp;
-                if (P.analytic) {
-                    const float E2 = E - E1;
-                    f1 = f_equilibrium(P, P.slot_species[info & 7], E1);
-                    f2 = f_equilibrium(P, P.slot_species[(info >> 3) & 7], E2);
-                    f3 = f_equilibrium(P, P.slot_species[(info >> 6) & 7], E3);
-                    fpp = f_equilibrium(P, d, Ep);
-                } else {
-                    const float* F = static_cast<const float*>(P.f);
-                    f1 = __ldg(F + i1);
-                    f2 = __ldg(F + i2);
-                    f3 = __ldg(F + i3);
-                    fpp = fp;
-                }
-                const float F1 = (info & (1 << 9)) ? 1.0f - f1 : 1.0f + f1;
-                const float F2 = (info & (1 << 10)) ? 1.0f - f2 : 1.0f + f2;
-                const float F3 = (info & (1 << 11)) ? 1.0f - f3 : 1.0f + f3;
-                const float Fp = (info & (1 << 12)) ? 1.0f - fpp : 1.0f + fpp;
-                const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
                 // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                 const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
-                const float ct = tmv.w * W * M2 / den;
-                const float wq = ct * P.Kown * (MODE == M_LEARNED ? S.wfac[src] : 1.0f);
-                if (MODE == M_RECORD) {  // record mode: sum |c~| per sample, no deposits
-                    atomicAdd(&S.wfac[src], fabsf(ct));
-                } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
-                    red_add(&P.flags[1], 1);
-                } else {
-                    const long long q = rint_ll(wq);
-                    if (q != 0) {
-                        own += q;
-                        if (P.sampler != 1) {
-                            red_add(&P.A[i3], q);
-                            red_add(&P.A[i1], -q);
-                            red_add(&P.A[i2], -q);
+                for (int k = 0; k < tn; ++k) {  // the group's terms: |M|^2, leg species, statistics
+                    const int ti = t0 + k;
+                    const float sym = S.tm[ti].w;
+                    const int info = S.tinfo[ti];
+                    const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
+                    const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
+                    const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
+                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
+                    float f1, f2, f3, fpp;
+                    if (P.analytic) {
+                        const float E2 = E - E1;
+                        f1 = f_equilibrium(P, P.slot_species[info & 7], E1);
+                        f2 = f_equilibrium(P, P.slot_species[(info >> 3) & 7], E2);
+                        f3 = f_equilibrium(P, P.slot_species[(info >> 6) & 7], E3);
+                        fpp = f_equilibrium(P, d, Ep);
+                    } else {
+                        const float* F = static_cast<const float*>(P.f);
+                        f1 = __ldg(F + i1);
+                        f2 = __ldg(F + i2);
+                        f3 = __ldg(F + i3);
+                        fpp = fp;
+                    }
+                    const float F1 = (info & (1 << 9)) ? 1.0f - f1 : 1.0f + f1;
+                    const float F2 = (info & (1 << 10)) ? 1.0f - f2 : 1.0f + f2;
+                    const float F3 = (info & (1 << 11)) ? 1.0f - f3 : 1.0f + f3;
+                    const float Fp = (info & (1 << 12)) ? 1.0f - fpp : 1.0f + fpp;
+                    const float W = f1 * f2 * F3 * Fp - F1 * F2 * f3 * fpp;
+                    const float ct = sym * W * M2 / den;
+                    const float wq = ct * P.Kown * (MODE == M_LEARNED ? S.wfac[src] : 1.0f);
+                    if (MODE == M_RECORD) {  // record mode: sum |c~| per sample, no deposits
+                        atomicAdd(&S.wfac[src], fabsf(ct));
+                    } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
+                        red_add(&P.flags[1], 1);
+                    } else {
+                        const long long q = rint_ll(wq);
+                        if (q != 0) {
+                            own += q;
+                            if (P.sampler != 1) {
+                                red_add(&P.A[i3], q);
+                                red_add(&P.A[i1], -q);
+                                red_add(&P.A[i2], -q);
+                            }
                         }
                     }
                 }
@@ -284,78 +290,73 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         }
         flush = false;
         if (ti >= 0 && ti < nt) {
-            // ---- phase A: term ti for this lane's live sample.  Terms of one
-            // kinematic group (equal leg masses) share E3, D, kappa, H, the roots
-            // and the FP64 deferral decision: the group's first term solves them,
-            // the others reuse them from shared memory. ----
+            // ---- phase A: the kinematic group opened by term ti, for this lane's
+            // live sample.  Its terms (equal leg masses) share E3, D, kappa, H, the
+            // roots and the re-evaluation decision; each valid root goes to the
+            // ring once, tagged with the group's terms. ----
             const int seq = bstart + lane;
-            int gfl;
-            float z0, z1, E3, sqH;
-            if (S.tfirst[ti]) {
-                const bool act = lane < bcnt;
-                const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
-                const float4 tmv = S.tm[ti];
-                const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
-                E3 = sqrtf(bkk3 + mc2);
-                const float E = bEp + E3;
-                const float Pz = bPz;
-                const float a2 = ba2m + ma2;
-                const float b2 = bb2m + mb2;
-                const float D = E * E - Pz * Pz;
-                const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
-                const float H = kap * kap - a2 * D;
-                // straight-line form (no divergent branches): every lane evaluates the
-                // roots, and the flags select; float-float re-evaluation when the term is
-                // ill-conditioned (|H| < tau kappa^2) or a solved coordinate sits on an edge
-                const bool ok = act & (D > 0.0f);
-                const bool hp = ok & (H > 0.0f);
-                bool defer = ok & may_defer & (fabsf(H) < P.tau * (kap * kap));
-                sqH = sqrtf(H);
-                const float kp = kap * Pz;
-                const float sq = E * sqH;
-                const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-                const bool qv = hp & (Q != 0.0f);
-                z0 = Q / D;
-                z1 = (E * E * a2 - kap * kap) / Q;
-                const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
-                const bool e0 = qv & (w0 > 0.0f) & (w0 < EE), e1v = qv & (w1 > 0.0f) & (w1 < EE);
-                const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-                const bool edge = (marg_xy & (e0 | e1v))
-                                  | (e0 & (near_edge(z0, L, inv_dp2, nu) | near_edge(Pz - z0, L, inv_dp2, nu)))
-                                  | (e1v & (near_edge(z1, L, inv_dp2, nu) | near_edge(Pz - z1, L, inv_dp2, nu)));
-                defer = defer | (may_defer & edge);
-                const bool v0 = k2xy_in & e0 & in_box(z0, L) & in_box(Pz - z0, L);
-                const bool v1 = k2xy_in & e1v & in_box(z1, L) & in_box(Pz - z1, L);
-                gfl = (int)v0 | ((int)v1 << 1) | ((int)defer << 2);
-                S.gz0[lane] = z0; S.gz1[lane] = z1; S.gE3[lane] = E3; S.gsq[lane] = sqH; S.gfl[lane] = gfl;
-            } else {
-                z0 = S.gz0[lane]; z1 = S.gz1[lane]; E3 = S.gE3[lane]; sqH = S.gsq[lane]; gfl = S.gfl[lane];
-            }
-            bool v0 = gfl & 1, v1 = (gfl >> 1) & 1;
-            if (gfl & 4) {  // queued for re-evaluation; when the queue is full the FP32 roots stand
-                const int qs = atomicAdd(dq.s_count, 1);
-                if (qs < dq.cap) {
-                    dq.seg[qs] = box_tag | ((unsigned long long)a << 24)
-                                 | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)ti;
-                    v0 = v1 = false;
-                } else {
-                    red_add(&P.flags[3], 1);
-                }
+            const int gn = S.tgn[ti];
+            const bool act = lane < bcnt;
+            const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
+            const float4 tmv = S.tm[ti];
+            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
+            const float E3 = sqrtf(bkk3 + mc2);
+            const float E = bEp + E3;
+            const float Pz = bPz;
+            const float a2 = ba2m + ma2;
+            const float b2 = bb2m + mb2;
+            const float D = E * E - Pz * Pz;
+            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+            const float H = kap * kap - a2 * D;
+            // straight-line form (no divergent branches): every lane evaluates the
+            // roots, and the flags select; float-float re-evaluation when the term is
+            // ill-conditioned (|H| < tau kappa^2) or a solved coordinate sits on an edge
+            const bool ok = act & (D > 0.0f);
+            const bool hp = ok & (H > 0.0f);
+            bool defer = ok & may_defer & (fabsf(H) < P.tau * (kap * kap));
+            const float sqH = sqrtf(H);
+            const float kp = kap * Pz;
+            const float sq = E * sqH;
+            const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+            const bool qv = hp & (Q != 0.0f);
+            const float z0 = Q / D;
+            const float z1 = (E * E * a2 - kap * kap) / Q;
+            const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
+            const bool e0 = qv & (w0 > 0.0f) & (w0 < EE), e1v = qv & (w1 > 0.0f) & (w1 < EE);
+            const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+            const bool edge = (marg_xy & (e0 | e1v))
+                              | (e0 & (near_edge(z0, L, inv_dp2, nu) | near_edge(Pz - z0, L, inv_dp2, nu)))
+                              | (e1v & (near_edge(z1, L, inv_dp2, nu) | near_edge(Pz - z1, L, inv_dp2, nu)));
+            defer = defer | (may_defer & edge);
+            bool v0 = k2xy_in & e0 & in_box(z0, L) & in_box(Pz - z0, L);
+            bool v1 = k2xy_in & e1v & in_box(z1, L) & in_box(Pz - z1, L);
+            int t0 = ti, tn = gn;  // terms whose roots phase B evaluates
+            if (defer) {  // queued for re-evaluation; when the queue is full the FP32 roots stand
+                const int qs = atomicAdd(dq.s_count, gn);
+                const int nq = min(gn, max(0, dq.cap - qs));
+                for (int k = 0; k < nq; ++k)
+                    dq.seg[qs + k] = box_tag | ((unsigned long long)a << 24)
+                                     | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)(ti + k);
+                if (nq < gn) red_add(&P.flags[3], gn - nq);
+                t0 = ti + nq;
+                tn = gn - nq;
+                if (tn == 0) v0 = v1 = false;
             }
             // append the valid roots to the ring
+            const unsigned tag = (unsigned)seq | ((unsigned)t0 << 24) | ((unsigned)(tn - 1) << 28);
             const unsigned b0 = __ballot_sync(0xffffffffu, v0);
             const unsigned b1 = __ballot_sync(0xffffffffu, v1);
             const int n0 = __popc(b0);
             if (v0) {
                 const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
-                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = seq | (ti << 24);
+                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
             }
             if (v1) {
                 const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
-                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = seq | (ti << 24);
+                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
             }
             tail += n0 + __popc(b1);
-            ++ti;
+            ti += gn;
             __syncwarp();
             continue;
         }
