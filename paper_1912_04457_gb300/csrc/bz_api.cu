@@ -1417,7 +1417,7 @@ static int batch_autotune(bz_batch b, long long* state, double dt, cudaStream_t 
     if (!dalloc(&scratch, b->ncell)) return bfail(b, BZ_ENOMEM, "cannot allocate the tuning copy");
     int rc = BZ_OK;
     const int chunks[] = {1, 2, 4, 8, 16};
-    const int bpss[] = {16 / F32_WARPS, 24 / F32_WARPS, 28 / F32_WARPS};  // 16, 24, 28 warps per SM
+    const int bpss[] = {16 / F32_WARPS, 20 / F32_WARPS, 24 / F32_WARPS};  // 16, 20, 24 warps per SM (24 resident at most)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -28,7 +28,7 @@ constexpr int RING = 128;         // pending roots per warp (power of 2)
 constexpr int SBUF = 64;          // buffered live samples per warp (power of 2)
 constexpr int WARPS = F32_WARPS;  // warps per block
 #ifndef BZ_F32_MIN_BLOCKS
-#define BZ_F32_MIN_BLOCKS (28 / WARPS)  // resident blocks per SM the register budget is cut for
+#define BZ_F32_MIN_BLOCKS (24 / WARPS)  // resident blocks per SM the register budget is cut for (80 registers)
 #endif
 
 struct WarpSmem {
