@@ -119,7 +119,7 @@ enum { M_UNIFORM = 0, M_LEARNED = 1, M_RECORD = 2 };
 // compacted into the live-sample buffer, and the roots are solved on full
 // warps of live samples.  box_tag is or-ed into queued items (the box index
 // << 48 in a batch).
-template <int MODE>
+template <int MODE, bool GROUPS>
 __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
                                              DeferCtx& dq, unsigned long long box_tag)
 {
@@ -201,7 +201,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         if (lane < n) {
             const int ri = (head + lane) & (RING - 1);
             const unsigned tg = S.tag[ri];
-            const int src = tg & (SBUF - 1), t0 = (tg >> 24) & 15, tn = (int)(tg >> 28) + 1;
+            const int src = tg & (SBUF - 1), t0 = (tg >> 24) & 15, tn = GROUPS ? (int)(tg >> 28) + 1 : 1;
             const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
             const float4 tmv0 = S.tm[t0];  // leg masses shared by the group's terms
             const float ma2 = tmv0.x, mc2 = tmv0.z;
@@ -295,7 +295,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             // roots and the re-evaluation decision; each valid root goes to the
             // ring once, tagged with the group's terms. ----
             const int seq = bstart + lane;
-            const int gn = S.tgn[ti];
+            const int gn = GROUPS ? S.tgn[ti] : 1;  // without GROUPS every group has one term
             const bool act = lane < bcnt;
             const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
             const float4 tmv = S.tm[ti];
@@ -537,7 +537,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
 // device memory, so a captured graph replays with the same parameters.
 // Both walk through the one call site of collide_unit: a box gives the same
 // bits alone or inside a batch.
-template <int MODE>
+template <int MODE, bool GROUPS>
 __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(const __grid_constant__ CollideArgs<float> one,
                                                         const CollideArgs<float>* __restrict__ boxes,
                                                         const int64_t* __restrict__ prefix, int nboxes,
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
             break;
         }
         const CollideArgs<float>& P = batch ? boxes[b] : one;
-        collide_unit<MODE>(P, batch ? u - prefix[b] : u, step, smem[warp], dq, (unsigned long long)b << 48);
+        collide_unit<MODE, GROUPS>(P, batch ? u - prefix[b] : u, step, smem[warp], dq, (unsigned long long)b << 48);
         u += batch ? 1 : nwarps;
     }
     __syncwarp();
@@ -593,17 +593,30 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
     }
 }
 
+// Some equation has a kinematic group of several terms (else every ring
+// entry carries one term and phase B needs no loop over a group).
+static bool has_groups(const CollideArgs<float>& a)
+{
+    for (int d = 0; d < NSPEC; ++d)
+        for (int t = 1; t < a.nterms[d]; ++t)
+            if (!a.terms[d][t].gfirst) return true;
+    return false;
+}
+
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
 {
     if (a.rec_stride)
-        k_collide_f32<M_RECORD><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
-                                                             a.qitems, a.qcap);
+        k_collide_f32<M_RECORD, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                                   a.qitems, a.qcap);
     else if (a.sampler == SAMPLER_LEARNED)
-        k_collide_f32<M_LEARNED><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
-                                                              a.qitems, a.qcap);
+        k_collide_f32<M_LEARNED, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                                    a.qitems, a.qcap);
+    else if (has_groups(a))
+        k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+                                                                    a.qitems, a.qcap);
     else
-        k_collide_f32<M_UNIFORM><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
-                                                              a.qitems, a.qcap);
+        k_collide_f32<M_UNIFORM, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0,
+                                                                     a.qcount, a.qitems, a.qcap);
     return cudaGetLastError();
 }
 
@@ -612,7 +625,7 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
                                      int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s)
 {
     const CollideArgs<float> none{};
-    k_collide_f32<M_UNIFORM><<<grid, 32 * WARPS, 0, s>>>(none, boxes, prefix, nboxes, counter, step_dev, chunk, qcount,
+    k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(none, boxes, prefix, nboxes, counter, step_dev, chunk, qcount,
                                                           qitems, qcap);
     return cudaGetLastError();
 }
