@@ -15,6 +15,7 @@ oracle on a bounded sample of anchors of the same workload.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -102,9 +103,14 @@ class ClockSampler:
 
 
 def source_hash():
+    """Hash of the collision kernel's sources without comments and blank
+    space, so that the committed ncu traffic is tied to the code it measured."""
     h = hashlib.sha256()
     for f in ("collide.cuh", "k_collide_f32.cu", "bz_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1912_04457_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1912_04457_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -2,16 +2,19 @@
 //
 // Work unit: one anchor (species d, x cell, p cell) and 32 of its samples,
 // one sample per lane, so the anchor's index decode, masses and f_p are
-// warp-uniform.  Per term of d's equation (Eqs. C_gluon / C_quark):
+// warp-uniform.  Per kinematic group of d's equation (Eqs. C_gluon /
+// C_quark: consecutive terms whose legs k1, k2, k3 carry equal masses):
 //   phase A (every lane): E3, D, kappa, H and the two k1z candidates of
 //     Eq. (work out delta E); ill-conditioned terms (|H| < tau kappa^2) go to
-//     the float-float re-evaluation queue; each valid root inside the box is appended, as
-//     (lane, term, z, E3, sqrt H), to a per-warp ring in shared memory;
+//     the float-float re-evaluation queue; each valid root inside the box is
+//     appended once, as (lane, the group's terms, z, E3, sqrt H), to a
+//     per-warp ring in shared memory;
 //   phase B (whenever 32 roots are pending, and at the end): all 32 lanes
-//     take one root each and evaluate E1, s, t, u, |M|^2, the leg bins, W
-//     and c~ (Eq. ca), using |J| E1 E2 = sqrt(H) at a root, then deposit the
-//     int64 weight to the k1, k2, k3 legs; the anchor's own +q is summed in
-//     registers and over the warp, one reduction per unit.
+//     take one root each and evaluate E1, s, t, u and the solved legs' bins,
+//     then for each term of the group |M|^2, W and c~ (Eq. ca), using
+//     |J| E1 E2 = sqrt(H) at a root, and deposit the int64 weight to the
+//     k1, k2, k3 legs; the anchor's own +q is summed in registers and over
+//     the warp, one reduction per unit.
 // The per-lane sample geometry lives in shared memory so phase B can read
 // any lane's sample.  Uniforms: u = ((x >> 9) + 1/2) 2^-23 built from the
 // mantissa bits; weights are rounded to int64 with integer operations only,
