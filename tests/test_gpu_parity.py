@@ -175,6 +175,26 @@ def test_collision_f32_within_tolerance(np_, mask, N):
     assert rel_l2(got, ref) <= F32_TOL
 
 
+@pytest.mark.parametrize("mask,N", [(0x7F, 48), (0x13, 40)])
+def test_collision_f32_massless_one_group(mask, N):
+    """With the massless dispersion every term of an equation has the same
+    kinematics, so all of them (up to ten) form one group and ride on each
+    root that phase B evaluates."""
+    from paper_1912_04457_gb300 import bz
+    torch = torch_mod()
+    np_ = (8, 8, 8)
+    h, cfg = make_pair(np_=np_, mask=mask, seed=4, mass_mode=1)
+    st = random_state(mask, 1, np_, 13, 0.05, 0.5)
+    A = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    h.collision_term(to_dev(st), A, N, 2, 0.01, bz.PREC_F32)
+    m2 = O.masses(cfg, st)
+    ref = O.collision(cfg, st, m2, N, step=2, dt=0.01, ubits=23)["A"]
+    got = A.cpu().numpy().reshape(ref.shape)
+    assert int(got.sum()) == 0
+    assert rel_l2(got, ref) <= F32_TOL
+    assert np.count_nonzero(ref) > 0
+
+
 def test_equilibrium_vanishes_on_gpu():
     from paper_1912_04457_gb300 import bz
     torch = torch_mod()
