@@ -419,6 +419,18 @@ int bz_set_step_sampler(bz_handle h, int32_t sampler);
 int bz_save(bz_handle h, const int64_t* state, int64_t step, const char* path);
 int bz_load(bz_handle h, int64_t* state, int64_t* step, const char* path);
 
+/* Bounds-checked builds (compiled with -DBZ_CHECK=1, a stand-in for a
+ * memory sanitizer): the collision (FP64, FP32 and its re-evaluation) and the
+ * streaming drift kernels test every index they compute into f, A, the
+ * state and the mass table before the access, skip an access outside its
+ * buffer and count it.  count: indices outside their buffers since the
+ * last reset (host, may be NULL); first_bad: one of them, -1 if none (host,
+ * may be NULL); reset = 1 clears the counters after reading.  The counters
+ * are read with a synchronous copy: synchronize the streams that ran the
+ * kernels first.  Errors: BZ_EINVAL in a build without BZ_CHECK (the
+ * default), BZ_ECUDA if the copy fails. */
+int bz_check_counts(int64_t* count, int64_t* first_bad, int32_t reset);
+
 /* Library version string. */
 const char* bz_version(void);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "bz_proposal_anchor_params": (C.c_int, [_P, _P, _P]),
     "bz_set_step_sampler": (C.c_int, [_P, _I32]),
     "bz_version": (C.c_char_p, []),
+    "bz_check_counts": (C.c_int, [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
 }
 
 
@@ -464,3 +465,14 @@ def collision_term_static(nx, dx, np_, L, seed, species_mask, alpha_s, mass_mode
 
 def version():
     return load().bz_version().decode()
+
+
+def check_counts(reset=False):
+    """(indices outside their buffers, one of them or -1) of a library built
+    with BZ_CHECK=1; raises BzError in the default build."""
+    lib = load()
+    n, first = C.c_int64(), C.c_int64()
+    rc = lib.bz_check_counts(C.byref(n), C.byref(first), 1 if reset else 0)
+    if rc != 0:
+        raise BzError(rc, lib.bz_last_error(None).decode())
+    return n.value, first.value

@@ -237,6 +237,23 @@ static void set_slots(bz_handle h)
 
 extern "C" const char* bz_version(void) { return "libbz 0.1 (sm_103a)"; }
 
+extern "C" int bz_check_counts(int64_t* count, int64_t* first_bad, int32_t reset)
+{
+    unsigned long long c[3][2];
+    const cudaError_t e[3] = {check_read_collide_f32(c[0], reset != 0), check_read_collide_f64(c[1], reset != 0),
+                              check_read_transport(c[2], reset != 0)};
+    if (e[0] == cudaErrorNotSupported) return fail(nullptr, BZ_EINVAL, "the library was built without BZ_CHECK");
+    long long n = 0, first = -1;
+    for (int u = 0; u < 3; ++u) {
+        if (e[u] != cudaSuccess) return fail(nullptr, BZ_ECUDA, "reading the check counters: %s", cudaGetErrorString(e[u]));
+        n += (long long)c[u][0];
+        if (first < 0 && c[u][0]) first = (long long)c[u][1];
+    }
+    if (count) *count = n;
+    if (first_bad) *first_bad = first;
+    return BZ_OK;
+}
+
 extern "C" const char* bz_last_error(bz_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
 
 extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
@@ -667,6 +684,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     a.flags = h->d_flags;
     a.nxc = h->nxc;
     a.npc = h->npc;
+    a.ncell = h->ncell;
     for (int d = 0; d < 3; ++d) {
         a.np[d] = h->g.np[d];
         a.dp[d] = (R)(twoL / h->g.np[d]);

@@ -6,6 +6,34 @@
 
 namespace bz {
 
+// Bounds-checked build (compile with -DBZ_CHECK=1): every index that the
+// collision and drift kernels compute into a global buffer is tested before
+// the access; an index outside its buffer is counted, with the first one
+// seen, in the translation unit's counters and the access is skipped, so a
+// wrong index shows up as a count (bz_check_counts) instead of a fault.  The
+// default build compiles the tests away.
+#ifndef BZ_CHECK
+#define BZ_CHECK 0
+#endif
+#ifdef __CUDACC__
+#if BZ_CHECK
+static __device__ unsigned long long g_bz_check[2];  // count, first index outside its buffer
+__device__ __forceinline__ bool bz_in(long long i, long long n)
+{
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&g_bz_check[0], 1ull) == 0ull) g_bz_check[1] = (unsigned long long)i;
+    return false;
+}
+#else
+__device__ __forceinline__ bool bz_in(long long, long long) { return true; }
+#endif
+#endif
+// Counters of each translation unit of a checked build (count, first index);
+// reset clears them.  cudaErrorNotSupported without BZ_CHECK.
+cudaError_t check_read_collide_f32(unsigned long long out[2], bool reset);
+cudaError_t check_read_collide_f64(unsigned long long out[2], bool reset);
+cudaError_t check_read_transport(unsigned long long out[2], bool reset);
+
 constexpr int NSPEC = 7;
 constexpr int MAX_TERMS = 10;
 constexpr int MAX_NP = 256;     // momentum cells per axis
@@ -94,6 +122,7 @@ struct CollideArgs {
     const double* m2;       // [x][4]
     long long* flags;       // [4]
     int64_t nxc, npc;
+    int64_t ncell;          // cells of f and A (slots x nxc x npc)
     int np[3];
     R L, twoL, dp[3];
     double L64, dp64[3];    // L and 2L/n in FP64 (the FP32 path's fixup works in FP64 geometry)

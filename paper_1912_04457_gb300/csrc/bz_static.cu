@@ -226,6 +226,7 @@ extern "C" int bz_collision_term_static(const bz_grid* g, uint32_t species_mask,
     a.flags = sc->flags;
     a.nxc = nxc;
     a.npc = npc;
+    a.ncell = ncell;
     for (int d = 0; d < 3; ++d) {
         a.np[d] = g->np[d];
         a.dp[d] = twoL / g->np[d];

@@ -317,6 +317,7 @@ __device__ __forceinline__ long long eval_term(const CollideArgs<R>& P, const Ge
         const int64_t i1 = (int64_t)T.slot[0] * nxc * npc + G.xoff + lin1;
         const int64_t i2 = (int64_t)T.slot[1] * nxc * npc + G.xoff + lin2;
         const int64_t i3 = (int64_t)T.slot[2] * nxc * npc + G.xoff + G.lin3;
+        if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell) & bz_in(a, P.ncell))) continue;
         R f1, f2, f3, fp;
         if (P.analytic) {
             f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
@@ -441,6 +442,7 @@ __device__ __forceinline__ long long eval_term_k3(const CollideArgs<R>& P, const
         const int64_t i1 = (int64_t)T.slot[0] * nxc * npc + G.xoff + lin1;
         const int64_t i2 = (int64_t)T.slot[1] * nxc * npc + G.xoff + lin2;
         const int64_t i3 = (int64_t)T.slot[2] * nxc * npc + G.xoff + lin3;
+        if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell) & bz_in(a, P.ncell))) continue;
         R f1, f2, f3, fp;
         if (P.analytic) {
             f1 = f_equilibrium(P, P.slot_species[T.slot[0]], E1);
@@ -515,8 +517,8 @@ __global__ void __launch_bounds__(256) k_collide(const __grid_constant__ Collide
         }
         if (warp_anchor) {
             own = warp_sum_ll(own);
-            if (lane == 0 && own != 0) red_add(&P.A[a], own);
-        } else if (own != 0) {
+            if (lane == 0 && own != 0 && bz_in(a, P.ncell)) red_add(&P.A[a], own);
+        } else if (own != 0 && bz_in(a, P.ncell)) {
             red_add(&P.A[a], own);
         }
     }

@@ -233,6 +233,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
                     const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
                     const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
+                    if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell))) continue;
                     float f1, f2, f3, fpp;
                     if (P.analytic) {
                         const float E2 = E - E1;
@@ -527,7 +528,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     }
     if (MODE != M_RECORD) {
         own = warp_sum_ll(own);
-        if (lane == 0 && own != 0) red_add(&P.A[a], own);
+        if (lane == 0 && own != 0 && bz_in(a, P.ncell)) red_add(&P.A[a], own);
     }
     __syncwarp();
 }
@@ -604,6 +605,20 @@ static bool has_groups(const CollideArgs<float>& a)
         for (int t = 1; t < a.nterms[d]; ++t)
             if (!a.terms[d][t].gfirst) return true;
     return false;
+}
+
+cudaError_t check_read_collide_f32(unsigned long long out[2], bool reset)
+{
+#if BZ_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_bz_check, 2 * sizeof(unsigned long long));
+    const unsigned long long zero[2] = {0ull, 0ull};
+    if (e == cudaSuccess && reset) e = cudaMemcpyToSymbol(g_bz_check, zero, sizeof(zero));
+    return e;
+#else
+    out[0] = out[1] = 0ull;
+    (void)reset;
+    return cudaErrorNotSupported;
+#endif
 }
 
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
@@ -827,6 +842,7 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
         const unsigned i1 = (unsigned)T.slot[0] * slot_stride + xoff + lin1;
         const unsigned i2 = (unsigned)T.slot[1] * slot_stride + xoff + lin2;
         const unsigned i3 = (unsigned)T.slot[2] * slot_stride + xoff + lin3;
+        if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell))) continue;
         float f1, f2, f3, fpp;
         if (P.analytic) {
             f1 = f_equilibrium(P, P.slot_species[T.slot[0]], ff_to_float(E1));
@@ -885,7 +901,7 @@ __global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ Colli
         const int64_t a = (int64_t)(it >> 24);
         const int smp = (int)((it >> 4) & 0xFFFFFu), ti = (int)(it & 0xFu);
         const long long own = fixup_term_ff<LEARNED>(P, a, smp, ti, P.step, pc);
-        if (own != 0) red_add(&P.A[a], own);
+        if (own != 0 && bz_in(a, P.ncell)) red_add(&P.A[a], own);
     }
 }
 
@@ -905,7 +921,7 @@ __global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float
         const CollideArgs<float>& P = boxes[(int)(it >> 48)];
         const int64_t a = (int64_t)((it >> 24) & 0xFFFFFFull);
         const long long own = fixup_term_ff<false>(P, a, (int)((it >> 4) & 0xFFFFFu), (int)(it & 0xFu), step, pc);
-        if (own != 0) red_add(&P.A[a], own);
+        if (own != 0 && bz_in(a, P.ncell)) red_add(&P.A[a], own);
     }
 }
 

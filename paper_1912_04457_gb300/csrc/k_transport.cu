@@ -466,7 +466,7 @@ __device__ __forceinline__ long long force_acc_inline(const DriftArgs& P, const 
         const int jo = jv[i] + (up ? 1 : -1), jb = jv[i] + (up ? -1 : 1);
         long long own = 0, behind = 0;
         if (jo >= 0 && jo < P.np[i]) own = force_flux(n, g, inv, P.Kp[i]);
-        if (jb >= 0 && jb < P.np[i]) {
+        if (jb >= 0 && jb < P.np[i] && bz_in(j + (up ? -stride[i] : stride[i]), P.npc)) {
             const int jj = j + (up ? -stride[i] : stride[i]);
             const float q0 = pf[0][i == 0 ? jb : jv[0]], q1 = pf[1][i == 1 ? jb : jv[1]], q2 = pf[2][i == 2 ? jb : jv[2]];
             const float invb = 1.0f / sqrtf((q0 * q0 + q1 * q1) + q2 * q2 + m);
@@ -531,8 +531,11 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_drift_stream(const __grid_con
         const int iy = sy ? tw : ny - 1 - tw;
         const int64_t rw = b_own + (int64_t)iy * nz * zs;
         for (int iz = 0; iz < nz; ++iz) {
-            const float inv = 1.0f / sqrtf(pp + __ldg(m2f + (xo + iy * nz + iz) * 4));
-            fy[iz * PLANE_THREADS] = flux_n(__ldg(in + rw + iz * zs), courant_cvt(p1, inv, K));
+            const int xw = xo + iy * nz + iz;
+            const int64_t ow = rw + iz * zs;
+            if (!(bz_in(xw, P.nxc) & bz_in(ow, P.ncell))) continue;
+            const float inv = 1.0f / sqrtf(pp + __ldg(m2f + xw * 4));
+            fy[iz * PLANE_THREADS] = flux_n(__ldg(in + ow), courant_cvt(p1, inv, K));
         }
     }
     // item i of a row: i < W the wrap cell, else the (i - W)-th cell in upwind order
@@ -544,9 +547,9 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_drift_stream(const __grid_con
             const bool wrap = k < 0;
             if (wrap) k = nz - 1;
             const int iz = sz ? k : nz - 1 - k;
-            const long long* src = in + b_own + ((int64_t)iy * nz + iz) * zs;
-            cp_async8(ring + (2 * ps) * PLANE_THREADS, src);
-            if (mx && !wrap) cp_async8(ring + (2 * ps + 1) * PLANE_THREADS, src + dup);
+            const int64_t o = b_own + ((int64_t)iy * nz + iz) * zs;
+            if (bz_in(o, P.ncell)) cp_async8(ring + (2 * ps) * PLANE_THREADS, in + o);
+            if (mx && !wrap && bz_in(o + dup, P.ncell)) cp_async8(ring + (2 * ps + 1) * PLANE_THREADS, in + o + dup);
             if (++pi == per_row) {
                 pi = 0;
                 ++pr;
@@ -570,7 +573,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_drift_stream(const __grid_con
         if (wrap) k = nz - 1;
         const int iz = sz ? k : nz - 1 - k;
         const int xr = iy * nz + iz;
-        const float m = __ldg(m2f + (xo + xr) * 4);
+        const float m = bz_in(xo + xr, P.nxc) ? __ldg(m2f + (xo + xr) * 4) : 0.0f;
         const float inv = 1.0f / sqrtf(pp + m);
         if (wrap) {
             fz_up = flux_n(n, courant_cvt(p2, inv, K));
@@ -590,21 +593,24 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_drift_stream(const __grid_con
             }
             if (mx) {
                 const long long nu = ring[(2 * cs + 1) * PLANE_THREADS];
-                const float invu = 1.0f / sqrtf(pp + __ldg(m2f + (xuo + xr) * 4));
+                const float invu = 1.0f / sqrtf(pp + (bz_in(xuo + xr, P.nxc) ? __ldg(m2f + (xuo + xr) * 4) : 0.0f));
                 const long long f0 = flux_n(n, courant_cvt(p0, inv, K));
                 const long long fu = flux_n(nu, courant_cvt(p0, invu, K));
                 acc += sx ? f0 - fu : fu - f0;
             }
             const int64_t oc = b_own + (int64_t)xr * zs;
-            if (FORCE)
-                acc += force_acc_inline(P, P.gforce + ((int64_t)(xo + xr) * 4 + ms) * 3, jp, j, in + (oc - j), n, inv,
-                                        s_pf, m);
-            P.out[oc] = n - acc;
-            if (P.freal) {
-                if (P.freal_double)
-                    static_cast<double*>(P.freal)[oc] = (double)n * TWO_POW_M40 / P.deg[sl];
-                else
-                    static_cast<float*>(P.freal)[oc] = (BZ_HW_CVT ? __ll2float_rn(n) : ll2float_rn(n)) * P.fscale[sl];
+            if (bz_in(oc, P.ncell) & bz_in(xo + xr, P.nxc)) {
+                if (FORCE)
+                    acc += force_acc_inline(P, P.gforce + ((int64_t)(xo + xr) * 4 + ms) * 3, jp, j, in + (oc - j), n,
+                                            inv, s_pf, m);
+                P.out[oc] = n - acc;
+                if (P.freal) {
+                    if (P.freal_double)
+                        static_cast<double*>(P.freal)[oc] = (double)n * TWO_POW_M40 / P.deg[sl];
+                    else
+                        static_cast<float*>(P.freal)[oc] =
+                            (BZ_HW_CVT ? __ll2float_rn(n) : ll2float_rn(n)) * P.fscale[sl];
+                }
             }
         }
         if (++ci == per_row) {
@@ -626,6 +632,20 @@ static int device_sms()
             nsm = 1;
     }
     return nsm;
+}
+
+cudaError_t check_read_transport(unsigned long long out[2], bool reset)
+{
+#if BZ_CHECK
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_bz_check, 2 * sizeof(unsigned long long));
+    const unsigned long long zero[2] = {0ull, 0ull};
+    if (e == cudaSuccess && reset) e = cudaMemcpyToSymbol(g_bz_check, zero, sizeof(zero));
+    return e;
+#else
+    out[0] = out[1] = 0ull;
+    (void)reset;
+    return cudaErrorNotSupported;
+#endif
 }
 
 cudaError_t launch_drift(const DriftArgs& a, cudaStream_t s)

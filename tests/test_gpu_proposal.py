@@ -117,7 +117,8 @@ def test_record_mode():
 def test_trained_proposal_lowers_the_error():
     """Record at t = 0 with the uniform sampler, train on the GPU, and compare the
     relative L2 error of the collision term against a high-N oracle reference
-    at equal samples per cell, learned vs uniform, over several seeds."""
+    at equal samples per cell, learned vs uniform, over several seeds (median
+    over the seeds)."""
     import torch
     from paper_1912_04457_gb300 import bz
     n, L = 12, 2.0
@@ -148,5 +149,8 @@ def test_trained_proposal_lowers_the_error():
         assert int(A.sum().item()) == 0
         el.append(_rel(A.cpu().numpy(), ref))
         hs.close()
-    print("uniform error %.4f, learned error %.4f" % (np.mean(eu), np.mean(el)))
-    assert np.mean(el) < 0.9 * np.mean(eu)
+    # the error of an importance-sampled 1/sqrt(H) integrand is heavy-tailed
+    # (a rare sample near the tangency dominates a stream), so the streams are
+    # compared by their median error
+    print("uniform errors", np.round(eu, 3), "learned errors", np.round(el, 3))
+    assert np.median(el) < 0.9 * np.median(eu)
