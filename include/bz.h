@@ -421,7 +421,7 @@ int bz_load(bz_handle h, int64_t* state, int64_t* step, const char* path);
 
 /* Bounds-checked builds (compiled with -DBZ_CHECK=1, a stand-in for a
  * memory sanitizer): the collision (FP64, FP32 and its re-evaluation) and the
- * streaming drift kernels test every index they compute into f, A, the
+ * drift kernels (streaming and row forms) test every index they compute into f, A, the
  * state and the mass table before the access, skip an access outside its
  * buffer and count it.  count: indices outside their buffers since the
  * last reset (host, may be NULL); first_bad: one of them, -1 if none (host,

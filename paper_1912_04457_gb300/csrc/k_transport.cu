@@ -325,7 +325,7 @@ __device__ __forceinline__ long long force_acc(const DriftArgs& P, const float* 
         const int jo = jv[i] + (up ? 1 : -1), jb = jv[i] + (up ? -1 : 1);
         long long own = 0, behind = 0;
         if (jo >= 0 && jo < P.np[i]) own = force_flux(n, g, inv, P.Kp[i]);
-        if (jb >= 0 && jb < P.np[i]) {
+        if (jb >= 0 && jb < P.np[i] && bz_in(j + (up ? -stride[i] : stride[i]), P.npc)) {
             const int jj = j + (up ? -stride[i] : stride[i]);
             behind = force_flux(__ldg(in_row + jj), g, __ldg(ie_row + jj), P.Kp[i]);
         }
@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
                 if (P.nx[d] == 1) continue;
                 const int own_C = rint_split(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
                 const long long off = s_off[2 * d + (pf[d] > 0.0f ? 0 : 1)];  // the upwind neighbour
+                if (!bz_in(row * P.npc + off + j, P.ncell)) continue;
                 const long long nn = __ldg(in_row + off + j);
                 const int nb_C = rint_split(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
                 const long long f_own = flux32(nh, nl, own_C), f_nb = flux32((int)(nn >> 32), (unsigned)nn, nb_C);
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(DRIFT_THREADS) k_drift(const __grid_constant__
                 if (P.nx[d] == 1) continue;
                 const long long own_C = rint_ll(((pf[d] * inv) * P.dtdxf) * 1073741824.0f);
                 const long long off = s_off[2 * d + (pf[d] > 0.0f ? 0 : 1)];  // the upwind neighbour
+                if (!bz_in(row * P.npc + off + j, P.ncell)) continue;
                 const long long nn = __ldg(in_row + off + j);
                 const long long nb_C = rint_ll(((pf[d] * __ldg(ie_row + off + j)) * P.dtdxf) * 1073741824.0f);
                 // p_d > 0: outflow up, inflow from below; p_d < 0: inflow from above, outflow down

@@ -1,5 +1,5 @@
 """Bounds-checked build (BZ_CHECK=1): the library is rebuilt with every
-computed index of the collision and streaming-drift kernels tested before
+computed index of the collision and drift kernels tested before
 its access, and small cases of each path run through it in a child process.
 No index may fall outside its buffer, and the results stay those of the
 default build: bit-identical to the oracle on the FP64 path and the drift,
@@ -65,6 +65,20 @@ h.drift(torch.from_numpy(st.reshape(-1)).cuda(), dst, 0.05)
 ref = O.drift(cfg, st, m2, 0.05).reshape(-1)
 out["drift_equal"] = bool(np.array_equal(dst.cpu().numpy(), ref))
 
+# the row kernel (n_z above the streaming kernel's buffer), with the force term
+nx, np_, mask = (2, 2, 41), (4, 4, 4), 0x01
+nxc = 164
+h = bz.Handle(nx=nx, dx=0.2, np_=np_, L=2.0, seed=1, species_mask=mask, alpha_s=0.3, mass_mode=2)
+cfg = O.make_config(nx=nx, dx=0.2, np_=np_, L=2.0, seed=1, species_mask=mask, alpha_s=0.3, mass_mode=2)
+cfg.force = 1
+h.set_force_term(True)
+m2 = np.random.default_rng(4).uniform(0.0, 0.5, size=(nxc, 4))
+h.set_masses(m2)
+st = state(mask, nxc, np_, 9, 0.0, 0.6)
+dst = torch.empty(st.size, dtype=torch.int64, device="cuda")
+h.drift(torch.from_numpy(st.reshape(-1)).cuda(), dst, 0.05)
+out["row_drift_equal"] = bool(np.array_equal(dst.cpu().numpy(), O.drift(cfg, st, m2, 0.05).reshape(-1)))
+
 torch.cuda.synchronize()
 out["count"], out["first_bad"] = bz.check_counts()
 print(json.dumps(out))
@@ -78,7 +92,7 @@ def test_checked_build_finds_no_index_outside_its_buffer(tmp_path):
     assert r.returncode == 0, r.stderr[-3000:]
     res = json.loads(r.stdout.strip().splitlines()[-1])
     assert res["count"] == 0 and res["first_bad"] == -1, res
-    assert res["f64_equal"] and res["drift_equal"], res
+    assert res["f64_equal"] and res["drift_equal"] and res["row_drift_equal"], res
     assert res["f32_rel_l2"] <= 2e-5, res
 
 
