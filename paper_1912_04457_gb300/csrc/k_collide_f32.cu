@@ -30,6 +30,9 @@ namespace {
 constexpr int RING = 128;         // pending roots per warp (power of 2)
 constexpr int SBUF = 64;          // buffered live samples per warp (power of 2)
 constexpr int WARPS = F32_WARPS;  // warps per block
+#ifndef BZ_FIX_MINB
+#define BZ_FIX_MINB 4  // resident blocks of 256 threads per SM the fixup's register budget is cut for (64 registers)
+#endif
 #ifndef BZ_F32_MIN_BLOCKS
 #define BZ_F32_MIN_BLOCKS (24 / WARPS)  // resident blocks per SM the register budget is cut for (80 registers)
 #endif
@@ -886,7 +889,7 @@ __device__ __noinline__ long long fixup_term_ff(const CollideArgs<float>& P, int
 // learned form gives each lane a contiguous run of items, so that its cached
 // per-anchor constants are reused.
 template <bool LEARNED>
-__global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ CollideArgs<float> P, const int* qcount,
+__global__ void __launch_bounds__(256, BZ_FIX_MINB) k_fixup_f32(const __grid_constant__ CollideArgs<float> P, const int* qcount,
                                                    const unsigned long long* qitems, int64_t qcap, int nseg)
 {
     const int64_t seg = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -907,7 +910,7 @@ __global__ void __launch_bounds__(256) k_fixup_f32(const __grid_constant__ Colli
 
 // Batch form: the item carries its box (bits 48..63); the step is read from
 // device memory.
-__global__ void __launch_bounds__(256) k_fixup_f32_batch(const CollideArgs<float>* __restrict__ boxes,
+__global__ void __launch_bounds__(256, BZ_FIX_MINB) k_fixup_f32_batch(const CollideArgs<float>* __restrict__ boxes,
                                                          const int* qcount, const unsigned long long* qitems,
                                                          int64_t qcap, const int* step_dev, int nseg)
 {
