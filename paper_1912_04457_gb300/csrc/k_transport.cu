@@ -42,6 +42,10 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v)
 // f and summed exactly.  Grid: one block per (x cell, chunk of 2048 bins).
 // ---------------------------------------------------------------------------
 constexpr int MASS_CHUNK = 2048;
+#ifndef BZ_MASS_MINB
+#define BZ_MASS_MINB 3  // resident blocks of 256 threads per SM the masses' register budget is cut for (85 registers)
+#endif
+
 static int device_sms();
 
 // Fixed-point partial sums of one (x cell, chunk of `chunk` bins) block; the
@@ -115,7 +119,7 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
     }
 }
 
-__global__ void __launch_bounds__(256) k_masses(const __grid_constant__ MassArgs P)
+__global__ void __launch_bounds__(256, BZ_MASS_MINB) k_masses(const __grid_constant__ MassArgs P)
 {
     const int64_t nchunk = (P.npc + P.chunk - 1) / P.chunk;
     masses_block(P, blockIdx.x / nchunk, (blockIdx.x % nchunk) * P.chunk, P.chunk, true);
@@ -132,7 +136,7 @@ __device__ __forceinline__ int find_box(const int64_t* prefix, int nboxes, int64
 }
 
 // Batch of homogeneous boxes: block -> (box, chunk) through chunk_prefix.
-__global__ void __launch_bounds__(256) k_masses_batch(const MassArgs* __restrict__ boxes,
+__global__ void __launch_bounds__(256, BZ_MASS_MINB) k_masses_batch(const MassArgs* __restrict__ boxes,
                                                       const int64_t* __restrict__ chunk_prefix, int nboxes,
                                                       const int* have_prev)
 {
