@@ -39,6 +39,7 @@ struct bz_handle_s {
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
     float* d_m2f = nullptr;        // drift scratch: FP32 m^2 per (x cell, mass slot)
+    unsigned long long* d_counter = nullptr;  // FP32 collision: units handed out
     double* d_m2prev = nullptr;    // energy source: the caller's previous masses [x][4]
     long long* d_mom_part = nullptr;  // moments: exact partial sums of the p-cell chunks
     int64_t mom_part_cap = 0;
@@ -167,6 +168,8 @@ static void free_scratch(bz_handle h)
     h->d_gforce = nullptr;
     cudaFree(h->d_m2f);
     h->d_m2f = nullptr;
+    cudaFree(h->d_counter);
+    h->d_counter = nullptr;
     cudaFree(h->d_m2prev);
     h->d_m2prev = nullptr;
     cudaFree(h->d_mom_part);
@@ -760,9 +763,15 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
     if (units >= ((int64_t)1 << 31))
         return fail(h, BZ_EINVAL, "anchors x samples too large for one FP32 call (%lld work units); use an anchor subset",
                     (long long)units);
+    CollideArgs<float> a{};
+    fill_collide(h, a, A, nsamples, step, dt, sampler);
+    // a resident grid whose warps take one unit at a time from a counter
     blocks = (units + F32_WARPS - 1) / F32_WARPS;
-    if (blocks > (int64_t)h->nsm * 48) blocks = (int64_t)h->nsm * 48;
+    const int64_t resident = (int64_t)h->nsm * collide_f32_resident_blocks(a);
+    if (blocks > resident) blocks = resident;
     if (blocks < 1) blocks = 1;
+    if (!h->d_counter && cudaMalloc(&h->d_counter, sizeof(unsigned long long)) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the unit counter");
     const int64_t warps = blocks * F32_WARPS;
     const int64_t samples_per_warp = ((units + warps - 1) / warps) * 32 * F32_GROUP;
     const int64_t qcap = samples_per_warp * MAX_TERMS / DEFER_CAP_DIV + 64;
@@ -779,15 +788,14 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
         h->q_warps = warps;
         h->q_items = warps * qcap;
     }
-    CollideArgs<float> a{};
-    fill_collide(h, a, A, nsamples, step, dt, sampler);
     a.tau = (float)DEFER_TAU;
     a.qcount = h->d_qcount;
     a.qitems = h->d_qitems;
     a.qcap = qcap;
+    CK(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     {
         ProfScope ps(h, BZ_K_COLLIDE, s);
-        CK(h, launch_collide_f32(a, (int)blocks, s));
+        CK(h, launch_collide_f32(a, (int)blocks, h->d_counter, s));
     }
     {  // float-float sample point and root solve, FP32 integrand
         ProfScope ps(h, BZ_K_FIXUP, s);
@@ -1752,7 +1760,7 @@ extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, in
     a.qcount = h->d_qcount;
     a.qitems = h->d_qitems;
     a.qcap = 0;
-    CK(h, launch_collide_f32(a, (int)blocks, s));
+    CK(h, launch_collide_f32(a, (int)blocks, nullptr, s));
     unsigned long long n = 0;
     CK(h, cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));

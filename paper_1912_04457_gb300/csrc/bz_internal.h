@@ -236,7 +236,10 @@ cudaError_t launch_collide_f64(const CollideArgs<double>& a, int grid, cudaStrea
 cudaError_t launch_fill_jtab(int* jtab, const int* np, cudaStream_t s);
 // exact int64 sum of a[0, n) added into *out
 cudaError_t launch_sum_ll(const long long* a, int64_t n, long long* out, cudaStream_t s);
-cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s);
+// counter: zeroed device word for the dynamic distribution of units over a
+// resident grid (see collide_f32_resident_blocks), or null for a static stride
+cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, unsigned long long* counter, cudaStream_t s);
+int collide_f32_resident_blocks(const CollideArgs<float>& a);  // per SM, for the instantiation `a` runs
 // FP32 path, uniform sampler: re-evaluation of the queued terms with an FP64
 // root solve (one warp per queue segment)
 cudaError_t launch_fixup_f32(const CollideArgs<float>& a, int nseg, cudaStream_t s);

@@ -537,7 +537,10 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
 }
 
 // FP32 collision, one warp per unit (an anchor and up to 32 F32_GROUP of its samples).
-// Single box (boxes == nullptr): warps stride over the units of `one`.
+// Single box (boxes == nullptr): a grid of resident blocks whose warps take
+// `chunk` units at a time from `counter` (zeroed by the caller), so every
+// warp works until the units run out; without a counter, warps stride over
+// the units of `one`.
 // Batch of independent boxes: warps take chunks of `chunk` units from a
 // global counter over the concatenated unit space (prefix[b] = first unit of
 // box b), so ragged boxes share the GPU evenly; the step index is read from
@@ -564,12 +567,13 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
     dq.seg = qitems + gw * qcap;
     dq.cap = (int)qcap;
     const bool batch = boxes != nullptr;
+    const bool dyn = counter != nullptr;  // chunks of units from the counter (a batch always)
     const int64_t total = batch ? prefix[nboxes] : f32_units(one.n_sel, one.nsamples);
     const int step = batch ? *step_dev : one.step;
     int b = 0;
-    int64_t u = batch ? 0 : gw, stop = 0;  // next unit; end of the current chunk (batch)
+    int64_t u = dyn ? 0 : gw, stop = 0;  // next unit; end of the current chunk
     for (;;) {
-        if (batch) {
+        if (dyn) {
             if (u >= stop) {
                 unsigned long long start = 0;
                 if (lane == 0) start = atomicAdd(counter, (unsigned long long)chunk);
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
                 u = (int64_t)start;
                 stop = min(u + chunk, total);
             }
-            if (u < prefix[b] || u >= prefix[b + 1]) {  // binary search for the box of u
+            if (batch && (u < prefix[b] || u >= prefix[b + 1])) {  // binary search for the box of u
                 int lo = 0, hi = nboxes - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
         }
         const CollideArgs<float>& P = batch ? boxes[b] : one;
         collide_unit<MODE, GROUPS>(P, batch ? u - prefix[b] : u, step, smem[warp], dq, (unsigned long long)b << 48);
-        u += batch ? 1 : nwarps;
+        u += dyn ? 1 : nwarps;
     }
     __syncwarp();
     if (lane == 0) {
@@ -624,19 +628,37 @@ cudaError_t check_read_collide_f32(unsigned long long out[2], bool reset)
 #endif
 }
 
-cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, cudaStream_t s)
+// The instantiation a single-box launch runs, and its resident blocks per SM.
+template <int MODE, bool GROUPS>
+static int resident_blocks()
+{
+    static int n = 0;
+    if (!n && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_f32<MODE, GROUPS>, 32 * WARPS, 0) !=
+                   cudaSuccess || n < 1))
+        n = 1;
+    return n;
+}
+
+int collide_f32_resident_blocks(const CollideArgs<float>& a)
+{
+    if (a.rec_stride) return resident_blocks<M_RECORD, true>();
+    if (a.sampler == SAMPLER_LEARNED) return resident_blocks<M_LEARNED, true>();
+    return has_groups(a) ? resident_blocks<M_UNIFORM, true>() : resident_blocks<M_UNIFORM, false>();
+}
+
+cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, unsigned long long* counter, cudaStream_t s)
 {
     if (a.rec_stride)
-        k_collide_f32<M_RECORD, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+        k_collide_f32<M_RECORD, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                    a.qitems, a.qcap);
     else if (a.sampler == SAMPLER_LEARNED)
-        k_collide_f32<M_LEARNED, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+        k_collide_f32<M_LEARNED, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                     a.qitems, a.qcap);
     else if (has_groups(a))
-        k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0, a.qcount,
+        k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                     a.qitems, a.qcap);
     else
-        k_collide_f32<M_UNIFORM, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr, 0,
+        k_collide_f32<M_UNIFORM, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1,
                                                                      a.qcount, a.qitems, a.qcap);
     return cudaGetLastError();
 }
