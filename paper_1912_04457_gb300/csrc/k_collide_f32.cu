@@ -41,11 +41,15 @@ constexpr int WARPS = F32_WARPS;  // warps per block
 #endif
 
 struct WarpSmem {
-    // live samples (k2 inside the box in x and y, or on its edge), [field][slot]
-    float Ep[SBUF], Pz[SBUF], PP[SBUF], a2m[SBUF], b2m[SBUF], kk3[SBUF];
-    float k13[SBUF], k3z[SBUF], k1p[SBUF], pz[SBUF];  // k1perp.k3perp, k3z, k1perp.pperp, pz
-    int b1xy[SBUF], b2xy[SBUF], lin3[SBUF];           // bins of k1perp, k2perp and k3
-    int meta[SBUF];               // sample index | k2perp inside << 24 | on an edge << 25
+    // live samples (k2 inside the box in x and y, or on its edge), [field][slot];
+    // fields read together are paired into 8-byte words
+    float2 EpPz[SBUF];            // Ep, Pz
+    float2 ab2m[SBUF];            // a^2 - m_a^2 = |k1perp|^2, b^2 - m_b^2 = |k2perp|^2
+    float2 PPkk3[SBUF];           // P^2, |k3|^2
+    float2 k13k3z[SBUF];          // k1perp.k3perp, k3z
+    float2 k1ppz[SBUF];           // k1perp.pperp, pz
+    int2 bxy[SBUF];               // bins of k1perp and k2perp (x, y)
+    int2 lin3meta[SBUF];          // bin of k3; sample index | k2perp inside << 24 | on an edge << 25
     float wfac[SBUF];             // learned: 1/(32 q(y)); record mode: sum of |c~| of the sample
     float3 tlc[4];                // learned: t2_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
     // pending roots
@@ -214,21 +218,24 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
             const float4 tmv0 = S.tm[t0];  // leg masses shared by the group's terms
             const float ma2 = tmv0.x, mc2 = tmv0.z;
-            const float Ep = S.Ep[src];
+            const float2 epz = S.EpPz[src];
+            const float Ep = epz.x;
             const float E = Ep + E3;
-            const float a2 = S.a2m[src] + ma2;
+            const float a2 = S.ab2m[src].x + ma2;
             const float E1 = sqrtf(a2 + z * z);
-            const float dz = S.Pz[src] - z;
-            const float s = E * E - S.PP[src];
-            const float k1k3 = S.k13[src] + z * S.k3z[src];
-            const float k1p = S.k1p[src] + z * S.pz[src];
+            const float dz = epz.y - z;
+            const float s = E * E - S.PPkk3[src].x;
+            const float2 k13 = S.k13k3z[src], k1p_ = S.k1ppz[src];
+            const float k1k3 = k13.x + z * k13.y;
+            const float k1p = k1p_.x + z * k1p_.y;
             const float t = (ma2 + mc2) - 2.0f * (E1 * E3 - k1k3);
             const float uu = (ma2 + md2) - 2.0f * (E1 * Ep - k1p);
             if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
                 red_add(&P.flags[0], tn);
             } else {
-                const int lin1 = S.b1xy[src] * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
-                const int lin2 = S.b2xy[src] * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
+                const int2 bxy = S.bxy[src];
+                const int lin1 = bxy.x * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
+                const int lin2 = bxy.y * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
                 // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                 const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
                 for (int k = 0; k < tn; ++k) {  // the group's terms: |M|^2, leg species, statistics
@@ -238,7 +245,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
                     const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
                     const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
-                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3[src];
+                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3meta[src].x;
                     if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell))) continue;
                     float f1, f2, f3, fpp;
                     if (P.analytic) {
@@ -415,8 +422,9 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             bcnt = min(nlive - cons, 32);
             const int sb = (bstart + lane) & (SBUF - 1);
             if (lane < bcnt) {
-                bEp = S.Ep[sb]; bPz = S.Pz[sb]; ba2m = S.a2m[sb]; bb2m = S.b2m[sb]; bkk3 = S.kk3[sb];
-                bmeta = S.meta[sb];
+                const float2 epz = S.EpPz[sb], ab = S.ab2m[sb];
+                bEp = epz.x; bPz = epz.y; ba2m = ab.x; bb2m = ab.y; bkk3 = S.PPkk3[sb].y;
+                bmeta = S.lin3meta[sb].y;
             } else {
                 bmeta = 0;
             }
@@ -498,27 +506,23 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             }
             if (keep) {
                 const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
-                S.Ep[sb] = sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2);
-                S.Pz[sb] = Pz;
-                S.PP[sb] = (Px * Px + Py * Py) + Pz * Pz;
-                S.a2m[sb] = k1x * k1x + k1y * k1y;
-                S.b2m[sb] = bx * bx + by * by;
-                S.kk3[sb] = (k30 * k30 + k31 * k31) + k32 * k32;
-                S.k13[sb] = k1x * k30 + k1y * k31;
-                S.k3z[sb] = k32;
-                S.k1p[sb] = k1x * p0 + k1y * p1;
-                S.pz[sb] = p2;
+                S.EpPz[sb] = make_float2(sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2), Pz);
+                S.PPkk3[sb] = make_float2((Px * Px + Py * Py) + Pz * Pz, (k30 * k30 + k31 * k31) + k32 * k32);
+                S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
+                S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
+                S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
+                int lin3, b1xy;
                 if (MODE == M_LEARNED) {
-                    S.lin3[sb] = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                    lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
                                  + binf(k32, L, inv_dp2, P.np[2]);
-                    S.b1xy[sb] = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                    b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
                 } else {
-                    S.lin3[sb] = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                    lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
                                  + bin_word(r1.w, P.np[2]);
-                    S.b1xy[sb] = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                    b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
                 }
-                S.b2xy[sb] = binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]);
-                S.meta[sb] = smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25);
+                S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
+                S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
                 S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
             }
             nlive += cnt;
