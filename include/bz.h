@@ -21,7 +21,10 @@
  *   memory.  The handle owns only its descriptors and device scratch.
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
  *   work is enqueued on it; calls return without synchronising unless
- *   stated.
+ *   stated.  A handle's device scratch (masses, f, the FP32 deferral queue
+ *   and work counter) serves one call at a time: calls on one handle must
+ *   be ordered (one stream, or events between streams); separate handles
+ *   run concurrently.
  * Errors: 0 on success; negative BZ_E* on error (nothing was enqueued
  *   after the failing check; bz_last_error gives the message).  No C++
  *   exception crosses this boundary.
