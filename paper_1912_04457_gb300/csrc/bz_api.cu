@@ -765,12 +765,15 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
                     (long long)units);
     CollideArgs<float> a{};
     fill_collide(h, a, A, nsamples, step, dt, sampler);
-    // a resident grid whose warps take one unit at a time from a counter
+    // a resident grid whose warps take one unit at a time from a counter; a
+    // problem of at most two units per resident warp keeps one warp per unit
+    // (no counter to reset, no atomics)
     blocks = (units + F32_WARPS - 1) / F32_WARPS;
     const int64_t resident = (int64_t)h->nsm * collide_f32_resident_blocks(a);
-    if (blocks > resident) blocks = resident;
+    const bool dyn = blocks > 2 * resident;
+    if (dyn) blocks = resident;
     if (blocks < 1) blocks = 1;
-    if (!h->d_counter && cudaMalloc(&h->d_counter, sizeof(unsigned long long)) != cudaSuccess)
+    if (dyn && !h->d_counter && cudaMalloc(&h->d_counter, sizeof(unsigned long long)) != cudaSuccess)
         return fail(h, BZ_ENOMEM, "cannot allocate the unit counter");
     const int64_t warps = blocks * F32_WARPS;
     const int64_t samples_per_warp = ((units + warps - 1) / warps) * 32 * F32_GROUP;
@@ -792,10 +795,10 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
     a.qcount = h->d_qcount;
     a.qitems = h->d_qitems;
     a.qcap = qcap;
-    CK(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
+    if (dyn) CK(h, cudaMemsetAsync(h->d_counter, 0, sizeof(unsigned long long), s));
     {
         ProfScope ps(h, BZ_K_COLLIDE, s);
-        CK(h, launch_collide_f32(a, (int)blocks, h->d_counter, s));
+        CK(h, launch_collide_f32(a, (int)blocks, dyn ? h->d_counter : nullptr, s));
     }
     {  // float-float sample point and root solve, FP32 integrand
         ProfScope ps(h, BZ_K_FIXUP, s);
