@@ -273,6 +273,8 @@ def run_bz(args):
 
     mk = workloads()[args.workload]
     kw = {"nsamples": args.nsamples} if args.nsamples else {}
+    if args.nxs:
+        kw["nxs"] = args.nxs
     w = mk(seed=rank_seed(mk().seed, rank), **kw) if world > 1 else mk(**kw)
     prec = bz.PREC_F32 if args.prec == "f32" else bz.PREC_F64
     h = bz.Handle(nx=w.nx, dx=w.dx, np_=w.np_, L=w.L, seed=w.seed, species_mask=w.species_mask,
@@ -811,6 +813,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--nsamples", type=int, default=0, help="override samples per cell (small profiling cases)")
+    ap.add_argument("--nxs", type=int, default=0,
+                    help="gluon_bump: spatial cells per axis (small profiling cases of the same box)")
     ap.add_argument("--rec-samples", type=int, default=16, help="tts: uniform samples per anchor recorded")
     ap.add_argument("--train-steps", type=int, default=3000, help="tts: Adam steps")
     args = ap.parse_args()

@@ -44,9 +44,7 @@
  *   - the mass integrals are summed exactly in 2^-30 fixed point, so their
  *     value does not depend on summation order.
  * Parity of the physical evolution curves (the paper's figures) is
- * unpinned: the figures are not available.  The -(1/4) m^2 I term of
- * T_total (bzo_energy_source) is the product of the pinned I and the
- * masses; beyond that its parity is unpinned.
+ * unpinned: the figures are not available.
  */
 #include <math.h>
 #include <stdint.h>
@@ -529,6 +527,7 @@ typedef struct {
     const double* prop;      /* sampler 2: per-anchor proposal (mu3 x3, sigma3, sigma1, alpha, -, -) */
     int32_t param;           /* 0: k2 = k3 + p - k1 eliminated (the paper's choice); 1: k3 = k1 + k2 - p
                                 eliminated, (k1_perp, k2) sampled (Sec. III.A, "less stable") */
+    int32_t u_shared;        /* 1: u_explicit is one [sample][8] set used by every anchor */
 } bzo_run;
 
 /* Learned-proposal sample: defensive mixture q(y) = alpha/32 + (1 - alpha)
@@ -715,7 +714,8 @@ static void collide_anchor(const bzo_config* c, const bzo_run* r, const int64_t*
     for (int32_t smp = 0; smp < r->nsamples; ++smp) {
         double u[8];
         if (r->u_explicit) {
-            for (int i = 0; i < 8; ++i) u[i] = r->u_explicit[(aidx * r->nsamples + smp) * 8 + i];
+            int64_t ua = r->u_shared ? 0 : aidx;
+            for (int i = 0; i < 8; ++i) u[i] = r->u_explicit[(ua * r->nsamples + smp) * 8 + i];
         } else {
             for (int blk = 0; blk < 2; ++blk) {
                 uint32_t ctr[4] = {(uint32_t)(2 * smp + blk), (uint32_t)j, (uint32_t)x,

@@ -37,6 +37,7 @@ class Run(C.Structure):
         ("u_explicit", C.POINTER(C.c_double)),
         ("prop", C.POINTER(C.c_double)),
         ("param", C.c_int32),
+        ("u_shared", C.c_int32),
     ]
 
 
@@ -175,9 +176,10 @@ def masses(cfg, state, m2_prev=None):
 
 
 def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=False,
-             anchor_stride=1, anchor_offset=0, u_explicit=None, prop=None, param=0):
+             anchor_stride=1, anchor_offset=0, u_explicit=None, prop=None, param=0, u_shared=False):
     r = Run()
     r.param = param
+    r.u_shared = 1 if u_shared else 0
     r.nsamples = nsamples
     r.step = step
     r.dt = dt
@@ -201,9 +203,11 @@ def make_run(nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32, p_center=Fa
 
 def collision(cfg, state, m2, nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubits=32,
               p_center=False, anchor_stride=1, anchor_offset=0, u_explicit=None,
-              want_c64=False, want_audit=False, prop=None, param=0):
+              want_c64=False, want_audit=False, prop=None, param=0, u_shared=False):
     """Returns dict with A (int64 [slot][x][p]), flags, and optionally C64/G64/audit.
-    param 0: k2 eliminated (the paper's choice), 1: k3 eliminated."""
+    param 0: k2 eliminated (the paper's choice), 1: k3 eliminated.  u_explicit:
+    [anchor][sample][8] uniforms replacing Philox, or with u_shared one
+    [sample][8] set used by every anchor."""
     ns, nxc, npc = ncells(cfg)
     state = np.ascontiguousarray(state, dtype=np.int64).reshape(-1)
     m2 = np.ascontiguousarray(m2, dtype=np.float64).reshape(nxc, 4)
@@ -211,7 +215,7 @@ def collision(cfg, state, m2, nsamples, step=0, dt=0.01, sampler=SYMMETRIC, ubit
         assert prop is not None and np.asarray(prop).size == ns * nxc * npc * 8
         assert param == 0, "the learned sampler draws (k1_perp, k3)"
     run = make_run(nsamples, step, dt, sampler, ubits, p_center, anchor_stride, anchor_offset,
-                   u_explicit, prop, param)
+                   u_explicit, prop, param, u_shared)
     A = np.zeros(ns * nxc * npc, dtype=np.int64)
     C64 = np.zeros(ns * nxc * npc) if want_c64 else None
     G64 = np.zeros(ns * nxc * npc) if want_c64 else None
