@@ -6,12 +6,17 @@ drift (+ f for the lookups), collision sampling and deposition (FP32
 integrand with float-float re-evaluation of ill-conditioned terms), moments.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bz|reference]
-                  [--workload qgp|gluon_step|gluon_bump]
+                  [--workload gluon_bump|qgp|gluon_step|batch|tts|stability]
+
+Default workload: the largest single-GPU configuration, pure gluons on a
+16^3 periodic spatial grid (dx = 0.2 fm) times a 20^3 momentum grid on
+[-2, 2) GeV, 256 samples per cell, 32.8 M phase-space cells.
 
 Prints one JSON line (rank 0).  Metric: collision samples/s, a sample being
 one (species, x cell, p cell, sample) anchor evaluated over all terms of its
-species' equation.  The reference arm (--impl reference) is the FP64 CPU
-oracle on a bounded sample of anchors of the same workload.
+species' equation, with cell-updates/s beside it.  The reference arm (--impl
+reference) is the FP64 CPU oracle on a bounded sample of anchors of the same
+workload.
 """
 import argparse
 import hashlib
@@ -114,9 +119,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per collision launch from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+def ncu_summary(workload):
+    """The committed ncu counters of the collision kernel on this workload
+    (DRAM bytes and executed FP32 flops per full launch), if they were taken
+    on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "collide_%s_traffic.json" % workload)
     try:
         d = json.load(open(path))
@@ -124,7 +130,7 @@ def ncu_traffic(workload):
         return None
     if d.get("source_hash") != source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d
 
 
 def term_counts(w):
@@ -385,7 +391,14 @@ def run_bz(args):
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clk.get("sm_mhz") or 1447.0
         peak = nsm * 128 * 2 * mhz * 1e6 / 1e12
-        traffic = ncu_traffic(args.workload)
+        summ = ncu_summary(args.workload) if not (args.nsamples or args.nxs) else None
+        traffic = summ.get("dram_bytes_per_launch") if summ else None
+        executed = None
+        if summ and summ.get("fp32_flop_executed_per_launch"):
+            ex = summ["fp32_flop_executed_per_launch"] / coll_s / 1e12
+            executed = {"achieved": ex, "frac": ex / peak, "unit": "TFLOP/s",
+                        "basis": "FP32 add + mul + 2 x FMA executed per launch (ncu instruction counters, "
+                                 "committed summary) over the same event-timed launch duration"}
 
         # the plain FP64 GPU path on the same workload (one step, same samples)
         fp64 = None
@@ -439,7 +452,8 @@ def run_bz(args):
             "kernel_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in prof.items()},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_collide<float> (FP32 pipe)",
+                         "kernel": "k_collide_f32 (FP32 pipe)",
+                         "executed": executed,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop (FMA) x %.0f MHz sampled "
                                        "median SM clock" % (nsm, mhz),
                          "work_basis": "%d flop/sample + %d flop/term + %d flop/accepted root, "
@@ -486,14 +500,14 @@ def measured_hbm_gbs():
 
 def transport_rooflines(h, w, state, mom, prof, steps, stream, barrier):
     """Drift (k_mass_table + drift kernel; algorithmic bytes 8 B read + 8 B
-    write + 4 B f per cell) and moments (8 B read per cell) of the timed steps
-    against the HBM peak, and the drift with the force term switched on,
-    timed over separate calls."""
+    write + 4 B f per cell), moments and thermal masses (8 B read per cell
+    each) of the timed steps against the HBM peak, and the drift with the
+    force term switched on, timed over separate calls."""
     import torch
     ncell = w.nslots * w.nxc * w.npc
     peak, basis = measured_hbm_gbs()
     out = {"hbm_peak_GBs": peak, "peak_basis": basis}
-    for name, nbytes in (("drift", 20 * ncell), ("moments", 8 * ncell)):
+    for name, nbytes in (("drift", 20 * ncell), ("moments", 8 * ncell), ("masses", 8 * ncell)):
         ms = prof[name][0] / max(prof[name][1], 1)
         gbs = nbytes / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "algorithmic_bytes": nbytes, "achieved_GBs": gbs, "frac": gbs / peak}
@@ -807,7 +821,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="bz", choices=["bz", "reference"])
-    ap.add_argument("--workload", default="qgp",
+    ap.add_argument("--workload", default="gluon_bump",
                     choices=["qgp", "gluon_step", "gluon_bump", "batch", "tts", "stability"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

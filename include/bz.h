@@ -28,6 +28,11 @@
  * Errors: 0 on success; negative BZ_E* on error (nothing was enqueued
  *   after the failing check; bz_last_error gives the message).  No C++
  *   exception crosses this boundary.
+ * Environment: BZ_F32_SCHEDULE (read at every FP32 collision call of a
+ *   handle) = "counter" or "static" forces how the warps of the FP32 kernel
+ *   share the work units -- taking them from a global counter, or one unit
+ *   per warp -- which is otherwise chosen by size; both give the same bits
+ *   (a test checks it).  Unset or any other value: chosen by size.
  */
 #ifndef BZ_H
 #define BZ_H
@@ -328,17 +333,20 @@ int bz_batch_get_flags(bz_batch b, int64_t* flags_host);
  *   (BZ_EINVAL with a message otherwise).
  *   Arguments: g (host), the species mask, alpha_s and mass mode as for
  *   bz_set_species; state (device int64 [nslots][nx][np], read only);
- *   m2_in (device double [nx][4]): BZ_MASS_THERMAL -- the previous masses
- *   giving E in Eqs. (mg), (mq), or NULL for E = |p|; BZ_MASS_MASSLESS --
- *   ignored; BZ_MASS_FIXED -- the masses to use (required); m2_out (device
- *   double [nx][4]) receives the masses used; A (device int64, same shape as
- *   state) is zeroed and filled exactly as bz_collision_term fills it with
- *   BZ_PREC_F64 and BZ_SAMPLER_SYMMETRIC; nsamples, step, dt as there.
- *   errbuf (host, may be NULL) receives a message of at most errbuf_len
- *   bytes when the return value is not BZ_OK.
+ *   m2_in (device double [nx][4]): BZ_MASS_THERMAL -- the masses of the
+ *   previous call, which give the energies E = sqrt(p^2 + m^2) inside the
+ *   thermal-mass sums, or NULL for E = |p|; BZ_MASS_MASSLESS -- ignored;
+ *   BZ_MASS_FIXED -- the masses to use (required); m2_out (device double
+ *   [nx][4], may be the same buffer as m2_in) receives the masses used; A
+ *   (device int64, same shape as state) is zeroed and filled exactly as
+ *   bz_collision_term fills it with BZ_PREC_F64 and BZ_SAMPLER_SYMMETRIC;
+ *   nsamples, step, dt as there.  errbuf (host, may be NULL) receives a
+ *   message of at most errbuf_len bytes when the return value is not BZ_OK.
  *   Set-up: the first call on a device looks up the device addresses of the
- *   scratch arrays (with that device current) and caches them; make that
- *   first call before any stream capture.
+ *   scratch arrays (with that device current) and caches them for the life
+ *   of the process; make that first call before any stream capture.  The
+ *   cached addresses belong to the device's context: do not call this entry
+ *   point again after cudaDeviceReset in the same process.
  *   Sharing: every call on a device uses the same scratch, which keeps the
  *   last call's contents; what must start at zero is cleared on the stream
  *   at the start of each call.  Calls that overlap on the GPU (different

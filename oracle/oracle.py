@@ -272,12 +272,15 @@ def energy_source(cfg, state, m2, m2_prev, dt):
     return out
 
 
-def step(cfg, state, m2, first, nsamples, step_index, dt, sampler=SYMMETRIC, ubits=32):
-    """One Euler step; returns (new state, masses used, flags)."""
+def step(cfg, state, m2, first, nsamples, step_index, dt, sampler=SYMMETRIC, ubits=32, prop=None):
+    """One Euler step; returns (new state, masses used, flags).  prop: the
+    per-anchor proposal parameters [anchor][8] of the learned sampler."""
     ns, nxc, npc = ncells(cfg)
     state = np.ascontiguousarray(state, dtype=np.int64).reshape(-1)
     m2 = np.array(m2 if m2 is not None else np.zeros((nxc, 4)), dtype=np.float64).reshape(nxc, 4)
-    run = make_run(nsamples, step_index, dt, sampler, ubits)
+    if sampler == LEARNED:
+        assert prop is not None and np.asarray(prop).size == ns * nxc * npc * 8
+    run = make_run(nsamples, step_index, dt, sampler, ubits, prop=prop)
     out = np.zeros_like(state)
     flags = np.zeros(2, dtype=np.int64)
     rc = lib().bzo_step(C.byref(cfg), C.byref(run), _ptr(state), _ptr(m2), 1 if first else 0,

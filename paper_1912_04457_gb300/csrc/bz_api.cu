@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -767,10 +768,15 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
     fill_collide(h, a, A, nsamples, step, dt, sampler);
     // a resident grid whose warps take one unit at a time from a counter; a
     // problem of at most two units per resident warp keeps one warp per unit
-    // (no counter to reset, no atomics)
+    // (no counter to reset, no atomics).  BZ_F32_SCHEDULE=counter|static
+    // forces either form, so tests can check that they give the same bits.
     blocks = (units + F32_WARPS - 1) / F32_WARPS;
     const int64_t resident = (int64_t)h->nsm * collide_f32_resident_blocks(a);
-    const bool dyn = blocks > 2 * resident;
+    bool dyn = blocks > 2 * resident;
+    if (const char* sched = std::getenv("BZ_F32_SCHEDULE")) {
+        if (!std::strcmp(sched, "counter")) dyn = true;
+        else if (!std::strcmp(sched, "static")) dyn = false;
+    }
     if (dyn) blocks = resident;
     if (blocks < 1) blocks = 1;
     if (dyn && !h->d_counter && cudaMalloc(&h->d_counter, sizeof(unsigned long long)) != cudaSuccess)

@@ -186,7 +186,8 @@ extern "C" int bz_collision_term_static(const bz_grid* g, uint32_t species_mask,
 
     // 1. thermal masses, Eqs. (mg), (mq), into m2_out (mass mode FIXED: copy m2_in)
     if (mass_mode == BZ_MASS_FIXED) {
-        CKS(cudaMemcpyAsync(m2_out, m2_in, sizeof(double) * 4 * nxc, cudaMemcpyDeviceToDevice, s));
+        if (m2_out != m2_in)
+            CKS(cudaMemcpyAsync(m2_out, m2_in, sizeof(double) * 4 * nxc, cudaMemcpyDeviceToDevice, s));
     } else {
         MassArgs ma{};
         ma.state = reinterpret_cast<const long long*>(state);

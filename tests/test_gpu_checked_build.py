@@ -4,7 +4,8 @@ its access, and small cases of each path run through it in a child process.
 No index may fall outside its buffer, and the results stay those of the
 default build: bit-identical to the oracle on the FP64 path and the drift,
 within the FP32 tolerance on the FP32 path (its float-float re-evaluation
-included)."""
+included), whose two work schedules (counter, one unit per warp) give the
+same bits."""
 import json
 import os
 import subprocess
@@ -49,6 +50,14 @@ h.reset_masses()
 h.collision_term(torch.from_numpy(st.reshape(-1)).cuda(), A, 32, 3, 0.01, bz.PREC_F32)
 ref23 = O.collision(cfg, st, m2, 32, step=3, dt=0.01, ubits=23)["A"]
 out["f32_rel_l2"] = rel_l2(A.cpu().numpy().reshape(ref23.shape), ref23)
+# the same through the counter schedule (warps take units from a global counter)
+import os
+os.environ["BZ_F32_SCHEDULE"] = "counter"
+A2 = torch.empty_like(A)
+h.reset_masses()
+h.collision_term(torch.from_numpy(st.reshape(-1)).cuda(), A2, 32, 3, 0.01, bz.PREC_F32)
+del os.environ["BZ_F32_SCHEDULE"]
+out["f32_counter_equal"] = bool(torch.equal(A, A2))
 
 # streaming drift with the force term on an inhomogeneous grid, several species
 nx, np_, mask = (3, 2, 4), (4, 6, 4), 0x03
@@ -93,7 +102,7 @@ def test_checked_build_finds_no_index_outside_its_buffer(tmp_path):
     res = json.loads(r.stdout.strip().splitlines()[-1])
     assert res["count"] == 0 and res["first_bad"] == -1, res
     assert res["f64_equal"] and res["drift_equal"] and res["row_drift_equal"], res
-    assert res["f32_rel_l2"] <= 2e-5, res
+    assert res["f32_rel_l2"] <= 2e-5 and res["f32_counter_equal"], res
 
 
 def test_default_build_has_no_checks():
