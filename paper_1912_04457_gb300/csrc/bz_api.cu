@@ -707,6 +707,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
     }
     a.key0 = (uint32_t)(h->g.seed & 0xffffffffu) ^ h->g.box;
     a.key1 = (uint32_t)(h->g.seed >> 32);
+    philox_key_schedule(a.key0, a.key1, a.ks);
     a.nsamples = nsamples;
     a.step = step;
     a.a_stride = h->a_stride;

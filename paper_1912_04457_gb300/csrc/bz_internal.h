@@ -113,6 +113,18 @@ struct UserRow {
 };
 constexpr int MSQ_ROWS = 7;
 
+// Philox4x32-10 keys of rounds 0..9: the key is bumped by the Weyl
+// constants 0x9E3779B9 and 0xBB67AE85 after every round (Salmon et al., SC'11).
+inline void philox_key_schedule(uint32_t k0, uint32_t k1, uint32_t ks[20])
+{
+    for (int r = 0; r < 10; ++r) {
+        ks[2 * r] = k0;
+        ks[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 template <typename R>
 struct CollideArgs {
     const void* f;          // f per cell [slot][x][p] (unused in equilibrium mode)
@@ -130,6 +142,8 @@ struct CollideArgs {
     // units per anchor, cells per slot, p cells, np[1] np[2], np[2]
     DivMagic dv_group, dv_slot, dv_npc, dv_yz, dv_z;
     uint32_t key0, key1;
+    uint32_t ks[20];        // Philox key schedule: (k0, k1) of rounds 0..9, so a kernel whose
+                            // arguments sit in the constant bank reads them as operands
     int nsamples, step;
     int64_t n_sel, a_stride, a_offset;
     int sampler, mass_mode, analytic, p_center;

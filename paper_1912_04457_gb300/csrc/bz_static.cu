@@ -236,6 +236,7 @@ extern "C" int bz_collision_term_static(const bz_grid* g, uint32_t species_mask,
     a.twoL = twoL;
     a.key0 = (uint32_t)(g->seed & 0xffffffffu) ^ g->box;
     a.key1 = (uint32_t)(g->seed >> 32);
+    philox_key_schedule(a.key0, a.key1, a.ks);
     a.nsamples = nsamples;
     a.step = step;
     a.n_sel = ncell;

@@ -41,6 +41,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same rounds with the keys taken from a schedule (philox_key_schedule).
+__device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ ks[2 * r], lo1, hi0 ^ c.w ^ ks[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 template <typename R> struct Ops;
 template <> struct Ops<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }

@@ -39,6 +39,9 @@ constexpr int WARPS = F32_WARPS;  // warps per block
 #ifndef BZ_F32_MIN_BLOCKS
 #define BZ_F32_MIN_BLOCKS (24 / WARPS)  // resident blocks per SM the register budget is cut for (80 registers)
 #endif
+#ifndef BZ_F32_MIN_BLOCKS_GROUPED
+#define BZ_F32_MIN_BLOCKS_GROUPED 7  // the same for single boxes whose equations have groups of several terms
+#endif
 
 struct WarpSmem {
     // live samples (k2 inside the box in x and y, or on its edge), [field][slot];
@@ -132,7 +135,16 @@ enum { M_UNIFORM = 0, M_LEARNED = 1, M_RECORD = 2 };
 // compacted into the live-sample buffer, and the roots are solved on full
 // warps of live samples.  box_tag is or-ed into queued items (the box index
 // << 48 in a batch).
-template <int MODE, bool GROUPS>
+// SINGLE: P is the kernel's own argument block (constant bank), so the Philox
+// key schedule is read from it as instruction operands; a batch box's block
+// lives in global memory and the keys are bumped round by round instead.
+template <bool SINGLE>
+__device__ __forceinline__ uint4 draw(const CollideArgs<float>& P, uint4 ctr)
+{
+    return SINGLE ? philox4x32_10_ks(ctr, P.ks) : philox4x32_10(ctr, P.key0, P.key1);
+}
+
+template <int MODE, bool GROUPS, bool SINGLE>
 __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
                                              DeferCtx& dq, unsigned long long box_tag)
 {
@@ -400,9 +412,8 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 const unsigned pos = __popc(keep_mask & lt_mask);
                 if (keep && (long long)(base + pos) < P.rec_cap) {
                     const int smp = bmeta & 0xFFFFFF;
-                    const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-                    const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0,
-                                                   P.key1);
+                    const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
+                    const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
                     ProposalRecord R;
                     R.a = a;
                     R.w = S.wfac[sb];
@@ -435,8 +446,8 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             // ---- sample geometry (one sample per lane) ----
             const int smp = c * 32 + lane;
             const bool live = smp < P.nsamples;
-            const uint4 r0 = philox4x32_10(make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
-            const uint4 r1 = philox4x32_10(make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3), P.key0, P.key1);
+            const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
+            const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
             const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
             const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
             const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
@@ -444,8 +455,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             bool margk = false;
             if (MODE == M_LEARNED) {
                 // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
-                const uint4 r2 = philox4x32_10(make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3),
-                                               P.key0, P.key1);
+                const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
                 // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
                 // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
                 // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
@@ -544,22 +554,23 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
 }
 
 // FP32 collision, one warp per unit (an anchor and up to 32 F32_GROUP of its samples).
-// Single box (boxes == nullptr): a grid of resident blocks whose warps take
+// Single box (BATCH false): a grid of resident blocks whose warps take
 // `chunk` units at a time from `counter` (zeroed by the caller), so every
 // warp works until the units run out; without a counter, warps stride over
 // the units of `one`.
-// Batch of independent boxes: warps take chunks of `chunk` units from a
-// global counter over the concatenated unit space (prefix[b] = first unit of
-// box b), so ragged boxes share the GPU evenly; the step index is read from
-// device memory, so a captured graph replays with the same parameters.
-// Both walk through the one call site of collide_unit: a box gives the same
-// bits alone or inside a batch.
-template <int MODE, bool GROUPS>
-__global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(const __grid_constant__ CollideArgs<float> one,
-                                                        const CollideArgs<float>* __restrict__ boxes,
-                                                        const int64_t* __restrict__ prefix, int nboxes,
-                                                        unsigned long long* counter, const int* step_dev, int chunk,
-                                                        int* qcount, unsigned long long* qitems, long long qcap)
+// Batch of independent boxes (BATCH true): warps take chunks of `chunk`
+// units from a global counter over the concatenated unit space (prefix[b] =
+// first unit of box b), so ragged boxes share the GPU evenly; the step index
+// is read from device memory, so a captured graph replays with the same
+// parameters.
+// Both run the same collide_unit source (the single box with its argument
+// block in the constant bank, the batch with each box's block in global
+// memory): a box gives the same bits alone or inside a batch.
+template <int MODE, bool GROUPS, bool BATCH>
+__global__ void __launch_bounds__(32 * WARPS, (GROUPS && !BATCH) ? BZ_F32_MIN_BLOCKS_GROUPED : BZ_F32_MIN_BLOCKS)
+    k_collide_f32(const __grid_constant__ CollideArgs<float> one, const CollideArgs<float>* __restrict__ boxes,
+                  const int64_t* __restrict__ prefix, int nboxes, unsigned long long* counter, const int* step_dev,
+                  int chunk, int* qcount, unsigned long long* qitems, long long qcap)
 {
     __shared__ WarpSmem smem[WARPS];
     __shared__ int s_qcount[WARPS];
@@ -573,7 +584,7 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
     dq.s_count = &s_qcount[warp];
     dq.seg = qitems + gw * qcap;
     dq.cap = (int)qcap;
-    const bool batch = boxes != nullptr;
+    const bool batch = BATCH;
     const bool dyn = counter != nullptr;  // chunks of units from the counter (a batch always)
     const int64_t total = batch ? prefix[nboxes] : f32_units(one.n_sel, one.nsamples);
     const int step = batch ? *step_dev : one.step;
@@ -600,8 +611,14 @@ __global__ void __launch_bounds__(32 * WARPS, BZ_F32_MIN_BLOCKS) k_collide_f32(c
         } else if (u >= total) {
             break;
         }
-        const CollideArgs<float>& P = batch ? boxes[b] : one;
-        collide_unit<MODE, GROUPS>(P, batch ? u - prefix[b] : u, step, smem[warp], dq, (unsigned long long)b << 48);
+        // one call site per instantiation: a single box reads its arguments
+        // from the constant bank, a batch box from global memory; the
+        // arithmetic is the same source, so a box gives the same bits either way
+        if (BATCH)
+            collide_unit<MODE, GROUPS, false>(boxes[b], u - prefix[b], step, smem[warp], dq,
+                                              (unsigned long long)b << 48);
+        else
+            collide_unit<MODE, GROUPS, true>(one, u, step, smem[warp], dq, 0ull);
         u += dyn ? 1 : nwarps;
     }
     __syncwarp();
@@ -640,7 +657,7 @@ template <int MODE, bool GROUPS>
 static int resident_blocks()
 {
     static int n = 0;
-    if (!n && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_f32<MODE, GROUPS>, 32 * WARPS, 0) !=
+    if (!n && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_f32<MODE, GROUPS, false>, 32 * WARPS, 0) !=
                    cudaSuccess || n < 1))
         n = 1;
     return n;
@@ -656,16 +673,16 @@ int collide_f32_resident_blocks(const CollideArgs<float>& a)
 cudaError_t launch_collide_f32(const CollideArgs<float>& a, int grid, unsigned long long* counter, cudaStream_t s)
 {
     if (a.rec_stride)
-        k_collide_f32<M_RECORD, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
+        k_collide_f32<M_RECORD, true, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                    a.qitems, a.qcap);
     else if (a.sampler == SAMPLER_LEARNED)
-        k_collide_f32<M_LEARNED, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
+        k_collide_f32<M_LEARNED, true, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                     a.qitems, a.qcap);
     else if (has_groups(a))
-        k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
+        k_collide_f32<M_UNIFORM, true, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1, a.qcount,
                                                                     a.qitems, a.qcap);
     else
-        k_collide_f32<M_UNIFORM, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1,
+        k_collide_f32<M_UNIFORM, false, false><<<grid, 32 * WARPS, 0, s>>>(a, nullptr, nullptr, 0, counter, nullptr, 1,
                                                                      a.qcount, a.qitems, a.qcap);
     return cudaGetLastError();
 }
@@ -675,7 +692,7 @@ cudaError_t launch_collide_f32_batch(const CollideArgs<float>* boxes, const int6
                                      int* qcount, unsigned long long* qitems, long long qcap, cudaStream_t s)
 {
     const CollideArgs<float> none{};
-    k_collide_f32<M_UNIFORM, true><<<grid, 32 * WARPS, 0, s>>>(none, boxes, prefix, nboxes, counter, step_dev, chunk, qcount,
+    k_collide_f32<M_UNIFORM, true, true><<<grid, 32 * WARPS, 0, s>>>(none, boxes, prefix, nboxes, counter, step_dev, chunk, qcount,
                                                           qitems, qcap);
     return cudaGetLastError();
 }
