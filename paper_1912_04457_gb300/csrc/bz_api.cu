@@ -37,6 +37,9 @@ struct bz_handle_s {
     long long* d_flags = nullptr;
     void* d_freal = nullptr;       // f of the state, double-sized
     int* d_jtab = nullptr;         // packed (jx, jy, jz) of every p cell
+    double* d_ppu = nullptr;       // thermal masses: the distinct p^2 of the cell centres
+    unsigned short* d_pidx = nullptr;  // and each p cell's index into them
+    int nu = 0;                    // their count (0: no table)
     float* d_inv_e = nullptr;      // drift scratch: 1/E of every cell (inhomogeneous grids)
     float* d_gforce = nullptr;     // force-term scratch: g_i per (x cell, mass slot, axis)
     float* d_m2f = nullptr;        // drift scratch: FP32 m^2 per (x cell, mass slot)
@@ -163,6 +166,11 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_freal);
     cudaFree(h->d_jtab);
     h->d_jtab = nullptr;
+    cudaFree(h->d_ppu);
+    h->d_ppu = nullptr;
+    cudaFree(h->d_pidx);
+    h->d_pidx = nullptr;
+    h->nu = 0;
     cudaFree(h->d_inv_e);
     h->d_inv_e = nullptr;
     cudaFree(h->d_gforce);
@@ -221,6 +229,55 @@ static int alloc_scratch(bz_handle h)
         return fail(h, BZ_ENOMEM, "cannot allocate the force-term scratch");
     if (h->nxc > 1 && !h->d_m2f && cudaMalloc(&h->d_m2f, sizeof(float) * 4 * h->nxc) != cudaSuccess)
         return fail(h, BZ_ENOMEM, "cannot allocate the drift's mass table");
+    return BZ_OK;
+}
+
+// The distinct values of p^2 = (px^2 + py^2) + pz^2 over the cell centres
+// p = -L + (j + 1/2) dp (FP64, in that order of operations: the same bits as
+// the mass kernels' per-cell evaluation) and each cell's index into them,
+// for the thermal-mass kernel, which then evaluates 1/(2E) once per distinct
+// value and x cell.  Grids with more than MASS_TAB_MAX distinct values get no
+// table (nu = 0).  Returns BZ_OK or BZ_ENOMEM / BZ_ECUDA.
+static int build_p2_table(bz_handle h)
+{
+    h->nu = 0;
+    if (h->npc > ((int64_t)1 << 24)) return BZ_OK;
+    double dp[3];
+    std::vector<double> pc[3];
+    for (int d = 0; d < 3; ++d) {
+        dp[d] = 2.0 * h->g.L / h->g.np[d];
+        for (int j = 0; j < h->g.np[d]; ++j) pc[d].push_back(-h->g.L + ((double)j + 0.5) * dp[d]);
+    }
+    std::vector<double> values;
+    std::vector<unsigned short> idx((size_t)h->npc);
+    std::vector<std::pair<uint64_t, int>> seen;  // bit pattern -> index, kept sorted
+    int64_t k = 0;
+    for (int jx = 0; jx < h->g.np[0]; ++jx)
+        for (int jy = 0; jy < h->g.np[1]; ++jy)
+            for (int jz = 0; jz < h->g.np[2]; ++jz, ++k) {
+                const double px = pc[0][jx], py = pc[1][jy], pz = pc[2][jz];
+                const double pp = (px * px + py * py) + pz * pz;
+                uint64_t bits;
+                std::memcpy(&bits, &pp, sizeof bits);
+                auto it = std::lower_bound(seen.begin(), seen.end(), std::make_pair(bits, -1));
+                int id;
+                if (it != seen.end() && it->first == bits) {
+                    id = it->second;
+                } else {
+                    if ((int)values.size() >= MASS_TAB_MAX) return BZ_OK;
+                    id = (int)values.size();
+                    values.push_back(pp);
+                    seen.insert(it, std::make_pair(bits, id));
+                }
+                idx[(size_t)k] = (unsigned short)id;
+            }
+    if (cudaMalloc(&h->d_ppu, sizeof(double) * values.size()) != cudaSuccess ||
+        cudaMalloc(&h->d_pidx, sizeof(unsigned short) * idx.size()) != cudaSuccess)
+        return fail(h, BZ_ENOMEM, "cannot allocate the p^2 table");
+    if (cudaMemcpy(h->d_ppu, values.data(), sizeof(double) * values.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_pidx, idx.data(), sizeof(unsigned short) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(h, BZ_ECUDA, "cannot upload the p^2 table");
+    h->nu = (int)values.size();
     return BZ_OK;
 }
 
@@ -303,6 +360,12 @@ extern "C" int bz_init_grid(bz_handle* out, const bz_grid* g)
         free_scratch(h);
         delete h;
         return fail(nullptr, BZ_ECUDA, "cannot build the p-cell index table");
+    }
+    if ((rc = build_p2_table(h)) != BZ_OK) {
+        g_init_error = h->err;
+        free_scratch(h);
+        delete h;
+        return rc;
     }
     if ((rc = alloc_scratch(h)) != BZ_OK) {
         g_init_error = h->err;
@@ -544,6 +607,9 @@ static void fill_masses(bz_handle h, MassArgs& a, const long long* state, long l
     a.pref_q = 2.0 * CF * g2;
     a.meas = dpx * dpy * dpz / (twopi * twopi * twopi);
     a.limit = INT64_MAX / (h->npc > 0 ? h->npc : 1) / 2;
+    a.ppu = h->d_ppu;
+    a.pidx = h->d_pidx;
+    a.nu = h->nu;
 }
 
 static int compute_masses(bz_handle h, const long long* state, cudaStream_t s)

@@ -187,7 +187,14 @@ struct MassArgs {
     double pref_g, pref_q, meas;
     long long limit;
     int64_t chunk;          // bins per block (set by launch_masses)
+    // the distinct values of p^2 = (px^2 + py^2) + pz^2 over the cell centres
+    // (FP64, in the order of the formula) and the index of each cell's value,
+    // or nu = 0 (no table: grids with more than MASS_TAB_MAX distinct values)
+    const double* ppu;
+    const unsigned short* pidx;  // [npc]
+    int nu;
 };
+constexpr int MASS_TAB_MAX = 6144;  // 4 x 6144 doubles of 1/(2E) per block in shared memory
 
 struct DriftArgs {
     const long long* in;

@@ -4,6 +4,7 @@
 // which threads accumulate.
 #include <cstdint>
 #include "bz_internal.h"
+#include "exact64.cuh"
 #include "intconv.cuh"
 
 namespace bz {
@@ -119,6 +120,143 @@ __device__ __forceinline__ void masses_block(const MassArgs& P, int64_t x, int64
     }
 }
 
+// One bin of the Eq. (mg), (mq) sums in FP64 with the factors r = 1/(2E)
+// given (0 for a skipped species pair): the integer parts of 3x and 24x the
+// bin integrands in 2^-30 of f, exactly as in masses_block.
+__device__ __forceinline__ void mass_bin_fp64(const long long nsp[NSPEC], const double r[4], const bool skip[4],
+                                              long long* qg, long long qq[3])
+{
+    const double ng = skip[0] ? 0.0 : (double)nsp[0];
+    double q[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q[i] = skip[1 + i] ? 0.0 : (double)(nsp[1 + i] + nsp[4 + i]);
+    const double g3 = 9.0 * ng * r[0] + 4.0 * ((q[0] * r[1] + q[1] * r[2]) + q[2] * r[3]);
+    *qg = __double2ll_rn(g3 * MASS_FX);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) qq[i] = __double2ll_rn((3.0 * ng * r[0] + 4.0 * q[i] * r[1 + i]) * MASS_FX);
+}
+
+// Thermal masses with the table of distinct p^2 values: the same sums as
+// masses_block, bit for bit.  A block (x cell, chunk of bins) first evaluates
+// r_a = 1/(2 E_a) = 0.5 / sqrt(p^2 + m_a^2) once per distinct p^2 (496 values
+// for the 20^3 grid instead of 8000 cells), in shared memory; every bin then
+// reads its r.  GLUON_ONLY (no quark slot): with the quark pairs skipped, the
+// bin integrands reduce to 3x: rint(2^-10 RN(RN(9 n) r_g)) and 24x:
+// rint(2^-10 RN(RN(3 n) r_g)) (the quark terms add +0), and for |n| < 2^49
+// 9n and 3n are exact integers, so each is one integer-times-double product
+// and one conversion, evaluated with integer instructions (exact64.cuh: the
+// same IEEE round-to-nearest-even results) instead of FP64 ones.  Bins outside
+// that range, and blocks whose r is not a normal double in [2^-900, 2^900],
+// take the FP64 instructions.
+// Species pairs whose 1/(2E) the mass sums skip: no state of the pair and
+// E^2 = p^2 + m^2 > 0 for every p (a skipped pair adds +0, see masses_block).
+__device__ __forceinline__ void mass_skips(const MassArgs& P, const double m2p[4], bool skip[4])
+{
+    skip[0] = P.slot_of[0] < 0 && m2p[0] >= 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) skip[1 + i] = P.slot_of[1 + i] < 0 && P.slot_of[4 + i] < 0 && m2p[1 + i] >= 0.0;
+}
+
+__device__ __forceinline__ void mass_prev(const MassArgs& P, int64_t x, double m2p[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) m2p[i] = P.m2_prev ? P.m2_prev[x * 4 + i] : 0.0;
+}
+
+template <bool GLUON_ONLY>
+__global__ void __launch_bounds__(256, 4) k_masses_tab(const __grid_constant__ MassArgs P)
+{
+    extern __shared__ double s_r[];  // [4][nu]
+    const int nu = P.nu;
+    const int64_t nchunk = (P.npc + P.chunk - 1) / P.chunk;
+    const int64_t x = blockIdx.x / nchunk, c0 = (blockIdx.x % nchunk) * P.chunk;
+    double m2p[4];
+    bool skip[4];
+    mass_prev(P, x, m2p);
+    mass_skips(P, m2p, skip);
+    int ok = 1;
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+        const double pp = P.ppu[u];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) s_r[s * nu + u] = skip[s] ? 0.0 : 0.5 / sqrt(pp + m2p[s]);
+        const double rg = s_r[u];
+        ok &= (rg >= 0x1p-900 && rg <= 0x1p+900) ? 1 : 0;
+    }
+    ok = __syncthreads_and(ok);
+    const bool fast = GLUON_ONLY && ok && skip[1] && skip[2] && skip[3];
+    long long sg = 0, sq[3] = {0, 0, 0};
+    bool ovf = false;
+    const long long* st0 = P.state + x * P.npc;  // slot 0 (the gluons when GLUON_ONLY)
+    const int64_t jend = c0 + P.chunk < P.npc ? c0 + P.chunk : P.npc;
+    constexpr int AHEAD = 4;  // bins whose loads are in flight together
+    for (int64_t jb = c0 + threadIdx.x; jb < jend; jb += AHEAD * (int64_t)blockDim.x) {
+        long long nb[AHEAD];
+        int ub[AHEAD];
+#pragma unroll
+        for (int k = 0; k < AHEAD; ++k) {
+            const int64_t j = jb + k * (int64_t)blockDim.x;
+            nb[k] = (fast && j < jend) ? st0[j] : 0;
+            ub[k] = j < jend ? P.pidx[j] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < AHEAD; ++k) {
+        const int64_t j = jb + k * (int64_t)blockDim.x;
+        if (j >= jend) break;
+        const int u = ub[k];
+        long long qg, qq[3];
+        bool done = false;
+        if (fast) {
+            const long long n = nb[k];
+            const uint64_t a = n < 0 ? 0ull - (uint64_t)n : (uint64_t)n;
+            if (a == 0) {
+                qg = qq[0] = 0;
+                done = true;
+            } else if (a < (1ull << 49)) {
+                Exact64 rg = x64_from_double(s_r[u]);
+                rg.neg = n < 0;  // r > 0: the sign of n
+                done = x64_rint_scaled(x64_mul_u(9ull * a, rg), -10, &qg) &
+                       x64_rint_scaled(x64_mul_u(3ull * a, rg), -10, &qq[0]);
+            }
+            qq[1] = qq[2] = qq[0];
+        }
+        if (!done) {
+            long long nsp[NSPEC];
+#pragma unroll
+            for (int s = 0; s < NSPEC; ++s) {
+                const int sl = P.slot_of[s];
+                nsp[s] = sl < 0 ? 0 : P.state[((int64_t)sl * P.nxc + x) * P.npc + j];
+            }
+            const double r[4] = {s_r[u], s_r[nu + u], s_r[2 * nu + u], s_r[3 * nu + u]};
+            mass_bin_fp64(nsp, r, skip, &qg, qq);
+        }
+        ovf |= qg > P.limit || qg < -P.limit;
+        sg += qg;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (fast && i > 0) break;  // the three quark-flavour sums are equal: added once, copied below
+            ovf |= qq[i] > P.limit || qq[i] < -P.limit;
+            sq[i] += qq[i];
+        }
+        }
+    }
+    if (fast) sq[1] = sq[2] = sq[0];
+    __shared__ long long red[4][8];
+    long long v[4] = {sg, sq[0], sq[1], sq[2]};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] = warp_sum(v[i]);
+        if (lane == 0) red[i][warp] = v[i];
+    }
+    if (ovf) red_add_ll(&P.flags[2], 1);
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        red_add_ll(&P.acc[x * 4 + threadIdx.x], t);
+    }
+}
+
 __global__ void __launch_bounds__(256, BZ_MASS_MINB) k_masses(const __grid_constant__ MassArgs P)
 {
     const int64_t nchunk = (P.npc + P.chunk - 1) / P.chunk;
@@ -168,13 +306,29 @@ cudaError_t launch_masses(const MassArgs& a, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * a.nxc, s);
     if (e != cudaSuccess) return e;
-    // chunks of 256 to 2048 bins, enough blocks for every SM on small grids
+    // chunks of 256 to 2048 bins, enough blocks for every SM on small grids;
+    // with the p^2 table a block of many x cells' grid takes a whole x cell,
+    // so that each x cell's table is evaluated once
     MassArgs b = a;
     const int64_t per_x = ((int64_t)4 * device_sms() + a.nxc - 1) / a.nxc;
     int64_t chunk = ((a.npc + per_x - 1) / per_x + 255) / 256 * 256;
     b.chunk = chunk < 256 ? 256 : (chunk > MASS_CHUNK ? MASS_CHUNK : chunk);
+    if (a.nu > 0 && per_x == 1) b.chunk = a.npc;
     const int64_t nchunk = (a.npc + b.chunk - 1) / b.chunk;
-    k_masses<<<(unsigned)(nchunk * a.nxc), 256, 0, s>>>(b);
+    if (a.nu > 0 && a.nu <= MASS_TAB_MAX) {
+        bool gluon_only = a.slot_of[0] == 0;
+        for (int s = 1; s < NSPEC; ++s) gluon_only = gluon_only && a.slot_of[s] < 0;
+        const size_t smem = sizeof(double) * 4 * (size_t)a.nu;
+        if (gluon_only) {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(k_masses_tab<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_masses_tab<true><<<(unsigned)(nchunk * a.nxc), 256, smem, s>>>(b);
+        } else {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(k_masses_tab<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_masses_tab<false><<<(unsigned)(nchunk * a.nxc), 256, smem, s>>>(b);
+        }
+    } else {
+        k_masses<<<(unsigned)(nchunk * a.nxc), 256, 0, s>>>(b);
+    }
     k_masses_finish<<<(unsigned)((a.nxc + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -467,3 +467,29 @@ def test_f32_step_with_force_conserves_number():
     got = dev.cpu().numpy()
     assert int(got.sum()) == int(st.sum())
     assert not np.array_equal(got.reshape(st.shape), st)
+
+
+@pytest.mark.parametrize("mask", [0x01, 0x13])
+def test_masses_table_path_extreme_states(mask):
+    """The thermal masses through the p^2 table (one 1/(2E) per distinct p^2
+    and x cell) and, for gluon-only states, the integer evaluation of the bin
+    products: bit-identical to the oracle on an inhomogeneous grid with
+    negative cells and cells beyond 2^49 (which take the FP64 instructions),
+    for the first evaluation (E = |p|) and the second (E from the first)."""
+    from paper_1912_04457_gb300 import bz
+    torch = torch_mod()
+    nx, np_ = (4, 2, 3), (20, 20, 20)
+    nxc = 24
+    h, cfg = make_pair(nx=nx, dx=0.2, np_=np_, mask=mask)
+    st = random_state(mask, nxc, np_, 14, -0.2, 0.8)
+    rng = np.random.default_rng(15)
+    flat = st.reshape(-1)
+    big = rng.choice(flat.size, size=200, replace=False)
+    flat[big] = rng.integers(1 << 49, 1 << 52, size=200) * rng.choice([-1, 1], size=200)
+    dev = to_dev(st)
+    A = torch.empty(st.size, dtype=torch.int64, device="cuda")
+    h.collision_term(dev, A, 1, 0, 0.01, bz.PREC_F32)
+    m1 = O.masses(cfg, st)
+    assert np.array_equal(h.get_masses(), m1)
+    h.collision_term(dev, A, 1, 1, 0.01, bz.PREC_F32)
+    assert np.array_equal(h.get_masses(), O.masses(cfg, st, m1))
