@@ -364,6 +364,32 @@ def run_bz(args):
                           "the binning of the legs, so the two agree up to that error"}
         del f_n, mom_a, mom_b, src
 
+    # step loop of several steps per call: replayed step graphs against direct
+    # launches (outside the timed region; launch-bound small boxes gain)
+    step_loop = None
+    if rank == 0 and 1e3 * t_max / args.steps < 5.0:
+        loop = {}
+        nloop = 10
+        for mode in ("graph", "direct"):
+            if mode == "direct":
+                os.environ["BZ_STEP_GRAPH"] = "0"
+            s_loop = state.clone()
+            h.step(s_loop, w.dt, nloop, w.nsamples, prec, step0=4000)   # warm (captures the graph)
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h.step(s_loop, w.dt, nloop, w.nsamples, prec, step0=4000 + nloop)
+            b.record(stream)
+            barrier()
+            loop[mode] = {"ms_per_step": a.elapsed_time(b) / nloop, "checksum": int(s_loop.sum().item())}
+            os.environ.pop("BZ_STEP_GRAPH", None)
+            del s_loop
+        step_loop = {"steps_per_call": nloop, "graph": loop["graph"], "direct": loop["direct"],
+                     "same_state": loop["graph"]["checksum"] == loop["direct"]["checksum"],
+                     "note": "one bz_step call of 10 steps: the first step launched directly, then 2-step CUDA "
+                             "graphs replayed (device-side step index), against every step launched directly "
+                             "(BZ_STEP_GRAPH=0); not part of the timed loop, which calls one step at a time"}
+
     # streaming kernels of inhomogeneous grids against the HBM roofline, and the
     # cost of the optional force term (outside the timed region)
     transport = None
@@ -470,6 +496,7 @@ def run_bz(args):
             "clocks": clk,
             "fp64_gpu_path": fp64,
             "transport": transport,
+            "step_loop": step_loop,
             "physics": {
                 "number_conserved_exactly": number_conserved,
                 "species": {I.SPECIES[sp]: {"number_density_GeV3": float(mom_last[:, k, 0].mean()),

@@ -33,6 +33,8 @@
  *   share the work units -- taking them from a global counter, or one unit
  *   per warp -- which is otherwise chosen by size; both give the same bits
  *   (a test checks it).  Unset or any other value: chosen by size.
+ *   BZ_STEP_GRAPH=0 (read by bz_step) launches every step of an FP32 run
+ *   eagerly instead of replaying captured step graphs (same bits).
  */
 #ifndef BZ_H
 #define BZ_H
@@ -151,7 +153,13 @@ int bz_drift(bz_handle h, const int64_t* in, int64_t* out, double dt, void* stre
  *   n^{n+1} = drift(n^n) + collision increment(n^n)
  * with Philox step index step0 + k.  state (device int64) is updated in
  * place.  moments_out (device, may be NULL): per step, the moments of
- * n^{n+1} as bz_moments, [nsteps][nx][nslots][5] doubles. */
+ * n^{n+1} as bz_moments, [nsteps][nx][nslots][5] doubles.
+ * With BZ_PREC_F32 and nsteps >= 3 the first step is launched directly and
+ * the following pairs of steps replay a CUDA graph of two captured steps
+ * (the step index and moments slot live in device memory), kept on the
+ * handle for the next call with the same state, moments buffer, dt and
+ * nsamples and no setter call in between; the results are those of direct
+ * launches, bit for bit.  While bz_profile is on every step is direct. */
 int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, int32_t nsamples,
             int32_t prec, int32_t step0, double* moments_out, void* stream);
 

@@ -79,6 +79,20 @@ struct bz_handle_s {
     double T = 0.5;
     double mu[NSPEC] = {0};
     int64_t a_stride = 1, a_offset = 0;
+    // replayed step loop (FP32): two steps captured as one CUDA graph, the step
+    // index and moments slot in device memory; every setter bumps gen, which
+    // retires the graph
+    unsigned gen = 0;
+    int* d_step_idx = nullptr;     // [2]: step index, moments slot
+    cudaStream_t cap_stream = nullptr;
+    struct StepGraph {               // one per parity of the current mass buffer
+        cudaGraphExec_t exec = nullptr;
+        const long long* cur = nullptr;
+        const double* mom = nullptr;
+        double dt = 0;
+        int nsamples = 0, sampler = 0;
+        unsigned gen = 0;
+    } sg[2];
     std::string err;
 };
 
@@ -157,8 +171,20 @@ static bool dalloc(T** p, size_t n)
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1)) == cudaSuccess;
 }
 
+static void drop_step_graph(bz_handle h, int parity)
+{
+    if (h->sg[parity].exec) cudaGraphExecDestroy(h->sg[parity].exec);
+    h->sg[parity].exec = nullptr;
+}
+
 static void free_scratch(bz_handle h)
 {
+    drop_step_graph(h, 0);
+    drop_step_graph(h, 1);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
+    cudaFree(h->d_step_idx);
+    h->d_step_idx = nullptr;
     cudaFree(h->d_m2[0]);
     cudaFree(h->d_m2[1]);
     cudaFree(h->d_acc);
@@ -425,6 +451,7 @@ extern "C" int bz_destroy(bz_handle h)
 extern "C" int bz_set_species(bz_handle h, uint32_t species_mask, double alpha_s, int mass_mode)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if ((species_mask & 0x7Fu) == 0 || (species_mask & ~0x7Fu)) return fail(h, BZ_EINVAL, "bad species mask 0x%x", species_mask);
     if (!(alpha_s > 0)) return fail(h, BZ_EINVAL, "alpha_s must be positive");
     if (mass_mode < 0 || mass_mode > 2) return fail(h, BZ_EINVAL, "bad mass mode %d", mass_mode);
@@ -455,6 +482,7 @@ extern "C" int bz_query_sizes(bz_handle h, int32_t* nslots, int64_t* nxcells, in
 extern "C" int bz_set_uniform_bits(bz_handle h, int32_t bits)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (bits != 32 && bits != 23) return fail(h, BZ_EINVAL, "uniform bits must be 32 or 23");
     h->f64_ubits = bits;
     return BZ_OK;
@@ -464,6 +492,7 @@ extern "C" int bz_set_matrix_element(bz_handle h, int32_t row, int32_t nterms, c
                                      const int32_t* exps)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (row < 0 || row >= MSQ_ROWS) return fail(h, BZ_EINVAL, "|M|^2 row must be in [0, %d)", MSQ_ROWS);
     if (nterms < 0 || nterms > 8) return fail(h, BZ_EINVAL, "a user row has 0 to 8 terms");
     if (nterms > 0 && (!coef || !exps)) return fail(h, BZ_EINVAL, "null coefficients or exponents");
@@ -493,6 +522,7 @@ extern "C" int bz_set_matrix_element(bz_handle h, int32_t row, int32_t nterms, c
 extern "C" int bz_set_parameterisation(bz_handle h, int32_t which)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (which != 0 && which != 1) return fail(h, BZ_EINVAL, "parameterisation must be 0 (k2) or 1 (k3)");
     h->param = which;
     return BZ_OK;
@@ -501,6 +531,7 @@ extern "C" int bz_set_parameterisation(bz_handle h, int32_t which)
 extern "C" int bz_set_force_term(bz_handle h, int32_t enable)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (enable != 0 && enable != 1) return fail(h, BZ_EINVAL, "enable must be 0 or 1");
     h->force = enable == 1;
     return BZ_OK;
@@ -509,6 +540,7 @@ extern "C" int bz_set_force_term(bz_handle h, int32_t enable)
 extern "C" int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (stride < 1 || offset < 0 || offset >= stride) return fail(h, BZ_EINVAL, "bad anchor subset");
     h->a_stride = stride;
     h->a_offset = offset;
@@ -518,6 +550,7 @@ extern "C" int bz_set_anchor_subset(bz_handle h, int64_t stride, int64_t offset)
 extern "C" int bz_set_equilibrium(bz_handle h, int enable, double T, const double* mu_host)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (enable && !(T > 0)) return fail(h, BZ_EINVAL, "T must be positive");
     h->analytic = enable ? 1 : 0;
     h->T = T;
@@ -536,6 +569,7 @@ extern "C" int bz_get_masses(bz_handle h, double* m2_host)
 extern "C" int bz_set_masses(bz_handle h, const double* m2_host)
 {
     if (!h || !m2_host) return BZ_EINVAL;
+    ++h->gen;
     for (int64_t i = 0; i < 4 * h->nxc; ++i)
         if (!(m2_host[i] >= 0)) return fail(h, BZ_EINVAL, "masses squared must be >= 0");
     CK(h, cudaDeviceSynchronize());
@@ -547,6 +581,7 @@ extern "C" int bz_set_masses(bz_handle h, const double* m2_host)
 extern "C" int bz_reset_masses(bz_handle h)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     h->have_masses = false;
     return BZ_OK;
 }
@@ -807,7 +842,7 @@ static void fill_collide(bz_handle h, CollideArgs<R>& a, long long* A, int nsamp
 }
 
 static int run_collide(bz_handle h, long long* A, int nsamples, int step, double dt, int prec, int sampler,
-                       cudaStream_t s)
+                       cudaStream_t s, const int* step_dev = nullptr)
 {
     const int64_t n_sel = h->a_offset < h->ncell ? (h->ncell - h->a_offset + h->a_stride - 1) / h->a_stride : 0;
     const int64_t total = n_sel * (int64_t)nsamples;
@@ -833,6 +868,7 @@ static int run_collide(bz_handle h, long long* A, int nsamples, int step, double
                     (long long)units);
     CollideArgs<float> a{};
     fill_collide(h, a, A, nsamples, step, dt, sampler);
+    a.step_dev = step_dev;
     // a resident grid whose warps take one unit at a time from a counter; a
     // problem of at most two units per resident warp keeps one warp per unit
     // (no counter to reset, no atomics).  BZ_F32_SCHEDULE=counter|static
@@ -1082,6 +1118,7 @@ extern "C" int bz_save(bz_handle h, const int64_t* state, int64_t step, const ch
 extern "C" int bz_load(bz_handle h, int64_t* state, int64_t* step, const char* path)
 {
     if (!h || !state || !step || !path) return BZ_EINVAL;
+    ++h->gen;
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(h, BZ_EINVAL, "cannot open %s", path);
     CkptHeader hd{};
@@ -1177,6 +1214,37 @@ extern "C" int bz_energy_source(bz_handle h, const int64_t* state, const double*
     return BZ_OK;
 }
 
+// One Euler step from cur into nxt (Sec. III): masses of cur, drift into nxt
+// (with f of cur for the lookups), collision deposits into nxt, moments of
+// nxt.  Eager (step_dev null): step index `step`, moments at mom; inside a
+// captured graph: the step index and the moments slot of mom are read from
+// the device words step_dev[0], step_dev[1], advanced after the step.
+static int one_step(bz_handle h, long long* cur, long long* nxt, double dt, int nsamples, int prec, int step,
+                    double* mom, const int* step_dev, cudaStream_t s)
+{
+    int rc;
+    if ((rc = compute_masses(h, cur, s))) return rc;
+    DriftArgs d{};
+    fill_drift(h, d, cur, nxt, dt, h->analytic ? nullptr : h->d_freal, prec == BZ_PREC_F64);
+    {
+        ProfScope ps(h, BZ_K_DRIFT, s);
+        CK(h, launch_drift(d, s));
+    }
+    if ((rc = run_collide(h, nxt, nsamples, step, dt, prec, h->step_sampler, s, step_dev))) return rc;
+    if (mom) {
+        MomentArgs m{};
+        if ((rc = fill_moments(h, m, nxt, mom))) return rc;
+        if (step_dev) {
+            m.kidx = step_dev + 1;
+            m.kstride = h->nxc * h->nslots * 5;
+        }
+        ProfScope ps(h, BZ_K_MOMENTS, s);
+        CK(h, launch_moments(m, s));
+    }
+    if (step_dev) CK(h, launch_step_advance(const_cast<int*>(step_dev), const_cast<int*>(step_dev) + 1, s));
+    return BZ_OK;
+}
+
 extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, int32_t nsamples, int32_t prec,
                        int32_t step0, double* moments_out, void* stream)
 {
@@ -1190,25 +1258,64 @@ extern "C" int bz_step(bz_handle h, int64_t* state, double dt, int32_t nsteps, i
         return fail(h, BZ_ENOMEM, "cannot allocate the second state buffer");
     long long* cur = reinterpret_cast<long long*>(state);
     long long* nxt = h->d_state2;
-    for (int k = 0; k < nsteps; ++k) {
-        if ((rc = compute_masses(h, cur, s))) return rc;
-        DriftArgs d{};
-        fill_drift(h, d, cur, nxt, dt, h->analytic ? nullptr : h->d_freal, prec == BZ_PREC_F64);
-        {
-            ProfScope ps(h, BZ_K_DRIFT, s);
-            CK(h, launch_drift(d, s));
+    const int64_t mstride = h->nxc * h->nslots * 5;
+    int k = 0;
+    auto eager = [&]() -> int {
+        int r = one_step(h, cur, nxt, dt, nsamples, prec, step0 + k, moments_out ? moments_out + k * mstride : nullptr,
+                         nullptr, s);
+        if (r) return r;
+        std::swap(cur, nxt);
+        ++k;
+        return BZ_OK;
+    };
+    // FP32 runs of several steps replay a captured pair of steps (cur -> nxt ->
+    // cur, the mass buffers back in their roles): the same launches with the
+    // same arguments, so the same bits, at one launch per two steps.  The first
+    // step runs eagerly (it sizes the scratch, and a fresh handle's first
+    // masses take E = |p|); per-kernel profiling, and BZ_STEP_GRAPH=0 in the
+    // environment, keep every step eager.
+    const char* env = std::getenv("BZ_STEP_GRAPH");
+    const bool graphs = prec == BZ_PREC_F32 && !h->prof && !(env && !std::strcmp(env, "0"));
+    if (graphs && nsteps >= 3) {
+        if ((rc = eager())) return rc;
+        if (!h->d_step_idx && cudaMalloc(&h->d_step_idx, 2 * sizeof(int)) != cudaSuccess)
+            return fail(h, BZ_ENOMEM, "cannot allocate the step index");
+        if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(h, BZ_ECUDA, "cannot create the capture stream");
+        bz_handle_s::StepGraph& G = h->sg[h->cur];
+        if (!G.exec || G.cur != cur || G.mom != moments_out || G.dt != dt || G.nsamples != nsamples ||
+            G.sampler != h->step_sampler || G.gen != h->gen) {
+            drop_step_graph(h, h->cur);
+            CK(h, cudaStreamSynchronize(s));
+            cudaGraph_t graph = nullptr;
+            CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = one_step(h, cur, nxt, dt, nsamples, prec, step0 + k, moments_out, h->d_step_idx, h->cap_stream);
+            if (!rc) rc = one_step(h, nxt, cur, dt, nsamples, prec, step0 + k + 1, moments_out, h->d_step_idx,
+                                   h->cap_stream);
+            const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ce != cudaSuccess) return fail(h, BZ_ECUDA, "step graph capture failed: %s", cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&G.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                G.exec = nullptr;
+                return fail(h, BZ_ECUDA, "step graph instantiation failed: %s", cudaGetErrorString(ie));
+            }
+            G.cur = cur;
+            G.mom = moments_out;
+            G.dt = dt;
+            G.nsamples = nsamples;
+            G.sampler = h->step_sampler;
+            G.gen = h->gen;
         }
-        if ((rc = run_collide(h, nxt, nsamples, step0 + k, dt, prec, h->step_sampler, s))) return rc;
-        if (moments_out) {
-            MomentArgs m{};
-            if ((rc = fill_moments(h, m, nxt, moments_out + (int64_t)k * h->nxc * h->nslots * 5))) return rc;
-            ProfScope ps(h, BZ_K_MOMENTS, s);
-            CK(h, launch_moments(m, s));
-        }
-        long long* t = cur;
-        cur = nxt;
-        nxt = t;
+        CK(h, launch_set_step(h->d_step_idx, step0 + k, h->d_step_idx + 1, k, s));
+        for (; nsteps - k >= 2; k += 2) CK(h, cudaGraphLaunch(G.exec, s));
     }
+    while (k < nsteps)
+        if ((rc = eager())) return rc;
     if (cur != reinterpret_cast<long long*>(state))
         CK(h, cudaMemcpyAsync(state, cur, sizeof(long long) * h->ncell, cudaMemcpyDeviceToDevice, s));
     return BZ_OK;
@@ -1648,6 +1755,7 @@ extern "C" int bz_proposal_nparams(void) { return mlp_nparam(); }
 extern "C" int bz_proposal_init(bz_handle h, uint64_t seed)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     int rc = prop_alloc(h);
     if (rc) return rc;
     const int H = 128, NIN = 16, NOUT = 8;
@@ -1760,6 +1868,7 @@ static int anchor_prm_alloc(bz_handle h)
 extern "C" int bz_proposal_infer(bz_handle h, void* stream)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (!h->d_prop) return fail(h, BZ_EINVAL, "no proposal network (bz_proposal_init)");
     int rc = anchor_prm_alloc(h);
     if (rc) return rc;
@@ -1772,6 +1881,7 @@ extern "C" int bz_proposal_infer(bz_handle h, void* stream)
 extern "C" int bz_proposal_anchor_params(bz_handle h, float* out_host, const float* in_host)
 {
     if (!h || (!out_host && !in_host)) return BZ_EINVAL;
+    ++h->gen;
     int rc = anchor_prm_alloc(h);
     if (rc) return rc;
     CK(h, cudaDeviceSynchronize());
@@ -1789,6 +1899,7 @@ extern "C" int bz_proposal_anchor_params(bz_handle h, float* out_host, const flo
 extern "C" int bz_set_step_sampler(bz_handle h, int32_t sampler)
 {
     if (!h) return BZ_EINVAL;
+    ++h->gen;
     if (sampler != BZ_SAMPLER_SYMMETRIC && sampler != BZ_SAMPLER_LEARNED)
         return fail(h, BZ_EINVAL, "bz_step supports the symmetric and learned samplers");
     h->step_sampler = sampler;

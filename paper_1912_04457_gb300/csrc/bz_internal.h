@@ -145,6 +145,7 @@ struct CollideArgs {
     uint32_t ks[20];        // Philox key schedule: (k0, k1) of rounds 0..9, so a kernel whose
                             // arguments sit in the constant bank reads them as operands
     int nsamples, step;
+    const int* step_dev;    // FP32 path: the step index in device memory (a replayed step graph), or null: step
     int64_t n_sel, a_stride, a_offset;
     int sampler, mass_mode, analytic, p_center;
     int param;              // FP64 path: 0 k2 eliminated (the paper's choice), 1 k3 eliminated
@@ -243,6 +244,9 @@ struct MomentArgs {
     // ([x][slot][chunk][5] 128-bit as (lo, hi) int64 pairs) when nchunk > 1
     int nchunk;
     long long* part;
+    // a replayed step graph writes the moments of step *kidx at out + *kidx kstride (kidx null: out)
+    const int* kidx;
+    int64_t kstride;
 };
 
 // Per-slot scales of the f conversion: FP64 degeneracy, and the FP32
@@ -279,6 +283,9 @@ cudaError_t launch_moments_batch(const MomentArgs* boxes, const int* slot_prefix
                                  double* out, const int* kidx, int per_step, cudaStream_t s);
 cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, int* have_prev, int* step_dev,
                                   int* kidx, cudaStream_t s);
+// a replayed single-box step: set, then advance, the device step index and moments slot
+cudaError_t launch_set_step(int* step_dev, int step, int* kidx, int k, cudaStream_t s);
+cudaError_t launch_step_advance(int* step_dev, int* kidx, cudaStream_t s);
 #ifndef BZ_DEFER_TAU
 #define BZ_DEFER_TAU 2e-3
 #endif

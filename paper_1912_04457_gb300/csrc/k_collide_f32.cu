@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(32 * WARPS, (GROUPS && !BATCH) ? BZ_F32_MIN_BL
     const bool batch = BATCH;
     const bool dyn = counter != nullptr;  // chunks of units from the counter (a batch always)
     const int64_t total = batch ? prefix[nboxes] : f32_units(one.n_sel, one.nsamples);
-    const int step = batch ? *step_dev : one.step;
+    const int step = batch ? *step_dev : (one.step_dev ? *one.step_dev : one.step);
     int b = 0;
     int64_t u = dyn ? 0 : gw, stop = 0;  // next unit; end of the current chunk
     for (;;) {
@@ -946,11 +946,12 @@ __global__ void __launch_bounds__(256, BZ_FIX_MINB) k_fixup_f32(const __grid_con
     const int run = LEARNED ? (n + slots - 1) / slots : 1;
     const int i0 = LEARNED ? slot * run : slot, i1 = LEARNED ? min(n, i0 + run) : n, di = LEARNED ? 1 : slots;
     PropCache pc;
+    const int step = P.step_dev ? *P.step_dev : P.step;
     for (int i = i0; i < i1; i += di) {
         const unsigned long long it = qitems[seg * qcap + i];
         const int64_t a = (int64_t)(it >> 24);
         const int smp = (int)((it >> 4) & 0xFFFFFu), ti = (int)(it & 0xFu);
-        const long long own = fixup_term_ff<LEARNED>(P, a, smp, ti, P.step, pc);
+        const long long own = fixup_term_ff<LEARNED>(P, a, smp, ti, step, pc);
         if (own != 0 && bz_in(a, P.ncell)) red_add(&P.A[a], own);
     }
 }

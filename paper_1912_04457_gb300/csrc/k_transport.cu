@@ -1075,8 +1075,8 @@ __global__ void __launch_bounds__(256, BZ_MOM_MINB) k_moments(const __grid_const
     const int64_t x = row / P.nslots;
     const int sl = (int)(row % P.nslots);
     const int jlo = (int)((int64_t)c * P.npc / nch), jhi = (int)((int64_t)(c + 1) * P.npc / nch);
-    moments_block(P, x, sl, jlo, jhi, P.out + (x * P.nslots + sl) * 5,
-                  nch > 1 ? P.part + (int64_t)blockIdx.x * 10 : nullptr);
+    double* out = P.out + (P.kidx ? (int64_t)*P.kidx * P.kstride : 0);
+    moments_block(P, x, sl, jlo, jhi, out + (x * P.nslots + sl) * 5, nch > 1 ? P.part + (int64_t)blockIdx.x * 10 : nullptr);
 }
 
 // Adds the chunks' partial sums of each (x cell, slot) in chunk order.
@@ -1090,7 +1090,7 @@ __global__ void k_moments_finish(const __grid_constant__ MomentArgs P)
         for (int i = 0; i < 5; ++i)
             t[i] += (__int128)(((unsigned __int128)(unsigned long long)q[2 * i + 1] << 64) | (unsigned long long)q[2 * i]);
     }
-    moments_out(P, t, P.out + row * 5);
+    moments_out(P, t, P.out + (P.kidx ? (int64_t)*P.kidx * P.kstride : 0) + row * 5);
 }
 
 cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s)
@@ -1252,6 +1252,30 @@ cudaError_t launch_batch_end_step(double* m2_prev, const double* m2_cur, int n, 
                                   int* kidx, cudaStream_t s)
 {
     k_batch_end_step<<<(n + 127) / 128, 128, 0, s>>>(m2_prev, m2_cur, n, have_prev, step_dev, kidx);
+    return cudaGetLastError();
+}
+
+__global__ void k_set_step(int* step_dev, int step, int* kidx, int k)
+{
+    *step_dev = step;
+    *kidx = k;
+}
+
+__global__ void k_step_advance(int* step_dev, int* kidx)
+{
+    *step_dev += 1;
+    *kidx += 1;
+}
+
+cudaError_t launch_set_step(int* step_dev, int step, int* kidx, int k, cudaStream_t s)
+{
+    k_set_step<<<1, 1, 0, s>>>(step_dev, step, kidx, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_advance(int* step_dev, int* kidx, cudaStream_t s)
+{
+    k_step_advance<<<1, 1, 0, s>>>(step_dev, kidx);
     return cudaGetLastError();
 }
 

@@ -159,3 +159,35 @@ def test_counter_and_static_schedules_give_the_same_bits(np_, mask, N, monkeypat
         ref = O.collision(cfg, st, O.masses(cfg, st), N, step=1, dt=0.01, ubits=23)["A"]
         assert _rel_l2(out["counter"].reshape(ref.shape), ref) <= F32_TOL
     h.close()
+
+
+@pytest.mark.parametrize("nx,np_,mask,force,nsteps", [((1, 1, 1), (12, 12, 12), 0x01, False, 7),
+                                                      ((4, 3, 2), (6, 6, 6), 0x13, True, 6)])
+def test_replayed_step_graph_gives_the_eager_bits(nx, np_, mask, force, nsteps, monkeypatch):
+    """FP32 runs of several steps replay a captured pair of steps (device-side
+    step index and moments slot): state, masses and per-step moments equal
+    those of the same run with every step launched eagerly (BZ_STEP_GRAPH=0),
+    over two calls (the second reuses the graph)."""
+    import torch
+    from paper_1912_04457_gb300 import bz
+    nxc = int(np.prod(nx))
+    ns = bin(mask).count("1")
+    st = I.encode(I.random_f(np_, ns, nxc, 61, 0.02, 0.5), mask)
+    out = {}
+    for mode in ("graph", "eager"):
+        if mode == "eager":
+            monkeypatch.setenv("BZ_STEP_GRAPH", "0")
+        h = bz.Handle(nx=nx, dx=0.2, np_=np_, L=2.0, seed=4, species_mask=mask, alpha_s=0.3)
+        h.set_force_term(force)
+        dev = torch.from_numpy(st.reshape(-1)).cuda()
+        mom = torch.zeros(nsteps * nxc * ns * 5, dtype=torch.float64, device="cuda")
+        h.step(dev, 0.01, nsteps, 32, bz.PREC_F32, step0=3, moments_out=mom)
+        a = (dev.cpu().numpy().copy(), mom.cpu().numpy().copy(), h.get_masses())
+        h.step(dev, 0.01, nsteps, 32, bz.PREC_F32, step0=3 + nsteps, moments_out=mom)
+        out[mode] = (a, (dev.cpu().numpy().copy(), mom.cpu().numpy().copy(), h.get_masses()))
+        h.close()
+    monkeypatch.delenv("BZ_STEP_GRAPH")
+    for call in range(2):
+        for g, e in zip(out["graph"][call], out["eager"][call]):
+            assert np.array_equal(g, e)
+    assert int(out["graph"][1][0].sum()) == int(st.sum())
