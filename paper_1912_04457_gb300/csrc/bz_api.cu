@@ -64,7 +64,9 @@ struct bz_handle_s {
     float *d_prop = nullptr, *d_prop_g = nullptr, *d_prop_m = nullptr, *d_prop_v = nullptr;
     float* d_anchor_prm = nullptr;
     float* d_loss = nullptr;
-    double* d_wsum = nullptr;
+    double* d_wsum = nullptr;          // [sum_weights_scratch()]: the sum, then the per-warp partial sums
+    float* d_prop_part = nullptr;      // per-block gradients [4 nsm][nparam] and losses [4 nsm]
+    float* d_loss_part = nullptr;
     int adam_step = 0;
     bool anchor_prm_ready = false;
     int step_sampler = BZ_SAMPLER_SYMMETRIC;
@@ -226,6 +228,9 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_anchor_prm);
     cudaFree(h->d_loss);
     cudaFree(h->d_wsum);
+    cudaFree(h->d_prop_part);
+    cudaFree(h->d_loss_part);
+    h->d_prop_part = h->d_loss_part = nullptr;
     cudaFree(h->d_rec_count);
     h->d_rec_count = nullptr;
     h->d_prop = h->d_prop_g = h->d_prop_m = h->d_prop_v = h->d_anchor_prm = h->d_loss = nullptr;
@@ -1731,7 +1736,8 @@ static int prop_alloc(bz_handle h)
     const int n = mlp_nparam();
     if (h->d_prop) return BZ_OK;
     if (!dalloc(&h->d_prop, n) || !dalloc(&h->d_prop_g, n) || !dalloc(&h->d_prop_m, n) ||
-        !dalloc(&h->d_prop_v, n) || !dalloc(&h->d_loss, 1) || !dalloc(&h->d_wsum, 1))
+        !dalloc(&h->d_prop_v, n) || !dalloc(&h->d_loss, 1) || !dalloc(&h->d_wsum, sum_weights_scratch()) ||
+        !dalloc(&h->d_prop_part, (size_t)4 * h->nsm * n) || !dalloc(&h->d_loss_part, (size_t)4 * h->nsm))
         return fail(h, BZ_ENOMEM, "cannot allocate the proposal network");
     CK(h, cudaMemset(h->d_prop_g, 0, sizeof(float) * n));
     CK(h, cudaMemset(h->d_prop_m, 0, sizeof(float) * n));
@@ -1820,7 +1826,8 @@ extern "C" int bz_proposal_grad(bz_handle h, const void* records, int64_t n, flo
     CK(h, cudaMemsetAsync(loss, 0, sizeof(float), s));
     const int64_t nch = (n + 63) / 64;
     const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
-    CK(h, launch_mlp_grad(h->d_prop, prop_args(h), rec, n, (float)(1.0 / wsum), grad, loss, grid, s));
+    CK(h, launch_mlp_grad(h->d_prop, prop_args(h), rec, n, (float)(1.0 / wsum), grad, loss, grid, h->d_prop_part,
+                          h->d_loss_part, s));
     return BZ_OK;
 }
 
@@ -1849,7 +1856,7 @@ extern "C" int bz_proposal_train(bz_handle h, const void* records, int64_t n, in
         const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
         const uint64_t key = ((uint64_t)(h->adam_step + 1) << 32) * 0x9E3779B97F4A7C15ull;
         CK(h, launch_mlp_grad(h->d_prop, A, rec, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss, grid,
-                              s, n, key));
+                              h->d_prop_part, h->d_loss_part, s, n, key));
         CK(h, launch_adam(h->d_prop, h->d_prop_g, h->d_prop_m, h->d_prop_v, np, (float)lr, ++h->adam_step, s));
         if (losses_host) CK(h, cudaMemcpyAsync(&losses_host[k], h->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     }
@@ -1951,6 +1958,10 @@ extern "C" int bz_record(bz_handle h, const int64_t* state, int32_t nsamples, in
     unsigned long long n = 0;
     CK(h, cudaMemcpyAsync(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
-    if (n_written) *n_written = (int64_t)(n < (unsigned long long)max_records ? n : (unsigned long long)max_records);
+    const int64_t nw = (int64_t)(n < (unsigned long long)max_records ? n : (unsigned long long)max_records);
+    // a fixed order (warps append in arrival order); when the buffer overflowed
+    // the set of kept records itself depends on that order
+    CK(h, launch_sort_records(static_cast<ProposalRecord*>(records), nw, s));
+    if (n_written) *n_written = nw;
     return BZ_OK;
 }

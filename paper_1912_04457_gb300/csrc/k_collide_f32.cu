@@ -223,10 +223,13 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
 
     // phase B on n pending roots starting at head
     auto process = [&](int n) {
+        float w_root = 0.0f;  // record mode: sum of |c~| over this root's terms
+        int src_rec = -1 - lane;
         if (lane < n) {
             const int ri = (head + lane) & (RING - 1);
             const unsigned tg = S.tag[ri];
             const int src = tg & (SBUF - 1), t0 = (tg >> 24) & 15, tn = GROUPS ? (int)(tg >> 28) + 1 : 1;
+            src_rec = src;
             const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
             const float4 tmv0 = S.tm[t0];  // leg masses shared by the group's terms
             const float ma2 = tmv0.x, mc2 = tmv0.z;
@@ -281,7 +284,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const float ct = sym * W * M2 / den;
                     const float wq = ct * P.Kown * (MODE == M_LEARNED ? S.wfac[src] : 1.0f);
                     if (MODE == M_RECORD) {  // record mode: sum |c~| per sample, no deposits
-                        atomicAdd(&S.wfac[src], fabsf(ct));
+                        w_root += fabsf(ct);
                     } else if (!(fabsf(wq) < 4611686018427387904.0f)) {
                         red_add(&P.flags[1], 1);
                     } else {
@@ -297,6 +300,18 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     }
                 }
             }
+        }
+        if (MODE == M_RECORD) {
+            // add each root's |c~| to its sample in lane order (two roots of one
+            // sample can share this pass), so the record weights do not depend on
+            // the order of shared-memory atomics
+            const unsigned same = __match_any_sync(0xffffffffu, src_rec);
+            float acc = 0.0f;
+            for (int l = 0; l < 32; ++l) {
+                const float v = __shfl_sync(0xffffffffu, w_root, l);
+                if ((same >> l) & 1u) acc += v;
+            }
+            if (src_rec >= 0 && lane == __ffs(same) - 1) S.wfac[src_rec] += acc;
         }
         head += n;
         __syncwarp();

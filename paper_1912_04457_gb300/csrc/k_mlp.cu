@@ -214,10 +214,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+// Each block writes its own gradient and loss (part[block][NPARAM],
+// part_loss[block]); k_grad_reduce adds the blocks in block order, so the
+// result does not depend on which block finishes first.
 __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ params, const ProposalArgs A,
                                                      const ProposalRecord* __restrict__ rec, int64_t n, float inv_wsum,
-                                                     float* __restrict__ grad, float* loss_sum, int64_t ntot,
-                                                     uint64_t key)
+                                                     float* __restrict__ part, float* __restrict__ part_loss,
+                                                     int64_t ntot, uint64_t key)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
@@ -354,8 +357,8 @@ __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ p
         }
         __syncthreads();
     }
-    // ---- flush this block's gradient to global ----
-    float* gW1g = grad;
+    // ---- this block's gradient, every parameter written once ----
+    float* gW1g = part + (int64_t)blockIdx.x * NPARAM;
     float* gb1g = gW1g + NIN * H;
     float* gW2g = gb1g + H;
     float* gb2g = gW2g + H * H;
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ p
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-            atomicAdd(&gW2g[m * H + nn], gW2[i][e]);
+            gW2g[m * H + nn] = gW2[i][e];
         }
     }
 #pragma unroll
@@ -377,30 +380,51 @@ __global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ p
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int m = g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-            atomicAdd(&gW1g[m * H + nn], gW1[i][e]);
+            gW1g[m * H + nn] = gW1[i][e];
         }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const int m = warp * 16 + g + (e >> 1) * 8, nn = 2 * t + (e & 1);
-        atomicAdd(&gW3g[m * NOUT + nn], gW3[e]);
+        gW3g[m * NOUT + nn] = gW3[e];
     }
     for (int col = threadIdx.x; col < 2 * H + NOUT; col += blockDim.x) {
         const float s = S.db[col];
         if (col < H)
-            atomicAdd(&gb1g[col], s);
+            gb1g[col] = s;
         else if (col < 2 * H)
-            atomicAdd(&gb2g[col - H], s);
+            gb2g[col - H] = s;
         else
-            atomicAdd(&gb3g[col - 2 * H], s);
+            gb3g[col - 2 * H] = s;
     }
-    // loss
+    // loss: the two warps of record threads, in warp order
     loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 16);
     loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 8);
     loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 4);
     loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 2);
     loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 1);
-    if (lane == 0 && warp < 2) atomicAdd(loss_sum, loss_blk);
+    __shared__ float s_loss[2];
+    if (lane == 0 && warp < 2) s_loss[warp] = loss_blk;
+    __syncthreads();
+    if (threadIdx.x == 0) part_loss[blockIdx.x] = s_loss[0] + s_loss[1];
+}
+
+// grad[i] += sum over blocks b = 0, 1, ... of part[b][i]; loss = sum of the
+// blocks' losses in block order.
+__global__ void k_grad_reduce(const float* __restrict__ part, const float* __restrict__ part_loss, int nblk,
+                              float* __restrict__ grad, float* loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NPARAM) {
+        float s = 0.0f;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * NPARAM + i];
+        grad[i] += s;
+    }
+    if (i == 0) {
+        float l = 0.0f;
+        for (int b = 0; b < nblk; ++b) l += part_loss[b];
+        *loss = l;
+    }
 }
 
 // Adam on the FP32 master parameters; zeroes the gradient.
@@ -486,28 +510,81 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ par
     }
 }
 
+// Sum of the record weights in a fixed order: per warp of a fixed grid, then
+// the warps' sums in warp order (out[1..] holds the partial sums).
+constexpr int SUMW_BLOCKS = 256, SUMW_WARPS = SUMW_BLOCKS * 8;
 __global__ void k_sum_weights(const ProposalRecord* __restrict__ rec, int64_t n, double* out)
 {
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s += (double)rec[i].w;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+    if ((threadIdx.x & 31) == 0) out[1 + blockIdx.x * 8 + (threadIdx.x >> 5)] = s;
+}
+
+__global__ void k_sum_weights_final(double* out)
+{
+    double s = 0.0;
+    for (int w = 0; w < SUMW_WARPS; ++w) s += out[1 + w];
+    out[0] = s;
 }
 
 cudaError_t launch_sum_weights(const ProposalRecord* rec, int64_t n, double* out, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
-    if (e != cudaSuccess) return e;
-    k_sum_weights<<<256, 256, 0, s>>>(rec, n, out);
+    k_sum_weights<<<SUMW_BLOCKS, 256, 0, s>>>(rec, n, out);
+    k_sum_weights_final<<<1, 1, 0, s>>>(out);
+    return cudaGetLastError();
+}
+
+int sum_weights_scratch() { return 1 + SUMW_WARPS; }
+
+// Records in a fixed order: ascending by (anchor, the bits of y[0..4], of w),
+// so that the training data and its minibatches do not depend on the order
+// in which warps appended them.  Bitonic network for any n, in place: per
+// block size k the mirror step (i, i ^ (k - 1)), then (i, i ^ j) for j =
+// k/4 ... 1, each putting the smaller record at the lower index; a partner
+// at or beyond n counts as larger than every record.
+__device__ __forceinline__ bool rec_less(const ProposalRecord& x, const ProposalRecord& y)
+{
+    if (x.a != y.a) return x.a < y.a;
+    for (int i = 0; i < 5; ++i) {
+        const unsigned bx = __float_as_uint(x.y[i]), by = __float_as_uint(y.y[i]);
+        if (bx != by) return bx < by;
+    }
+    return __float_as_uint(x.w) < __float_as_uint(y.w);
+}
+
+__global__ void k_sort_records(ProposalRecord* rec, int64_t n, int64_t k, int64_t j, int mirror)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = mirror ? (i ^ (k - 1)) : (i ^ j);
+    if (p <= i || p >= n) return;
+    if (mirror && (i & (k >> 1))) return;
+    const ProposalRecord a = rec[i], b = rec[p];
+    if (rec_less(b, a)) {
+        rec[i] = b;
+        rec[p] = a;
+    }
+}
+
+cudaError_t launch_sort_records(ProposalRecord* rec, int64_t n, cudaStream_t s)
+{
+    int64_t P = 1;
+    while (P < n) P <<= 1;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    for (int64_t k = 2; k <= P; k <<= 1) {
+        k_sort_records<<<grid, 256, 0, s>>>(rec, n, k, 0, 1);
+        for (int64_t j = k >> 2; j >= 1; j >>= 1) k_sort_records<<<grid, 256, 0, s>>>(rec, n, k, j, 0);
+    }
     return cudaGetLastError();
 }
 
 int mlp_nparam() { return NPARAM; }
 
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
-                            float inv_wsum, float* grad, float* loss, int grid, cudaStream_t s, int64_t ntot,
-                            uint64_t key)
+                            float inv_wsum, float* grad, float* loss, int grid, float* part, float* part_loss,
+                            cudaStream_t s, int64_t ntot, uint64_t key)
 {
     const size_t smem = sizeof(TrainSmem);
     static bool attr = false;
@@ -516,7 +593,8 @@ cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const Pr
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_mlp_grad<<<grid, 256, smem, s>>>(params, A, rec, n, inv_wsum, grad, loss, ntot, key);
+    k_mlp_grad<<<grid, 256, smem, s>>>(params, A, rec, n, inv_wsum, part, part_loss, ntot, key);
+    k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(part, part_loss, grid, grad, loss);
     return cudaGetLastError();
 }
 

@@ -154,3 +154,34 @@ def test_trained_proposal_lowers_the_error():
     # compared by their median error
     print("uniform errors", np.round(eu, 3), "learned errors", np.round(el, 3))
     assert np.median(el) < 0.9 * np.median(eu)
+
+
+def test_recording_and_training_reproduce_bit_for_bit():
+    """Two record passes over the same state give the same records in the same
+    (sorted) order; two trainings from the same initial network on them give
+    the same parameters and losses; a gradient evaluation gives the same bits
+    twice.  (Gradients and losses are per-block partial sums added in block
+    order; record weights are summed per sample in a fixed lane order.)"""
+    import torch
+    from paper_1912_04457_gb300 import bz
+    np_, mask = (8, 8, 8), 0x7F
+    st = torch.from_numpy(I.encode(I.random_f(np_, 7, 1, 12, 0.05, 0.5), mask).reshape(-1)).cuda()
+    runs = []
+    for _ in range(2):
+        h = bz.Handle(np_=np_, L=2.0, seed=3, species_mask=mask)
+        rec, n = h.record(st, 16, step=5, dt=0.01, max_records=1 << 18)
+        assert n > 1000
+        h.proposal_init(21)
+        g, l = h.proposal_grad(rec, n)
+        losses = h.proposal_train(rec, n, 40, batch=4096, lr=2e-3)
+        runs.append((rec[: n * bz.RECORD_BYTES].cpu().numpy(), g.cpu().numpy(), float(l.item()), losses,
+                     h.proposal_params()))
+        h.close()
+    (r0, g0, l0, L0, p0), (r1, g1, l1, L1, p1) = runs
+    assert np.array_equal(r0, r1)
+    assert np.array_equal(g0, g1) and l0 == l1
+    assert np.array_equal(L0, L1)
+    assert np.array_equal(p0, p1)
+    recs = r0.view(REC)
+    assert np.all(np.diff(recs["a"]) >= 0)          # sorted by anchor first
+    assert np.all(recs["w"] > 0)
