@@ -413,7 +413,9 @@ int bz_proposal_grad(bz_handle h, const void* records, int64_t n, float* grad, f
 int bz_proposal_train(bz_handle h, const void* records, int64_t n, int32_t steps, int32_t batch, double lr,
                       float* losses_host, void* stream);
 /* Runs the network for every anchor of h (8 floats each: mu3 x3, sigma3,
- * sigma1, alpha, 0, 0); required before BZ_SAMPLER_LEARNED. */
+ * sigma1, alpha, 0, 0) on the tensor cores (tcgen05, 128 anchors per tile);
+ * required before BZ_SAMPLER_LEARNED.  Synchronises; BZ_ECUDA if a
+ * tensor-core wait timed out. */
 int bz_proposal_infer(bz_handle h, void* stream);
 /* Reads (out_host) and/or replaces (in_host) the per-anchor parameters,
  * host float [nslots nx np][8]; synchronises. */

@@ -67,6 +67,7 @@ struct bz_handle_s {
     double* d_wsum = nullptr;          // [sum_weights_scratch()]: the sum, then the per-warp partial sums
     float* d_prop_part = nullptr;      // per-block gradients [4 nsm][nparam] and losses [4 nsm]
     float* d_loss_part = nullptr;
+    int* d_prop_err = nullptr;         // tensor-core waits that timed out in the network's kernels
     int adam_step = 0;
     bool anchor_prm_ready = false;
     int step_sampler = BZ_SAMPLER_SYMMETRIC;
@@ -230,7 +231,9 @@ static void free_scratch(bz_handle h)
     cudaFree(h->d_wsum);
     cudaFree(h->d_prop_part);
     cudaFree(h->d_loss_part);
+    cudaFree(h->d_prop_err);
     h->d_prop_part = h->d_loss_part = nullptr;
+    h->d_prop_err = nullptr;
     cudaFree(h->d_rec_count);
     h->d_rec_count = nullptr;
     h->d_prop = h->d_prop_g = h->d_prop_m = h->d_prop_v = h->d_anchor_prm = h->d_loss = nullptr;
@@ -1737,7 +1740,8 @@ static int prop_alloc(bz_handle h)
     if (h->d_prop) return BZ_OK;
     if (!dalloc(&h->d_prop, n) || !dalloc(&h->d_prop_g, n) || !dalloc(&h->d_prop_m, n) ||
         !dalloc(&h->d_prop_v, n) || !dalloc(&h->d_loss, 1) || !dalloc(&h->d_wsum, sum_weights_scratch()) ||
-        !dalloc(&h->d_prop_part, (size_t)4 * h->nsm * n) || !dalloc(&h->d_loss_part, (size_t)4 * h->nsm))
+        !dalloc(&h->d_prop_part, (size_t)4 * h->nsm * n) || !dalloc(&h->d_loss_part, (size_t)4 * h->nsm) ||
+        !dalloc(&h->d_prop_err, 1))
         return fail(h, BZ_ENOMEM, "cannot allocate the proposal network");
     CK(h, cudaMemset(h->d_prop_g, 0, sizeof(float) * n));
     CK(h, cudaMemset(h->d_prop_m, 0, sizeof(float) * n));
@@ -1824,10 +1828,13 @@ extern "C" int bz_proposal_grad(bz_handle h, const void* records, int64_t n, flo
     if (!(wsum > 0)) return fail(h, BZ_EINVAL, "records carry no weight");
     CK(h, cudaMemsetAsync(grad, 0, sizeof(float) * mlp_nparam(), s));
     CK(h, cudaMemsetAsync(loss, 0, sizeof(float), s));
-    const int64_t nch = (n + 63) / 64;
-    const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
-    CK(h, launch_mlp_grad(h->d_prop, prop_args(h), rec, n, (float)(1.0 / wsum), grad, loss, grid, h->d_prop_part,
-                          h->d_loss_part, s));
+    CK(h, cudaMemsetAsync(h->d_prop_err, 0, sizeof(int), s));
+    CK(h, launch_mlp_grad(h->d_prop, prop_args(h), rec, n, (float)(1.0 / wsum), grad, loss, h->nsm, h->d_prop_part,
+                          h->d_loss_part, h->d_prop_err, s));
+    int herr = 0;
+    CK(h, cudaMemcpyAsync(&herr, h->d_prop_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, BZ_ECUDA, "proposal gradient: %d tensor-core waits timed out", herr);
     return BZ_OK;
 }
 
@@ -1849,18 +1856,19 @@ extern "C" int bz_proposal_train(bz_handle h, const void* records, int64_t n, in
     CK(h, cudaMemsetAsync(h->d_prop_g, 0, sizeof(float) * np, s));
     // each step's minibatch: b records drawn independently and uniformly from all n
     // (the record buffer is in arrival order, i.e. clustered by anchor)
+    CK(h, cudaMemsetAsync(h->d_prop_err, 0, sizeof(int), s));
     for (int k = 0; k < steps; ++k) {
         const int64_t b = batch;
-        CK(h, cudaMemsetAsync(h->d_loss, 0, sizeof(float), s));
-        const int64_t nch = (b + 63) / 64;
-        const int grid = (int)std::min<int64_t>(nch, (int64_t)h->nsm * 4);
         const uint64_t key = ((uint64_t)(h->adam_step + 1) << 32) * 0x9E3779B97F4A7C15ull;
-        CK(h, launch_mlp_grad(h->d_prop, A, rec, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss, grid,
-                              h->d_prop_part, h->d_loss_part, s, n, key));
+        CK(h, launch_mlp_grad(h->d_prop, A, rec, b, (float)(1.0 / (wbar * (double)b)), h->d_prop_g, h->d_loss, h->nsm,
+                              h->d_prop_part, h->d_loss_part, h->d_prop_err, s, n, key));
         CK(h, launch_adam(h->d_prop, h->d_prop_g, h->d_prop_m, h->d_prop_v, np, (float)lr, ++h->adam_step, s));
         if (losses_host) CK(h, cudaMemcpyAsync(&losses_host[k], h->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     }
-    if (losses_host) CK(h, cudaStreamSynchronize(s));
+    int herr = 0;
+    CK(h, cudaMemcpyAsync(&herr, h->d_prop_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, BZ_ECUDA, "proposal training: %d tensor-core waits timed out", herr);
     h->anchor_prm_ready = false;
     return BZ_OK;
 }
@@ -1880,7 +1888,13 @@ extern "C" int bz_proposal_infer(bz_handle h, void* stream)
     int rc = anchor_prm_alloc(h);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CK(h, launch_mlp_infer(h->d_prop, prop_args(h), h->ncell, h->d_anchor_prm, h->nsm * 2, s));
+    int* err = h->d_prop_err;
+    CK(h, cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(h, launch_mlp_infer(h->d_prop, prop_args(h), h->ncell, h->d_anchor_prm, h->nsm * 2, err, s));
+    int herr = 0;
+    CK(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (herr) return fail(h, BZ_ECUDA, "proposal inference: %d tensor-core waits timed out", herr);
     h->anchor_prm_ready = true;
     return BZ_OK;
 }

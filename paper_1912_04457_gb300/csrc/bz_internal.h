@@ -307,13 +307,16 @@ __host__ __device__ inline int64_t f32_units(int64_t n_sel, int nsamples)
 int mlp_nparam();
 // ntot > 0: minibatch position r reads record splitmix64(key + r) mod ntot of rec
 // (i.i.d. draws from all ntot records); ntot = 0: records [0, n) in order
-// part [grid][nparam], part_loss [grid]: per-block scratch, added in block order into grad (+=) and loss (=)
+// part [grid][nparam], part_loss [grid]: per-block scratch, added in block order into grad (+=) and loss (=);
+// err (device int): incremented by a block whose tensor-core wait timed out.  At most `grid` blocks, one
+// per SM (each holds 512 columns of tensor memory).
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
-                            float inv_wsum, float* grad, float* loss, int grid, float* part, float* part_loss,
+                            float inv_wsum, float* grad, float* loss, int grid, float* part, float* part_loss, int* err,
                             cudaStream_t s, int64_t ntot = 0, uint64_t key = 0);
 cudaError_t launch_adam(float* p, float* g, float* m, float* v, int n, float lr, int step, cudaStream_t s);
+// err (device int, zeroed by the caller): incremented by a CTA whose tensor-core wait timed out
 cudaError_t launch_mlp_infer(const float* params, const ProposalArgs& A, int64_t nanchor, float* out, int grid,
-                             cudaStream_t s);
+                             int* err, cudaStream_t s);
 // out[0] = sum of the weights in a fixed order; out needs sum_weights_scratch() doubles
 cudaError_t launch_sum_weights(const ProposalRecord* rec, int64_t n, double* out, cudaStream_t s);
 int sum_weights_scratch();

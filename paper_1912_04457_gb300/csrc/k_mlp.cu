@@ -28,40 +28,6 @@ namespace bz {
 
 namespace {
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi)
-{
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// C[16x8 tile at (m0, n0)] += A[m0.., 0..K) B[0..K, n0..], A(m, k) = A[m ars + k acs],
-// B(k, n) = B[k bks + n bns], K a multiple of 16.  Fragment layout of
-// mma.m16n8k16 .row.col (PTX ISA): g = lane >> 2, t = lane & 3;
-// A regs {(g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)},
-// B regs {(2t..2t+1, g), (2t+8.., g)}, C {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)}.
-__device__ __forceinline__ void mma_tile(float c[4], const __nv_bfloat16* A, int ars, int acs, const __nv_bfloat16* B,
-                                         int bks, int bns, int m0, int n0, int K)
-{
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const __nv_bfloat16* a0 = A + (m0 + g) * ars;
-    const __nv_bfloat16* a1 = A + (m0 + g + 8) * ars;
-    const __nv_bfloat16* bb = B + (n0 + g) * bns;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        const int ka = k0 + 2 * t, kb = k0 + 2 * t + 8;
-        uint32_t ra[4], rb[2];
-        ra[0] = pack2(a0[ka * acs], a0[(ka + 1) * acs]);
-        ra[1] = pack2(a1[ka * acs], a1[(ka + 1) * acs]);
-        ra[2] = pack2(a0[kb * acs], a0[(kb + 1) * acs]);
-        ra[3] = pack2(a1[kb * acs], a1[(kb + 1) * acs]);
-        rb[0] = pack2(bb[ka * bks], bb[(ka + 1) * bks]);
-        rb[1] = pack2(bb[kb * bks], bb[(kb + 1) * bks]);
-        asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-            "{%0,%1,%2,%3};\n"
-            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-            : "r"(ra[0]), "r"(ra[1]), "r"(ra[2]), "r"(ra[3]), "r"(rb[0]), "r"(rb[1]));
-    }
-}
-
 __device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
 __device__ __forceinline__ float silu(float z) { return z * sigm(z); }
 __device__ __forceinline__ float dsilu(float z)
@@ -73,34 +39,7 @@ __device__ __forceinline__ float dsilu(float z)
 constexpr int H = 128;        // hidden width
 constexpr int NIN = 16;       // padded input width (9 used)
 constexpr int NOUT = 8;       // padded output width (6 used)
-constexpr int CH = 64;        // samples per training chunk
 constexpr int NPARAM = NIN * H + H + H * H + H + H * NOUT + NOUT;
-
-struct MlpSmem {
-    __nv_bfloat16 W1[NIN * H], W2[H * H], W3[H * 16];  // W3 padded to 16 output columns (zero)
-    float b1[H], b2[H], b3[NOUT];
-};
-
-__device__ void load_weights(MlpSmem& S, const float* __restrict__ P)
-{
-    const float* W1 = P;
-    const float* b1 = W1 + NIN * H;
-    const float* W2 = b1 + H;
-    const float* b2 = W2 + H * H;
-    const float* W3 = b2 + H;
-    const float* b3 = W3 + H * NOUT;
-    for (int i = threadIdx.x; i < NIN * H; i += blockDim.x) S.W1[i] = __float2bfloat16_rn(W1[i]);
-    for (int i = threadIdx.x; i < H * H; i += blockDim.x) S.W2[i] = __float2bfloat16_rn(W2[i]);
-    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
-        const int r = i >> 4, c = i & 15;
-        S.W3[i] = __float2bfloat16_rn(c < NOUT ? W3[r * NOUT + c] : 0.0f);
-    }
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        S.b1[i] = b1[i];
-        S.b2[i] = b2[i];
-    }
-    if (threadIdx.x < NOUT) S.b3[threadIdx.x] = b3[threadIdx.x];
-}
 
 // features of an anchor: p at its cell centre / L, |p|/L, |p|^2/L^2, species one-hot, 1
 __device__ __forceinline__ void anchor_features(const ProposalArgs& A, int64_t a, float f[NIN])
@@ -189,17 +128,97 @@ __device__ void logq_grad(const float o[6], const float y[5], float& logq, float
     g[5] = ((1.0f / 32.0f) - G) / q * 0.9f * sa * (1.0f - sa);
 }
 
-struct TrainSmem {
-    MlpSmem w;
-    __nv_bfloat16 X[CH * NIN];
-    __nv_bfloat16 Z1[CH * H], H1[CH * H], Z2[CH * H], H2[CH * H];
-    __nv_bfloat16 dO[CH * 16], dZ2[CH * H], dZ1[CH * H];
-    float O[CH * NOUT];
-    float yv[CH * 5], wv[CH];
-    float db[H + H + NOUT];
+}  // namespace
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// instruction descriptor of tcgen05.mma .kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 =
+// 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// shared-memory matrix descriptor, no swizzle: start >> 4 (bits 0-13), leading-dimension byte offset
+// >> 4 (bits 16-29, here the K-direction core stride), stride-dimension byte offset >> 4 (bits 32-45, the
+// row-direction core stride), descriptor version 1 (bits 46-47), layout type 0 (no swizzle, bits 61-63)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ int op_off(int r, int k, int K)  // element offset of (r, k) in an R x K operand
+{
+    return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(dt), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void commit(uint64_t* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// waits for the mbarrier phase `parity` to complete; false after ~2^22 polls
+__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(mbar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void ld32(uint32_t taddr, float v[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int TM = 128;    // anchors per tile (the MMA's M)
+constexpr int TCOLS = 128; // tensor-memory columns held by a CTA
+
+struct InferSmem {
+    __nv_bfloat16 B1[H * NIN];   // W1^T: 128 x 16
+    __nv_bfloat16 B3[16 * H];    // W3^T: 16 x 128 (output rows 6..15 zero)
+    __nv_bfloat16 X[TM * NIN];   // 128 x 16
+    __nv_bfloat16 B2[H * H];     // W2^T: 128 x 128
+    __nv_bfloat16 H1[TM * H];
+    __nv_bfloat16 H2[TM * H];
+    float b1[H], b2[H], b3[16];
+    uint64_t mbar;
+    uint32_t taddr;
 };
 
-}  // namespace
+}  // namespace tc
 
 // One gradient evaluation over records [0, n): grad (FP32, NPARAM) += dL/dtheta
 // with L = -sum w log q / wsum, and loss_sum += L.  Each block walks chunks of
@@ -214,199 +233,285 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
-// Each block writes its own gradient and loss (part[block][NPARAM],
-// part_loss[block]); k_grad_reduce adds the blocks in block order, so the
-// result does not depend on which block finishes first.
-__global__ void __launch_bounds__(256, 1) k_mlp_grad(const float* __restrict__ params, const ProposalArgs A,
+// Training pass on the tensor cores (tcgen05), chunks of 128 records (the
+// MMA's M).  Weights stay in shared memory in their [in][out] orientation
+// (op_off(in, out, OUT)), activations as [record][unit]; a descriptor reads a
+// buffer either K-major (rows = the operand's M or N) or MN-major (rows = K):
+// no-swizzle core matrices, the K-direction stride as the leading byte
+// offset and the M/N-direction stride as the stride byte offset.  Per chunk:
+//   Z1 = X W1 + b1, H1 = silu(Z1); Z2 = H1 W2 + b2, H2; O = H2 W3 + b3;
+//   dO = -w dlogq/dO per record;  dW3 += H2^T dO;  dZ2 = (dO W3^T) silu'(Z2);
+//   dW2 += H1^T dZ2;  dZ1 = (dZ2 W2^T) silu'(Z1);  dW1^T += dZ1^T X,
+// with Z, H, dO and dZ rounded to BF16 where the CPU reference rounds, FP32
+// accumulation in tensor memory; the weight gradients accumulate there over
+// all of the block's chunks in a fixed order.  Each block then writes its own
+// gradient and loss (part[block][NPARAM], part_loss[block]); k_grad_reduce
+// adds the blocks in block order, so the result does not depend on which
+// block finishes first.  Waits are bounded (err counts timeouts).
+namespace tc {
+constexpr int RB = 128;          // records per chunk
+constexpr int TRAIN_COLS = 512;  // tensor memory: temp [0,128), O [128,144), dW2 [256,384), dW3 [384,400), dW1^T [400,416)
+constexpr uint32_t C_T = 0, C_O = 128, C_W2 = 256, C_W3 = 384, C_W1 = 400;
+
+struct TrainSmem {
+    __nv_bfloat16 W1[NIN * H];  // op_off(f, i, H)
+    __nv_bfloat16 W3[H * 16];   // op_off(i, j, 16), outputs 8..15 zero
+    __nv_bfloat16 X[RB * NIN];  // op_off(r, f, NIN)
+    __nv_bfloat16 dO[RB * 16];  // op_off(r, j, 16)
+    __nv_bfloat16 W2[H * H];    // op_off(i, n, H)
+    __nv_bfloat16 H1[RB * H], H2[RB * H], Z1[RB * H], Z2[RB * H];  // op_off(r, i, H); Z1, Z2 later hold dZ1, dZ2
+    float b1[H], b2[H], b3[16];
+    float yv[RB * 5], wv[RB];
+    float db[H + H + NOUT];
+    float wloss[4];
+    uint64_t mbar;
+    uint32_t taddr;
+};
+
+__host__ __device__ constexpr uint32_t idesc_major(int M, int N, int a_mn, int b_mn)
+{
+    return idesc_bf16(M, N) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
+}
+// K-slice kk (16 deep) of a buffer read K-major (rows = M or N, K columns)
+__device__ __forceinline__ uint64_t dk(uint32_t base, int K, int kk) { return sdesc(base + kk * 256, 128, (K / 8) * 128); }
+// K-slice kk of a buffer read MN-major (rows = K, C columns = M or N)
+__device__ __forceinline__ uint64_t dmn(uint32_t base, int C, int kk)
+{
+    return sdesc(base + kk * 2 * (C / 8) * 128, (C / 8) * 128, 128);
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(128, 1) k_mlp_grad(const float* __restrict__ params, const ProposalArgs A,
                                                      const ProposalRecord* __restrict__ rec, int64_t n, float inv_wsum,
                                                      float* __restrict__ part, float* __restrict__ part_loss,
-                                                     int64_t ntot, uint64_t key)
+                                                     int64_t ntot, uint64_t key, int* err)
 {
+    using namespace tc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    load_weights(S.w, params);
-    for (int i = threadIdx.x; i < 2 * H + NOUT; i += blockDim.x) S.db[i] = 0.0f;
-    // register tiles of the weight gradients owned by this warp
-    float gW2[16][4], gW1[2][4], gW3[4];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) gW2[i][0] = gW2[i][1] = gW2[i][2] = gW2[i][3] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) gW1[i][0] = gW1[i][1] = gW1[i][2] = gW1[i][3] = 0.0f;
-    gW3[0] = gW3[1] = gW3[2] = gW3[3] = 0.0f;
-    float loss_blk = 0.0f;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const float* W1 = params;
+        const float* b1 = W1 + NIN * H;
+        const float* W2 = b1 + H;
+        const float* b2 = W2 + H * H;
+        const float* W3 = b2 + H;
+        const float* b3 = W3 + H * NOUT;
+        for (int i = tid; i < NIN * H; i += blockDim.x) S.W1[op_off(i / H, i % H, H)] = __float2bfloat16_rn(W1[i]);
+        for (int i = tid; i < H * H; i += blockDim.x) S.W2[op_off(i / H, i % H, H)] = __float2bfloat16_rn(W2[i]);
+        for (int i = tid; i < H * 16; i += blockDim.x) {
+            const int r = i / 16, c = i % 16;
+            S.W3[op_off(r, c, 16)] = __float2bfloat16_rn(c < NOUT ? W3[r * NOUT + c] : 0.0f);
+        }
+        for (int i = tid; i < H; i += blockDim.x) {
+            S.b1[i] = b1[i];
+            S.b2[i] = b2[i];
+        }
+        if (tid < 16) S.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
+        for (int i = tid; i < 2 * H + NOUT; i += blockDim.x) S.db[i] = 0.0f;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&S.taddr)),
+                     "r"(TRAIN_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
     __syncthreads();
-    const int64_t nchunks = (n + CH - 1) / CH;
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        // ---- inputs ----
-        if (threadIdx.x < CH) {
-            const int64_t r = c * CH + threadIdx.x;
+    fence_after();
+    const uint32_t tmem = S.taddr, lq = (uint32_t)(warp * 32) << 16;
+    const uint32_t aX = smem_u32(S.X), adO = smem_u32(S.dO), aH1 = smem_u32(S.H1), aH2 = smem_u32(S.H2);
+    const uint32_t aZ1 = smem_u32(S.Z1), aZ2 = smem_u32(S.Z2);
+    const uint32_t aW1 = smem_u32(S.W1), aW2 = smem_u32(S.W2), aW3 = smem_u32(S.W3);
+    uint32_t phase = 0;
+    bool ok = true;
+    float loss_me = 0.0f;
+    auto wait_all = [&]() -> bool {
+        const bool done = wait_parity(&S.mbar, phase);
+        phase ^= 1;
+        fence_after();
+        return __syncthreads_and(done) != 0;
+    };
+    auto sync_operands = [&]() {  // activations written by the threads become MMA operands; TMEM reads done
+        fence_before();
+        fence_async_smem();
+        __syncthreads();
+    };
+    const int64_t nchunks = (n + RB - 1) / RB;
+    bool first = true;
+    for (int64_t c = blockIdx.x; c < nchunks && ok; c += gridDim.x, first = false) {
+        // ---- inputs: one record per thread ----
+        {
+            const int64_t r = c * RB + tid;
             float f[NIN];
             if (r < n) {
                 const int64_t ri = ntot > 0 ? (int64_t)(splitmix64(key + (uint64_t)r) % (uint64_t)ntot) : r;
                 const ProposalRecord R = rec[ri];
                 anchor_features(A, R.a, f);
-                for (int i = 0; i < 5; ++i) S.yv[threadIdx.x * 5 + i] = R.y[i];
-                S.wv[threadIdx.x] = R.w * inv_wsum;
+                for (int i = 0; i < 5; ++i) S.yv[tid * 5 + i] = R.y[i];
+                S.wv[tid] = R.w * inv_wsum;
             } else {
                 for (int i = 0; i < NIN; ++i) f[i] = 0.0f;
-                for (int i = 0; i < 5; ++i) S.yv[threadIdx.x * 5 + i] = 0.0f;
-                S.wv[threadIdx.x] = 0.0f;
+                for (int i = 0; i < 5; ++i) S.yv[tid * 5 + i] = 0.0f;
+                S.wv[tid] = 0.0f;
             }
-            for (int i = 0; i < NIN; ++i) S.X[threadIdx.x * NIN + i] = __float2bfloat16_rn(f[i]);
+            for (int i = 0; i < NIN; ++i) S.X[op_off(tid, i, NIN)] = __float2bfloat16_rn(f[i]);
         }
-        __syncthreads();
-        // ---- Z1 = X W1 + b1 (64 x 128): 32 tiles of 16x8 per ... 4 m x 16 n = 64 tiles, 8 per warp ----
-        for (int tt = warp; tt < 64; tt += 8) {
-            const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, S.X, NIN, 1, S.w.W1, H, 1, m0, n0, NIN);
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                const __nv_bfloat16 z = __float2bfloat16_rn(acc[e] + S.w.b1[nn]);
-                S.Z1[m * H + nn] = z;
-                S.H1[m * H + nn] = __float2bfloat16_rn(silu(__bfloat162float(z)));
+        sync_operands();
+        // ---- hidden layers ----
+        for (int l = 0; l < 2 && ok; ++l) {
+            if (tid == 0) {
+                fence_after();
+                if (l == 0) {
+                    mma(tmem + C_T, dk(aX, NIN, 0), dmn(aW1, H, 0), idesc_major(RB, H, 0, 1), 0);
+                } else {
+                    for (int kk = 0; kk < H / 16; ++kk)
+                        mma(tmem + C_T, dk(aH1, H, kk), dmn(aW2, H, kk), idesc_major(RB, H, 0, 1), kk > 0);
+                }
+                commit(&S.mbar);
             }
-        }
-        __syncthreads();
-        // ---- Z2 = H1 W2 + b2 ----
-        for (int tt = warp; tt < 64; tt += 8) {
-            const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, S.H1, H, 1, S.w.W2, H, 1, m0, n0, H);
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                const __nv_bfloat16 z = __float2bfloat16_rn(acc[e] + S.w.b2[nn]);
-                S.Z2[m * H + nn] = z;
-                S.H2[m * H + nn] = __float2bfloat16_rn(silu(__bfloat162float(z)));
+            if (!(ok = wait_all())) break;
+            __nv_bfloat16* Zb = l == 0 ? S.Z1 : S.Z2;
+            __nv_bfloat16* Hb = l == 0 ? S.H1 : S.H2;
+            const float* bias = l == 0 ? S.b1 : S.b2;
+            for (int c0 = 0; c0 < H; c0 += 32) {
+                float v[32];
+                ld32(tmem + lq + C_T + c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const __nv_bfloat16 z = __float2bfloat16_rn(v[i] + bias[c0 + i]);
+                    Zb[op_off(tid, c0 + i, H)] = z;
+                    Hb[op_off(tid, c0 + i, H)] = __float2bfloat16_rn(silu(__bfloat162float(z)));
+                }
             }
+            sync_operands();
         }
-        __syncthreads();
-        // ---- O = H2 W3 + b3 (64 x 8): 4 tiles ----
-        if (warp < 4) {
-            const int m0 = warp * 16;
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, S.H2, H, 1, S.w.W3, 16, 1, m0, 0, H);
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + g + (e >> 1) * 8, nn = 2 * t + (e & 1);
-                S.O[m * NOUT + nn] = acc[e] + S.w.b3[nn];
-            }
+        if (!ok) break;
+        // ---- outputs, loss and dO (one record per thread) ----
+        if (tid == 0) {
+            fence_after();
+            for (int kk = 0; kk < H / 16; ++kk)
+                mma(tmem + C_O, dk(aH2, H, kk), dmn(aW3, 16, kk), idesc_major(RB, 16, 0, 1), kk > 0);
+            commit(&S.mbar);
         }
-        __syncthreads();
-        // ---- loss and dL/dO per record ----
-        if (threadIdx.x < CH) {
-            const int r = threadIdx.x;
-            const float w = S.wv[r];
-            float gq[6] = {0, 0, 0, 0, 0, 0}, lq = 0.0f;
+        if (!(ok = wait_all())) break;
+        {
+            float v[32];
+            ld32(tmem + lq + C_O, v);
+            float o[NOUT];
+            for (int i = 0; i < NOUT; ++i) o[i] = v[i] + S.b3[i];
+            const float w = S.wv[tid];
+            float gq[6] = {0, 0, 0, 0, 0, 0}, lg = 0.0f;
             if (w != 0.0f) {
-                logq_grad(&S.O[r * NOUT], &S.yv[r * 5], lq, gq);
-                loss_blk += -w * lq;
+                logq_grad(o, &S.yv[tid * 5], lg, gq);
+                loss_me += -w * lg;
             }
-            for (int i = 0; i < 16; ++i) S.dO[r * 16 + i] = __float2bfloat16_rn(i < 6 ? -w * gq[i] : 0.0f);
+            for (int j = 0; j < 16; ++j) S.dO[op_off(tid, j, 16)] = __float2bfloat16_rn(j < 6 ? -w * gq[j] : 0.0f);
         }
-        __syncthreads();
-        // ---- dW3 += H2^T dO (128 x 8): 8 row tiles, one per warp ----
-        mma_tile(gW3, S.H2, 1, H, S.dO, 16, 1, warp * 16, 0, CH);
-        // ---- dZ2 = (dO W3^T) * silu'(Z2) (64 x 128), K = 16 ----
-        for (int tt = warp; tt < 64; tt += 8) {
-            const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, S.dO, 16, 1, S.w.W3, 1, 16, m0, n0, 16);
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                S.dZ2[m * H + nn] = __float2bfloat16_rn(acc[e] * dsilu(__bfloat162float(S.Z2[m * H + nn])));
-            }
+        sync_operands();
+        // ---- dW3 += H2^T dO;  T = dO W3^T ----
+        if (tid == 0) {
+            fence_after();
+            for (int kk = 0; kk < RB / 16; ++kk)
+                mma(tmem + C_W3, dmn(aH2, H, kk), dmn(adO, 16, kk), idesc_major(H, 16, 1, 1), !(first && kk == 0));
+            mma(tmem + C_T, dk(adO, 16, 0), dk(aW3, 16, 0), idesc_major(RB, H, 0, 0), 0);
+            commit(&S.mbar);
         }
-        __syncthreads();
-        // ---- dW2 += H1^T dZ2 (128 x 128): 128 tiles, 16 per warp ----
+        if (!(ok = wait_all())) break;
+        for (int c0 = 0; c0 < H; c0 += 32) {  // dZ2 = T silu'(Z2), in place of Z2
+            float v[32];
+            ld32(tmem + lq + C_T + c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int tt = warp * 16 + i;
-            const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-            mma_tile(gW2[i], S.H1, 1, H, S.dZ2, H, 1, m0, n0, CH);
-        }
-        // ---- dZ1 = (dZ2 W2^T) * silu'(Z1), K = 128 ----
-        for (int tt = warp; tt < 64; tt += 8) {
-            const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, S.dZ2, H, 1, S.w.W2, 1, H, m0, n0, H);
-            for (int e = 0; e < 4; ++e) {
-                const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                S.dZ1[m * H + nn] = __float2bfloat16_rn(acc[e] * dsilu(__bfloat162float(S.Z1[m * H + nn])));
+            for (int i = 0; i < 32; ++i) {
+                const int o2 = op_off(tid, c0 + i, H);
+                S.Z2[o2] = __float2bfloat16_rn(v[i] * dsilu(__bfloat162float(S.Z2[o2])));
             }
         }
-        __syncthreads();
-        // ---- dW1 += X^T dZ1 (16 x 128): 16 tiles, 2 per warp ----
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int n0 = (warp * 2 + i) * 8;
-            mma_tile(gW1[i], S.X, 1, NIN, S.dZ1, H, 1, 0, n0, CH);
+        sync_operands();
+        // ---- dW2 += H1^T dZ2;  T = dZ2 W2^T ----
+        if (tid == 0) {
+            fence_after();
+            for (int kk = 0; kk < RB / 16; ++kk)
+                mma(tmem + C_W2, dmn(aH1, H, kk), dmn(aZ2, H, kk), idesc_major(H, H, 1, 1), !(first && kk == 0));
+            for (int kk = 0; kk < H / 16; ++kk)
+                mma(tmem + C_T, dk(aZ2, H, kk), dk(aW2, H, kk), idesc_major(RB, H, 0, 0), kk > 0);
+            commit(&S.mbar);
         }
-        // ---- bias gradients: column sums of dZ1, dZ2, dO ----
-        for (int col = threadIdx.x; col < 2 * H + NOUT; col += blockDim.x) {
+        if (!(ok = wait_all())) break;
+        for (int c0 = 0; c0 < H; c0 += 32) {  // dZ1 = T silu'(Z1), in place of Z1
+            float v[32];
+            ld32(tmem + lq + C_T + c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const int o1 = op_off(tid, c0 + i, H);
+                S.Z1[o1] = __float2bfloat16_rn(v[i] * dsilu(__bfloat162float(S.Z1[o1])));
+            }
+        }
+        sync_operands();
+        // ---- dW1^T += dZ1^T X; meanwhile the bias gradients (column sums of dZ1, dZ2, dO) ----
+        if (tid == 0) {
+            fence_after();
+            for (int kk = 0; kk < RB / 16; ++kk)
+                mma(tmem + C_W1, dmn(aZ1, H, kk), dmn(aX, NIN, kk), idesc_major(H, 16, 1, 1), !(first && kk == 0));
+            commit(&S.mbar);
+        }
+        for (int col = tid; col < 2 * H + NOUT; col += blockDim.x) {
             float s = 0.0f;
             if (col < H) {
-                for (int m = 0; m < CH; ++m) s += __bfloat162float(S.dZ1[m * H + col]);
+                for (int r = 0; r < RB; ++r) s += __bfloat162float(S.Z1[op_off(r, col, H)]);
             } else if (col < 2 * H) {
-                for (int m = 0; m < CH; ++m) s += __bfloat162float(S.dZ2[m * H + col - H]);
+                for (int r = 0; r < RB; ++r) s += __bfloat162float(S.Z2[op_off(r, col - H, H)]);
             } else {
-                for (int m = 0; m < CH; ++m) s += __bfloat162float(S.dO[m * 16 + col - 2 * H]);
+                for (int r = 0; r < RB; ++r) s += __bfloat162float(S.dO[op_off(r, col - 2 * H, 16)]);
             }
             S.db[col] += s;
         }
-        __syncthreads();
+        if (!(ok = wait_all())) break;  // X and Z1 may be overwritten by the next chunk
     }
     // ---- this block's gradient, every parameter written once ----
-    float* gW1g = part + (int64_t)blockIdx.x * NPARAM;
-    float* gb1g = gW1g + NIN * H;
-    float* gW2g = gb1g + H;
-    float* gb2g = gW2g + H * H;
-    float* gW3g = gb2g + H;
-    float* gb3g = gW3g + H * NOUT;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-        const int tt = warp * 16 + i;
-        const int m0 = (tt >> 4) * 16, n0 = (tt & 15) * 8;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int m = m0 + g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-            gW2g[m * H + nn] = gW2[i][e];
+    float* gW1 = part + (int64_t)blockIdx.x * NPARAM;
+    float* gb1 = gW1 + NIN * H;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + H * NOUT;
+    if (ok) {
+        const int i = tid;  // tensor-memory lane = hidden unit i of the weight-gradient accumulators
+        for (int c0 = 0; c0 < H; c0 += 32) {
+            float v[32];
+            ld32(tmem + lq + C_W2 + c0, v);
+            for (int k = 0; k < 32; ++k) gW2[i * H + c0 + k] = v[k];
         }
+        float v[32];
+        ld32(tmem + lq + C_W3, v);  // columns 384..415: dW3 (16), then dW1^T (16)
+        for (int j = 0; j < NOUT; ++j) gW3[i * NOUT + j] = v[j];
+        for (int f = 0; f < NIN; ++f) gW1[f * H + i] = v[16 + f];
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int n0 = (warp * 2 + i) * 8;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int m = g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-            gW1g[m * H + nn] = gW1[i][e];
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int m = warp * 16 + g + (e >> 1) * 8, nn = 2 * t + (e & 1);
-        gW3g[m * NOUT + nn] = gW3[e];
-    }
-    for (int col = threadIdx.x; col < 2 * H + NOUT; col += blockDim.x) {
+    __syncthreads();
+    for (int col = tid; col < 2 * H + NOUT; col += blockDim.x) {
         const float s = S.db[col];
         if (col < H)
-            gb1g[col] = s;
+            gb1[col] = s;
         else if (col < 2 * H)
-            gb2g[col - H] = s;
+            gb2[col - H] = s;
         else
-            gb3g[col - 2 * H] = s;
+            gb3[col - 2 * H] = s;
     }
-    // loss: the two warps of record threads, in warp order
-    loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 16);
-    loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 8);
-    loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 4);
-    loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 2);
-    loss_blk += __shfl_xor_sync(0xffffffffu, loss_blk, 1);
-    __shared__ float s_loss[2];
-    if (lane == 0 && warp < 2) s_loss[warp] = loss_blk;
+    // loss: warps in order
+    for (int o = 16; o > 0; o >>= 1) loss_me += __shfl_xor_sync(0xffffffffu, loss_me, o);
+    if (lane == 0) S.wloss[warp] = loss_me;
     __syncthreads();
-    if (threadIdx.x == 0) part_loss[blockIdx.x] = s_loss[0] + s_loss[1];
+    if (tid == 0) part_loss[blockIdx.x] = ((S.wloss[0] + S.wloss[1]) + S.wloss[2]) + S.wloss[3];
+    if (!ok && tid == 0) atomicAdd(err, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TRAIN_COLS) : "memory");
 }
 
 // grad[i] += sum over blocks b = 0, 1, ... of part[b][i]; loss = sum of the
@@ -442,72 +547,140 @@ __global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __re
     g[i] = 0.0f;
 }
 
-// Per-anchor proposal parameters (8 floats: mu3 x3, sigma3, sigma1, alpha, 0, 0)
-// for anchors [0, nanchor): each warp runs 16 anchors through the network.
-__global__ void __launch_bounds__(256) k_mlp_infer(const float* __restrict__ params, const ProposalArgs A,
-                                                   int64_t nanchor, float* __restrict__ out)
+// ---------------------------------------------------------------------------
+// Per-anchor inference on the 5th-generation tensor cores (tcgen05).  A CTA of
+// four warps takes tiles of 128 anchors: the activations of a tile (A, 128
+// rows) and the transposed weights (B) sit in shared memory in the
+// no-swizzle K-major layout of 8-row x 16-byte core matrices (element (r, k)
+// of an R x K operand at byte ((r/8)(K/8) + k/8) 128 + (r%8) 16 + (k%8) 2, so
+// core matrices adjacent along K are 128 bytes apart and along the rows
+// (K/8) 128 bytes); one thread issues tcgen05.mma (M = 128, K = 16 per
+// instruction, BF16 operands, FP32 accumulation in tensor memory) and
+// commits to an mbarrier; each warp then reads its 32 rows of the
+// accumulator (tcgen05.ld, lane quarter = warp) for the epilogue: bias, BF16
+// rounding of Z, SiLU in FP32, BF16 activation written back as the next
+// layer's A.  Every wait on the mbarrier is bounded: on a timeout the CTA
+// records it in err and stops issuing work, then releases its tensor memory.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_mlp_infer(const float* __restrict__ params, const ProposalArgs A,
+                                                   int64_t nanchor, float* __restrict__ out, int* err)
 {
+    using namespace tc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MlpSmem& W = *reinterpret_cast<MlpSmem*>(smem_raw);
-    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(smem_raw + sizeof(MlpSmem));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    __nv_bfloat16* X = act + warp * (16 * NIN + 2 * 16 * H);
-    __nv_bfloat16* H1 = X + 16 * NIN;
-    __nv_bfloat16* H2 = H1 + 16 * H;
-    load_weights(W, params);
+    InferSmem& S = *reinterpret_cast<InferSmem*>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights, transposed into the B operands (K-major rows = output units)
+    {
+        const float* W1 = params;
+        const float* b1 = W1 + NIN * H;
+        const float* W2 = b1 + H;
+        const float* b2 = W2 + H * H;
+        const float* W3 = b2 + H;
+        const float* b3 = W3 + H * NOUT;
+        for (int i = tid; i < H * NIN; i += blockDim.x) {
+            const int n = i / NIN, k = i % NIN;
+            S.B1[op_off(n, k, NIN)] = __float2bfloat16_rn(W1[k * H + n]);
+        }
+        for (int i = tid; i < H * H; i += blockDim.x) {
+            const int n = i / H, k = i % H;
+            S.B2[op_off(n, k, H)] = __float2bfloat16_rn(W2[k * H + n]);
+        }
+        for (int i = tid; i < 16 * H; i += blockDim.x) {
+            const int n = i / H, k = i % H;
+            S.B3[op_off(n, k, H)] = __float2bfloat16_rn(n < NOUT ? W3[k * NOUT + n] : 0.0f);
+        }
+        for (int i = tid; i < H; i += blockDim.x) {
+            S.b1[i] = b1[i];
+            S.b2[i] = b2[i];
+        }
+        if (tid < 16) S.b3[tid] = tid < NOUT ? b3[tid] : 0.0f;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&S.taddr)),
+                     "r"(TCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
     __syncthreads();
-    const int64_t ngroups = (nanchor + 15) / 16;
-    for (int64_t grp = (int64_t)blockIdx.x * 8 + warp; grp < ngroups; grp += (int64_t)gridDim.x * 8) {
-        if (lane < 16) {
-            const int64_t a = grp * 16 + lane;
+    fence_after();
+    const uint32_t tmem = S.taddr;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's lane quarter
+    const uint32_t aX = smem_u32(S.X), aH1 = smem_u32(S.H1), aH2 = smem_u32(S.H2);
+    const uint32_t aB1 = smem_u32(S.B1), aB2 = smem_u32(S.B2), aB3 = smem_u32(S.B3);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (nanchor + TM - 1) / TM;
+    // one layer: MMAs over K (K/16 instructions), then all threads wait for the accumulator
+    auto layer = [&](uint32_t a_base, uint32_t b_base, int K, int N) -> bool {
+        if (tid == 0) {
+            fence_after();
+            for (int kk = 0; kk < K / 16; ++kk)
+                mma(tmem, sdesc(a_base + kk * 256, 128, (K / 8) * 128), sdesc(b_base + kk * 256, 128, (K / 8) * 128),
+                    idesc_bf16(TM, N), kk > 0);
+            commit(&S.mbar);
+        }
+        const bool done = wait_parity(&S.mbar, phase);
+        phase ^= 1;
+        fence_after();
+        return __syncthreads_and(done) != 0;  // the same answer in every thread
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const int64_t a = tile * TM + tid;
+        {
             float f[NIN];
             if (a < nanchor)
                 anchor_features(A, a, f);
             else
                 for (int i = 0; i < NIN; ++i) f[i] = 0.0f;
-            for (int i = 0; i < NIN; ++i) X[lane * NIN + i] = __float2bfloat16_rn(f[i]);
+            for (int i = 0; i < NIN; ++i) S.X[op_off(tid, i, NIN)] = __float2bfloat16_rn(f[i]);
         }
-        __syncwarp();
-        for (int n0 = 0; n0 < H; n0 += 8) {
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, X, NIN, 1, W.W1, H, 1, 0, n0, NIN);
-            for (int e = 0; e < 4; ++e) {
-                const int m = g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                const __nv_bfloat16 z = __float2bfloat16_rn(acc[e] + W.b1[nn]);
-                H1[m * H + nn] = __float2bfloat16_rn(silu(__bfloat162float(z)));
+        fence_async_smem();
+        __syncthreads();
+        // hidden layers: Z = bf16(acc + b), activation bf16(silu(Z)) as the next A operand
+        for (int l = 0; l < 2 && ok; ++l) {
+            ok = layer(l == 0 ? aX : aH1, l == 0 ? aB1 : aB2, l == 0 ? NIN : H, H);
+            if (!ok) break;
+            __nv_bfloat16* act = l == 0 ? S.H1 : S.H2;
+            const float* bias = l == 0 ? S.b1 : S.b2;
+            for (int c0 = 0; c0 < H; c0 += 32) {
+                float v[32];
+                ld32(tmem + lane_base + c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const __nv_bfloat16 z = __float2bfloat16_rn(v[i] + bias[c0 + i]);
+                    act[op_off(tid, c0 + i, H)] = __float2bfloat16_rn(silu(__bfloat162float(z)));
+                }
             }
+            fence_before();
+            fence_async_smem();
+            __syncthreads();
         }
-        __syncwarp();
-        for (int n0 = 0; n0 < H; n0 += 8) {
-            float acc[4] = {0, 0, 0, 0};
-            mma_tile(acc, H1, H, 1, W.W2, H, 1, 0, n0, H);
-            for (int e = 0; e < 4; ++e) {
-                const int m = g + (e >> 1) * 8, nn = n0 + 2 * t + (e & 1);
-                const __nv_bfloat16 z = __float2bfloat16_rn(acc[e] + W.b2[nn]);
-                H2[m * H + nn] = __float2bfloat16_rn(silu(__bfloat162float(z)));
-            }
+        if (!ok) break;
+        ok = layer(aH2, aB3, H, 16);
+        if (!ok) break;
+        float v[32];
+        ld32(tmem + lane_base, v);  // columns 0..31: the 16 outputs (and whatever follows)
+        if (a < nanchor) {
+            float o[NOUT], prm[8];
+            for (int i = 0; i < NOUT; ++i) o[i] = v[i] + S.b3[i];
+            head(o, prm);
+            for (int i = 0; i < 8; ++i) out[a * 8 + i] = prm[i];
         }
-        __syncwarp();
-        float acc[4] = {0, 0, 0, 0};
-        mma_tile(acc, H2, H, 1, W.W3, 16, 1, 0, 0, H);
-        // gather the 6 outputs of each anchor row through shared memory (reuse X)
-        float* o = reinterpret_cast<float*>(X);
-        for (int e = 0; e < 4; ++e) {
-            const int m = g + (e >> 1) * 8, nn = 2 * t + (e & 1);
-            o[m * NOUT + nn] = acc[e] + W.b3[nn];
-        }
-        __syncwarp();
-        if (lane < 16) {
-            const int64_t a = grp * 16 + lane;
-            if (a < nanchor) {
-                float prm[8];
-                head(&o[lane * NOUT], prm);
-                for (int i = 0; i < 8; ++i) out[a * 8 + i] = prm[i];
-            }
-        }
-        __syncwarp();
+        fence_before();
+        __syncthreads();
     }
+    if (!ok && tid == 0) atomicAdd(err, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS) : "memory");
 }
 
 // Sum of the record weights in a fixed order: per warp of a fixed grid, then
@@ -583,18 +756,22 @@ cudaError_t launch_sort_records(ProposalRecord* rec, int64_t n, cudaStream_t s)
 int mlp_nparam() { return NPARAM; }
 
 cudaError_t launch_mlp_grad(const float* params, const ProposalArgs& A, const ProposalRecord* rec, int64_t n,
-                            float inv_wsum, float* grad, float* loss, int grid, float* part, float* part_loss,
+                            float inv_wsum, float* grad, float* loss, int grid, float* part, float* part_loss, int* err,
                             cudaStream_t s, int64_t ntot, uint64_t key)
 {
-    const size_t smem = sizeof(TrainSmem);
+    // room beyond the buffers: a descriptor read of the last activation buffer stays inside the
+    // allocation for either assignment of the two core-matrix strides
+    const size_t smem = sizeof(tc::TrainSmem) > 212 * 1024 ? sizeof(tc::TrainSmem) : 212 * 1024;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_mlp_grad<<<grid, 256, smem, s>>>(params, A, rec, n, inv_wsum, part, part_loss, ntot, key);
-    k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(part, part_loss, grid, grad, loss);
+    const int64_t nch = (n + tc::RB - 1) / tc::RB;
+    const int g = (int)(nch < grid ? nch : grid);
+    k_mlp_grad<<<g > 0 ? g : 1, 128, smem, s>>>(params, A, rec, n, inv_wsum, part, part_loss, ntot, key, err);
+    k_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(part, part_loss, g > 0 ? g : 1, grad, loss);
     return cudaGetLastError();
 }
 
@@ -607,16 +784,18 @@ cudaError_t launch_adam(float* p, float* g, float* m, float* v, int n, float lr,
 }
 
 cudaError_t launch_mlp_infer(const float* params, const ProposalArgs& A, int64_t nanchor, float* out, int grid,
-                             cudaStream_t s)
+                             int* err, cudaStream_t s)
 {
-    const size_t smem = sizeof(MlpSmem) + 8 * (16 * NIN + 2 * 16 * H) * sizeof(__nv_bfloat16);
+    const size_t smem = sizeof(tc::InferSmem) + 128;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_mlp_infer<<<grid, 256, smem, s>>>(params, A, nanchor, out);
+    const int64_t ntiles = (nanchor + tc::TM - 1) / tc::TM;
+    const int g = (int)(ntiles < grid ? ntiles : grid);
+    k_mlp_infer<<<g > 0 ? g : 1, 128, smem, s>>>(params, A, nanchor, out, err);
     return cudaGetLastError();
 }
 
