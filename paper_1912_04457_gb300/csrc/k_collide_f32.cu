@@ -78,20 +78,21 @@ __device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)
 // Bin of a solved coordinate, clamped to [0, n).  floor(t) for 0 <= t < 2^23
 // is read from the mantissa of t + 2^23 added with rounding down (no
 // float-to-int conversion instruction; those issue on the FP64 pipe here).
+// t is clamped to [0, n - 1/2] first (a NaN to 0), so floor(t) <= n - 1.
 __device__ __forceinline__ int binf(float k, float L, float inv_dp, int n)
 {
     const float nf = __uint_as_float(0x4B000000u | (unsigned)n) - 8388608.0f;  // (float)n exactly, n < 2^23
     const float t = fminf(fmaxf((k + L) * inv_dp, 0.0f), nf - 0.5f);
-    const int j = __float_as_int(__fadd_rd(t, 8388608.0f)) - 0x4B000000;
-    return j >= n ? n - 1 : j;
+    return __float_as_int(__fadd_rd(t, 8388608.0f)) - 0x4B000000;
 }
 
 // Bin of a sampled coordinate k = -L + 2L u, u = ((x >> 9) + 1/2) 2^-23:
 // floor(u n) = ((2 (x >> 9) + 1) n) >> 24 exactly (u n is never within 2^-24
-// of an integer, so the FP64 definition floor((k + L)/dp) gives the same bin).
+// of an integer, so the FP64 definition floor((k + L)/dp) gives the same bin),
+// evaluated as the high word of ((x >> 9) 2^9 + 2^8) n (n < 2^23).
 __device__ __forceinline__ int bin_word(uint32_t x, int n)
 {
-    return (int)((((x >> 9) * 2u + 1u) * (uint32_t)n) >> 24);
+    return (int)__umulhi((x & 0xFFFFFE00u) | 0x100u, (uint32_t)n);
 }
 
 // A solved coordinate within nu bin widths of a bin (or box) edge: FP32
@@ -319,9 +320,13 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
 
     // One loop with a single site per phase, so the code stays small enough
     // for the instruction cache.  In order of priority: evaluate 32 pending
-    // roots (or all of them during a flush); solve the next term of the
-    // running batch of <= 32 live samples; start a batch; draw the next chunk
-    // of 32 samples into the live-sample buffer.
+    // roots (or all of them during a flush); solve the next kinematic group
+    // of the running batch of <= 32 live samples; otherwise draw the next
+    // chunk of 32 samples into the live-sample buffer and, once 32 live
+    // samples are buffered (or the unit's chunks are drawn), start a batch
+    // and solve its first group in the same pass: each pass through the loop
+    // costs issue slots of its own (the dispatch and the register moves at
+    // its joins), so the common path draw -> batch -> group takes one pass.
     int bstart = 0, bcnt = 0, ti = -1;  // running batch: first sequence number, size, next term (-1: none)
     bool flush = false, rec_due = false;
     float bEp = 0.0f, bPz = 0.0f, ba2m = 0.0f, bb2m = 0.0f, bkk3 = 0.0f;
@@ -333,117 +338,143 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             continue;
         }
         flush = false;
-        if (ti >= 0 && ti < nt) {
-            // ---- phase A: the kinematic group opened by term ti, for this lane's
-            // live sample.  Its terms (equal leg masses) share E3, D, kappa, H, the
-            // roots and the re-evaluation decision; each valid root goes to the
-            // ring once, tagged with the group's terms. ----
-            const int seq = bstart + lane;
-            const int gn = GROUPS ? S.tgn[ti] : 1;  // without GROUPS every group has one term
-            const bool act = lane < bcnt;
-            const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
-            const float4 tmv = S.tm[ti];
-            const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
-            const float E3 = sqrtf(bkk3 + mc2);
-            const float E = bEp + E3;
-            const float Pz = bPz;
-            const float a2 = ba2m + ma2;
-            const float b2 = bb2m + mb2;
-            const float D = E * E - Pz * Pz;
-            const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
-            const float H = kap * kap - a2 * D;
-            // straight-line form (no divergent branches): every lane evaluates the
-            // roots, and the flags select; float-float re-evaluation when the term is
-            // ill-conditioned (|H| < tau kappa^2) or a solved coordinate sits on an edge
-            const bool ok = act & (D > 0.0f);
-            const bool hp = ok & (H > 0.0f);
-            bool defer = ok & may_defer & (fabsf(H) < P.tau * (kap * kap));
-            const float sqH = sqrtf(H);
-            const float kp = kap * Pz;
-            const float sq = E * sqH;
-            const float Q = kp >= 0.0f ? kp + sq : kp - sq;
-            const bool qv = hp & (Q != 0.0f);
-            const float z0 = Q / D;
-            const float z1 = (E * E * a2 - kap * kap) / Q;
-            const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
-            const bool e0 = qv & (w0 > 0.0f) & (w0 < EE), e1v = qv & (w1 > 0.0f) & (w1 < EE);
-            const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
-            const bool edge = (marg_xy & (e0 | e1v))
-                              | (e0 & (near_edge(z0, L, inv_dp2, nu) | near_edge(Pz - z0, L, inv_dp2, nu)))
-                              | (e1v & (near_edge(z1, L, inv_dp2, nu) | near_edge(Pz - z1, L, inv_dp2, nu)));
-            defer = defer | (may_defer & edge);
-            bool v0 = k2xy_in & e0 & in_box(z0, L) & in_box(Pz - z0, L);
-            bool v1 = k2xy_in & e1v & in_box(z1, L) & in_box(Pz - z1, L);
-            int t0 = ti, tn = gn;  // terms whose roots phase B evaluates
-            if (defer) {  // queued for re-evaluation; when the queue is full the FP32 roots stand
-                const int qs = atomicAdd(dq.s_count, gn);
-                const int nq = min(gn, max(0, dq.cap - qs));
-                for (int k = 0; k < nq; ++k)
-                    dq.seg[qs + k] = box_tag | ((unsigned long long)a << 24)
-                                     | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)(ti + k);
-                if (nq < gn) red_add(&P.flags[3], gn - nq);
-                t0 = ti + nq;
-                tn = gn - nq;
-                if (tn == 0) v0 = v1 = false;
-            }
-            // append the valid roots to the ring
-            const unsigned tag = (unsigned)seq | ((unsigned)t0 << 24) | ((unsigned)(tn - 1) << 28);
-            const unsigned b0 = __ballot_sync(0xffffffffu, v0);
-            const unsigned b1 = __ballot_sync(0xffffffffu, v1);
-            const int n0 = __popc(b0);
-            if (v0) {
-                const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
-                S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
-            }
-            if (v1) {
-                const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
-                S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
-            }
-            tail += n0 + __popc(b1);
-            ti += gn;
-            __syncwarp();
-            continue;
-        }
-        if (ti == nt) {  // batch done; record mode first finishes its roots, then writes records
-            cons = bstart + bcnt;
-            ti = -1;
-            if (MODE == M_RECORD) {
-                flush = true;
-                rec_due = true;
-            }
-            continue;
-        }
-        if (MODE == M_RECORD && rec_due) {
-            // one record per sample with at least one accepted root (a zero
-            // weight teaches nothing); the sample's coordinates are drawn again
-            rec_due = false;
-            if (unit % P.rec_stride == 0) {
-                const int sb = (bstart + lane) & (SBUF - 1);
-                const bool keep = lane < bcnt && S.wfac[sb] > 0.0f;
-                const unsigned keep_mask = __ballot_sync(0xffffffffu, keep);
-                unsigned long long base = 0;
-                if (lane == 0 && keep_mask) base = atomicAdd(P.rec_count, (unsigned long long)__popc(keep_mask));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                const unsigned pos = __popc(keep_mask & lt_mask);
-                if (keep && (long long)(base + pos) < P.rec_cap) {
-                    const int smp = bmeta & 0xFFFFFF;
-                    const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
-                    const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
-                    ProposalRecord R;
-                    R.a = a;
-                    R.w = S.wfac[sb];
-                    R.y[0] = (-L + twoL * unif23(r0.w)) / L;
-                    R.y[1] = (-L + twoL * unif23(r1.x)) / L;
-                    R.y[2] = (-L + twoL * unif23(r1.y)) / L;
-                    R.y[3] = (-L + twoL * unif23(r1.z)) / L;
-                    R.y[4] = (-L + twoL * unif23(r1.w)) / L;
-                    P.rec[base + pos] = R;
+        if (ti < 0) {  // no running batch
+            if (MODE == M_RECORD && rec_due) {
+                // one record per sample with at least one accepted root (a zero
+                // weight teaches nothing); the sample's coordinates are drawn again
+                rec_due = false;
+                if (unit % P.rec_stride == 0) {
+                    const int sb = (bstart + lane) & (SBUF - 1);
+                    const bool keep = lane < bcnt && S.wfac[sb] > 0.0f;
+                    const unsigned keep_mask = __ballot_sync(0xffffffffu, keep);
+                    unsigned long long base = 0;
+                    if (lane == 0 && keep_mask) base = atomicAdd(P.rec_count, (unsigned long long)__popc(keep_mask));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const unsigned pos = __popc(keep_mask & lt_mask);
+                    if (keep && (long long)(base + pos) < P.rec_cap) {
+                        const int smp = bmeta & 0xFFFFFF;
+                        const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
+                        const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
+                        ProposalRecord R;
+                        R.a = a;
+                        R.w = S.wfac[sb];
+                        R.y[0] = (-L + twoL * unif23(r0.w)) / L;
+                        R.y[1] = (-L + twoL * unif23(r1.x)) / L;
+                        R.y[2] = (-L + twoL * unif23(r1.y)) / L;
+                        R.y[3] = (-L + twoL * unif23(r1.z)) / L;
+                        R.y[4] = (-L + twoL * unif23(r1.w)) / L;
+                        P.rec[base + pos] = R;
+                    }
                 }
+                __syncwarp();
+                continue;
             }
-            __syncwarp();
-            continue;
-        }
-        if (nlive - cons >= 32 || (c >= c1 && nlive > cons)) {  // start a batch
+            if (!(nlive - cons >= 32 || (c >= c1 && nlive > cons))) {
+                if (c >= c1) {  // every chunk drawn and every live sample taken: finish the pending roots
+                    if (tail > head) {
+                        flush = true;
+                        continue;
+                    }
+                    break;
+                }
+                // ---- sample geometry (one sample per lane) ----
+                const int smp = c * 32 + lane;
+                const bool live = smp < P.nsamples;
+                const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
+                const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
+                const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
+                const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
+                const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
+                float k1x, k1y, k30, k31, k32, wfac = 1.0f;
+                bool margk = false;
+                if (MODE == M_LEARNED) {
+                    // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
+                    const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
+                    // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
+                    // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
+                    // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
+                    // (2 + z^2)^(-3/2) / (s D).  Square roots only.
+                    const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
+                    float y[5];
+                    const bool uni = unif23(r2.x) < pa;
+                    float G = 1.0f;
+#pragma unroll
+                    for (int i = 0; i < 5; ++i) {
+                        const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
+                        const float sg = i < 2 ? ps1 : ps3;
+                        const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
+                        if (uni) {
+                            y[i] = 2.0f * uv[i] - 1.0f;
+                            const float zz = (y[i] - mu) / sg;
+                            const float r = rsqrtf(2.0f + zz * zz);
+                            G *= r * r * r / (sg * tc.z);
+                        } else {
+                            const float v = tc.x + uv[i] * tc.z;
+                            const float cv = tc.y + (1.0f - uv[i]) * tc.z;
+                            const float t = 2.0f * v * cv;
+                            const float rt = rsqrtf(t);
+                            y[i] = fminf(fmaxf(mu + sg * ((v - cv) * rt), -1.0f), 0.99999994f);
+                            G *= t * t * rt / (sg * tc.z);
+                        }
+                    }
+                    wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
+                    k1x = L * y[0];
+                    k1y = L * y[1];
+                    k30 = L * y[2];
+                    k31 = L * y[3];
+                    k32 = L * y[4];
+                    margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
+                            near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
+                            near_edge(k32, L, inv_dp2, EDGE_XY);
+                } else {
+                    k1x = -L + twoL * unif23(r0.w);
+                    k1y = -L + twoL * unif23(r1.x);
+                    k30 = -L + twoL * unif23(r1.y);
+                    k31 = -L + twoL * unif23(r1.z);
+                    k32 = -L + twoL * unif23(r1.w);
+                }
+                const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+                const float bx = Px - k1x, by = Py - k1y;
+                const bool k2xy_in = in_box(bx, L) && in_box(by, L);
+                const bool marg_xy = near_edge(bx, L, inv_dp0, EDGE_XY) || near_edge(by, L, inv_dp1, EDGE_XY) || margk;
+                const bool keep = live && (k2xy_in || marg_xy);
+                const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                const int cnt = __popc(kb);
+                // the new samples take the slots of sequence numbers nlive - SBUF ..:
+                // finish the pending roots that may still refer to those first.  The
+                // oldest pending root belongs to the batch of the head root, which
+                // starts at a multiple of 32 (only the last batch of a unit is short).
+                if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
+                    flush = true;  // draw this chunk again after the flush
+                    continue;
+                }
+                if (keep) {
+                    const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
+                    S.EpPz[sb] = make_float2(sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2), Pz);
+                    S.PPkk3[sb] = make_float2((Px * Px + Py * Py) + Pz * Pz, (k30 * k30 + k31 * k31) + k32 * k32);
+                    S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
+                    S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
+                    S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
+                    int lin3, b1xy;
+                    if (MODE == M_LEARNED) {
+                        lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                                     + binf(k32, L, inv_dp2, P.np[2]);
+                        b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                    } else {
+                        lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                                     + bin_word(r1.w, P.np[2]);
+                        b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                    }
+                    S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
+                    S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
+                    S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
+                }
+                nlive += cnt;
+                ++c;
+                __syncwarp();
+                if (!(nlive - cons >= 32 || (c >= c1 && nlive > cons))) continue;
+            }
+            // start a batch: the next <= 32 live samples, one per lane
             bstart = cons;
             bcnt = min(nlive - cons, 32);
             const int sb = (bstart + lane) & (SBUF - 1);
@@ -455,111 +486,88 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 bmeta = 0;
             }
             ti = 0;
-            continue;
         }
-        if (c < c1) {
-            // ---- sample geometry (one sample per lane) ----
-            const int smp = c * 32 + lane;
-            const bool live = smp < P.nsamples;
-            const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
-            const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
-            const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
-            const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
-            const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
-            float k1x, k1y, k30, k31, k32, wfac = 1.0f;
-            bool margk = false;
-            if (MODE == M_LEARNED) {
-                // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
-                const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
-                // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
-                // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
-                // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
-                // (2 + z^2)^(-3/2) / (s D).  Square roots only.
-                const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
-                float y[5];
-                const bool uni = unif23(r2.x) < pa;
-                float G = 1.0f;
-    #pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                    const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
-                    const float sg = i < 2 ? ps1 : ps3;
-                    const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
-                    if (uni) {
-                        y[i] = 2.0f * uv[i] - 1.0f;
-                        const float zz = (y[i] - mu) / sg;
-                        const float r = rsqrtf(2.0f + zz * zz);
-                        G *= r * r * r / (sg * tc.z);
-                    } else {
-                        const float v = tc.x + uv[i] * tc.z;
-                        const float cv = tc.y + (1.0f - uv[i]) * tc.z;
-                        const float t = 2.0f * v * cv;
-                        const float rt = rsqrtf(t);
-                        y[i] = fminf(fmaxf(mu + sg * ((v - cv) * rt), -1.0f), 0.99999994f);
-                        G *= t * t * rt / (sg * tc.z);
-                    }
+        if (ti < nt) {
+            // the batch's further groups in the same pass while the ring has room
+            do {
+                // ---- phase A: the kinematic group opened by term ti, for this lane's
+                // live sample.  Its terms (equal leg masses) share E3, D, kappa, H, the
+                // roots and the re-evaluation decision; each valid root goes to the
+                // ring once, tagged with the group's terms. ----
+                const int seq = bstart + lane;
+                const int gn = GROUPS ? S.tgn[ti] : 1;  // without GROUPS every group has one term
+                const bool act = lane < bcnt;
+                const bool k2xy_in = (bmeta >> 24) & 1, marg_xy = (bmeta >> 25) & 1;
+                const float4 tmv = S.tm[ti];
+                const float ma2 = tmv.x, mb2 = tmv.y, mc2 = tmv.z;
+                const float E3 = sqrtf(bkk3 + mc2);
+                const float E = bEp + E3;
+                const float Pz = bPz;
+                const float a2 = ba2m + ma2;
+                const float b2 = bb2m + mb2;
+                const float D = E * E - Pz * Pz;
+                const float kap = (E * E + a2 - b2 - Pz * Pz) * 0.5f;
+                const float H = kap * kap - a2 * D;
+                // straight-line form (no divergent branches): every lane evaluates the
+                // roots, and the flags select; float-float re-evaluation when the term is
+                // ill-conditioned (|H| < tau kappa^2) or a solved coordinate sits on an edge
+                const bool ok = act & (D > 0.0f);
+                const bool hp = ok & (H > 0.0f);
+                bool defer = ok & may_defer & (fabsf(H) < P.tau * (kap * kap));
+                const float sqH = sqrtf(H);
+                const float kp = kap * Pz;
+                const float sq = E * sqH;
+                const float Q = kp >= 0.0f ? kp + sq : kp - sq;
+                const bool qv = hp & (Q != 0.0f);
+                const float z0 = Q / D;
+                const float z1 = (E * E * a2 - kap * kap) / Q;
+                const float w0 = kap + Pz * z0, w1 = kap + Pz * z1, EE = E * E;
+                const bool e0 = qv & (w0 > 0.0f) & (w0 < EE), e1v = qv & (w1 > 0.0f) & (w1 < EE);
+                const float nu = EDGE_Z * (1.0f + fabsf(kap) / sqH);
+                const bool edge = (marg_xy & (e0 | e1v))
+                                  | (e0 & (near_edge(z0, L, inv_dp2, nu) | near_edge(Pz - z0, L, inv_dp2, nu)))
+                                  | (e1v & (near_edge(z1, L, inv_dp2, nu) | near_edge(Pz - z1, L, inv_dp2, nu)));
+                defer = defer | (may_defer & edge);
+                bool v0 = k2xy_in & e0 & in_box(z0, L) & in_box(Pz - z0, L);
+                bool v1 = k2xy_in & e1v & in_box(z1, L) & in_box(Pz - z1, L);
+                int t0 = ti, tn = gn;  // terms whose roots phase B evaluates
+                if (defer) {  // queued for re-evaluation; when the queue is full the FP32 roots stand
+                    const int qs = atomicAdd(dq.s_count, gn);
+                    const int nq = min(gn, max(0, dq.cap - qs));
+                    for (int k = 0; k < nq; ++k)
+                        dq.seg[qs + k] = box_tag | ((unsigned long long)a << 24)
+                                         | ((unsigned long long)(bmeta & 0xFFFFFF) << 4) | (unsigned long long)(ti + k);
+                    if (nq < gn) red_add(&P.flags[3], gn - nq);
+                    t0 = ti + nq;
+                    tn = gn - nq;
+                    if (tn == 0) v0 = v1 = false;
                 }
-                wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
-                k1x = L * y[0];
-                k1y = L * y[1];
-                k30 = L * y[2];
-                k31 = L * y[3];
-                k32 = L * y[4];
-                margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
-                        near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
-                        near_edge(k32, L, inv_dp2, EDGE_XY);
-            } else {
-                k1x = -L + twoL * unif23(r0.w);
-                k1y = -L + twoL * unif23(r1.x);
-                k30 = -L + twoL * unif23(r1.y);
-                k31 = -L + twoL * unif23(r1.z);
-                k32 = -L + twoL * unif23(r1.w);
-            }
-            const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
-            const float bx = Px - k1x, by = Py - k1y;
-            const bool k2xy_in = in_box(bx, L) && in_box(by, L);
-            const bool marg_xy = near_edge(bx, L, inv_dp0, EDGE_XY) || near_edge(by, L, inv_dp1, EDGE_XY) || margk;
-            const bool keep = live && (k2xy_in || marg_xy);
-            const unsigned kb = __ballot_sync(0xffffffffu, keep);
-            const int cnt = __popc(kb);
-            // the new samples take the slots of sequence numbers nlive - SBUF ..:
-            // finish the pending roots that may still refer to those first.  The
-            // oldest pending root belongs to the batch of the head root, which
-            // starts at a multiple of 32 (only the last batch of a unit is short).
-            if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
-                flush = true;  // draw this chunk again after the flush
-                continue;
-            }
-            if (keep) {
-                const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
-                S.EpPz[sb] = make_float2(sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2), Pz);
-                S.PPkk3[sb] = make_float2((Px * Px + Py * Py) + Pz * Pz, (k30 * k30 + k31 * k31) + k32 * k32);
-                S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
-                S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
-                S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
-                int lin3, b1xy;
-                if (MODE == M_LEARNED) {
-                    lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
-                                 + binf(k32, L, inv_dp2, P.np[2]);
-                    b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
-                } else {
-                    lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
-                                 + bin_word(r1.w, P.np[2]);
-                    b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                // append the valid roots to the ring
+                const unsigned tag = (unsigned)seq | ((unsigned)t0 << 24) | ((unsigned)(tn - 1) << 28);
+                const unsigned b0 = __ballot_sync(0xffffffffu, v0);
+                const unsigned b1 = __ballot_sync(0xffffffffu, v1);
+                const int n0 = __popc(b0);
+                if (v0) {
+                    const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
+                    S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
                 }
-                S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
-                S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
-                S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
+                if (v1) {
+                    const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
+                    S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
+                }
+                tail += n0 + __popc(b1);
+                ti += gn;
+                __syncwarp();
+            } while (GROUPS && ti < nt && tail - head < 32);
+        }
+        if (ti >= nt) {  // batch done; record mode first finishes its roots, then writes records
+            cons = bstart + bcnt;
+            ti = -1;
+            if (MODE == M_RECORD) {
+                flush = true;
+                rec_due = true;
             }
-            nlive += cnt;
-            ++c;
-            __syncwarp();
-            continue;
         }
-        if (tail > head) {
-            flush = true;
-            continue;
-        }
-        break;
     }
     if (MODE != M_RECORD) {
         own = warp_sum_ll(own);
