@@ -332,10 +332,11 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
     float bEp = 0.0f, bPz = 0.0f, ba2m = 0.0f, bb2m = 0.0f, bkk3 = 0.0f;
     int bmeta = 0;
     for (;;) {
-        const int pend = tail - head;
+        int pend = tail - head;
         if (pend >= 32 || (flush && pend > 0)) {
             process(min(pend, 32));
-            continue;
+            pend = tail - head;
+            if (pend >= 32 || (flush && pend > 0)) continue;
         }
         flush = false;
         if (ti < 0) {  // no running batch
@@ -377,101 +378,110 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     }
                     break;
                 }
-                // ---- sample geometry (one sample per lane) ----
-                const int smp = c * 32 + lane;
-                const bool live = smp < P.nsamples;
-                const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
-                const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
-                const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
-                const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
-                const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
-                float k1x, k1y, k30, k31, k32, wfac = 1.0f;
-                bool margk = false;
-                if (MODE == M_LEARNED) {
-                    // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
-                    const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
-                    // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
-                    // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
-                    // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
-                    // (2 + z^2)^(-3/2) / (s D).  Square roots only.
-                    const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
-                    float y[5];
-                    const bool uni = unif23(r2.x) < pa;
-                    float G = 1.0f;
-#pragma unroll
-                    for (int i = 0; i < 5; ++i) {
-                        const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
-                        const float sg = i < 2 ? ps1 : ps3;
-                        const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
-                        if (uni) {
-                            y[i] = 2.0f * uv[i] - 1.0f;
-                            const float zz = (y[i] - mu) / sg;
-                            const float r = rsqrtf(2.0f + zz * zz);
-                            G *= r * r * r / (sg * tc.z);
-                        } else {
-                            const float v = tc.x + uv[i] * tc.z;
-                            const float cv = tc.y + (1.0f - uv[i]) * tc.z;
-                            const float t = 2.0f * v * cv;
-                            const float rt = rsqrtf(t);
-                            y[i] = fminf(fmaxf(mu + sg * ((v - cv) * rt), -1.0f), 0.99999994f);
-                            G *= t * t * rt / (sg * tc.z);
+                // draw chunks until 32 live samples are buffered (the buffer then holds
+                // fewer than 64 not yet taken) or the unit's chunks are drawn
+                bool redo = false;
+                do {
+                    // ---- sample geometry (one sample per lane) ----
+                    const int smp = c * 32 + lane;
+                    const bool live = smp < P.nsamples;
+                    const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
+                    const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
+                    const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
+                    const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
+                    const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
+                    float k1x, k1y, k30, k31, k32, wfac = 1.0f;
+                    bool margk = false;
+                    if (MODE == M_LEARNED) {
+                        // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
+                        const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
+                        // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
+                        // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
+                        // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
+                        // (2 + z^2)^(-3/2) / (s D).  Square roots only.
+                        const float uv[5] = {unif23(r0.w), unif23(r1.x), unif23(r1.y), unif23(r1.z), unif23(r1.w)};
+                        float y[5];
+                        const bool uni = unif23(r2.x) < pa;
+                        float G = 1.0f;
+    #pragma unroll
+                        for (int i = 0; i < 5; ++i) {
+                            const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
+                            const float sg = i < 2 ? ps1 : ps3;
+                            const float3 tc = S.tlc[i < 2 ? 0 : i - 1];
+                            if (uni) {
+                                y[i] = 2.0f * uv[i] - 1.0f;
+                                const float zz = (y[i] - mu) / sg;
+                                const float r = rsqrtf(2.0f + zz * zz);
+                                G *= r * r * r / (sg * tc.z);
+                            } else {
+                                const float v = tc.x + uv[i] * tc.z;
+                                const float cv = tc.y + (1.0f - uv[i]) * tc.z;
+                                const float t = 2.0f * v * cv;
+                                const float rt = rsqrtf(t);
+                                y[i] = fminf(fmaxf(mu + sg * ((v - cv) * rt), -1.0f), 0.99999994f);
+                                G *= t * t * rt / (sg * tc.z);
+                            }
                         }
+                        wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
+                        k1x = L * y[0];
+                        k1y = L * y[1];
+                        k30 = L * y[2];
+                        k31 = L * y[3];
+                        k32 = L * y[4];
+                        margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
+                                near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
+                                near_edge(k32, L, inv_dp2, EDGE_XY);
+                    } else {
+                        k1x = -L + twoL * unif23(r0.w);
+                        k1y = -L + twoL * unif23(r1.x);
+                        k30 = -L + twoL * unif23(r1.y);
+                        k31 = -L + twoL * unif23(r1.z);
+                        k32 = -L + twoL * unif23(r1.w);
                     }
-                    wfac = 1.0f / (32.0f * (pa * (1.0f / 32.0f) + (1.0f - pa) * G));
-                    k1x = L * y[0];
-                    k1y = L * y[1];
-                    k30 = L * y[2];
-                    k31 = L * y[3];
-                    k32 = L * y[4];
-                    margk = near_edge(k1x, L, inv_dp0, EDGE_XY) || near_edge(k1y, L, inv_dp1, EDGE_XY) ||
-                            near_edge(k30, L, inv_dp0, EDGE_XY) || near_edge(k31, L, inv_dp1, EDGE_XY) ||
-                            near_edge(k32, L, inv_dp2, EDGE_XY);
-                } else {
-                    k1x = -L + twoL * unif23(r0.w);
-                    k1y = -L + twoL * unif23(r1.x);
-                    k30 = -L + twoL * unif23(r1.y);
-                    k31 = -L + twoL * unif23(r1.z);
-                    k32 = -L + twoL * unif23(r1.w);
-                }
-                const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
-                const float bx = Px - k1x, by = Py - k1y;
-                const bool k2xy_in = in_box(bx, L) && in_box(by, L);
-                const bool marg_xy = near_edge(bx, L, inv_dp0, EDGE_XY) || near_edge(by, L, inv_dp1, EDGE_XY) || margk;
-                const bool keep = live && (k2xy_in || marg_xy);
-                const unsigned kb = __ballot_sync(0xffffffffu, keep);
-                const int cnt = __popc(kb);
-                // the new samples take the slots of sequence numbers nlive - SBUF ..:
-                // finish the pending roots that may still refer to those first.  The
-                // oldest pending root belongs to the batch of the head root, which
-                // starts at a multiple of 32 (only the last batch of a unit is short).
-                if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
-                    flush = true;  // draw this chunk again after the flush
+                    const float Px = p0 + k30, Py = p1 + k31, Pz = p2 + k32;
+                    const float bx = Px - k1x, by = Py - k1y;
+                    const bool k2xy_in = in_box(bx, L) && in_box(by, L);
+                    const bool marg_xy = near_edge(bx, L, inv_dp0, EDGE_XY) || near_edge(by, L, inv_dp1, EDGE_XY) || margk;
+                    const bool keep = live && (k2xy_in || marg_xy);
+                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                    const int cnt = __popc(kb);
+                    // the new samples take the slots of sequence numbers nlive - SBUF ..:
+                    // finish the pending roots that may still refer to those first.  The
+                    // oldest pending root belongs to the batch of the head root, which
+                    // starts at a multiple of 32 (only the last batch of a unit is short).
+                    if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
+                        redo = true;  // draw this chunk again after the flush
+                        break;
+                    }
+                    if (keep) {
+                        const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
+                        S.EpPz[sb] = make_float2(sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2), Pz);
+                        S.PPkk3[sb] = make_float2((Px * Px + Py * Py) + Pz * Pz, (k30 * k30 + k31 * k31) + k32 * k32);
+                        S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
+                        S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
+                        S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
+                        int lin3, b1xy;
+                        if (MODE == M_LEARNED) {
+                            lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                                         + binf(k32, L, inv_dp2, P.np[2]);
+                            b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                        } else {
+                            lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                                         + bin_word(r1.w, P.np[2]);
+                            b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                        }
+                        S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
+                        S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
+                        S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
+                    }
+                    nlive += cnt;
+                    ++c;
+                    __syncwarp();
+                } while (c < c1 && nlive - cons < 32);
+                if (redo) {
+                    flush = true;
                     continue;
                 }
-                if (keep) {
-                    const int sb = (nlive + __popc(kb & lt_mask)) & (SBUF - 1);
-                    S.EpPz[sb] = make_float2(sqrtf((p0 * p0 + p1 * p1) + p2 * p2 + md2), Pz);
-                    S.PPkk3[sb] = make_float2((Px * Px + Py * Py) + Pz * Pz, (k30 * k30 + k31 * k31) + k32 * k32);
-                    S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
-                    S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
-                    S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
-                    int lin3, b1xy;
-                    if (MODE == M_LEARNED) {
-                        lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
-                                     + binf(k32, L, inv_dp2, P.np[2]);
-                        b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
-                    } else {
-                        lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
-                                     + bin_word(r1.w, P.np[2]);
-                        b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
-                    }
-                    S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
-                    S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
-                    S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
-                }
-                nlive += cnt;
-                ++c;
-                __syncwarp();
                 if (!(nlive - cons >= 32 || (c >= c1 && nlive > cons))) continue;
             }
             // start a batch: the next <= 32 live samples, one per lane
