@@ -53,6 +53,60 @@ __device__ __forceinline__ uint4 philox4x32_10_ks(uint4 c, const uint32_t* ks)
     return c;
 }
 
+// Philox4x32-10 over a family of counters (c0, cy, cz, cw) that share
+// (cy, cz, cw) -- the samples of one anchor: in the first round the product
+// of cz, and in the second the product of the first round's x word
+// mulhi(M1, cz) ^ cy ^ k0, do not depend on c0.  philox_head computes them
+// once for the family, folded with the key words they meet; philox_tail_*
+// finishes one counter.  The rounds and the words are those of
+// philox4x32_10.  Head words: (cw ^ k1 of round 1, lo(M1 cz) ^ k0 of round 2,
+// hi(M0 x1) ^ k1 of round 2, lo(M0 x1)).
+__device__ __forceinline__ uint4 philox_head(uint32_t cy, uint32_t cz, uint32_t cw, uint32_t k0a, uint32_t k1a,
+                                             uint32_t k0b, uint32_t k1b)
+{
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, cz), lo1 = 0xCD9E8D57u * cz;
+    const uint32_t x1 = hi1 ^ cy ^ k0a;
+    return make_uint4(cw ^ k1a, lo1 ^ k0b, __umulhi(0xD2511F53u, x1) ^ k1b, 0xD2511F53u * x1);
+}
+
+// Rounds 1 and 2 of counter c0 from the head, rounds 3..10 in full.
+__device__ __forceinline__ uint4 philox_tail_first2(uint32_t c0, uint4 h)
+{
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t z1 = hi0 ^ h.x;
+    return make_uint4(__umulhi(0xCD9E8D57u, z1) ^ h.y, 0xCD9E8D57u * z1, h.z ^ lo0, h.w);
+}
+
+// The key words of every round from a schedule (philox_key_schedule).
+__device__ __forceinline__ uint4 philox_tail_ks(uint32_t c0, uint4 h, const uint32_t* ks)
+{
+    uint4 c = philox_tail_first2(c0, h);
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ ks[2 * r], lo1, hi0 ^ c.w ^ ks[2 * r + 1], lo0);
+    }
+    return c;
+}
+
+// The key words bumped round by round from the key (k0, k1) of round 1.
+__device__ __forceinline__ uint4 philox_tail(uint32_t c0, uint4 h, uint32_t k0, uint32_t k1)
+{
+    uint4 c = philox_tail_first2(c0, h);
+    k0 += 2u * 0x9E3779B9u;
+    k1 += 2u * 0xBB67AE85u;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
 template <typename R> struct Ops;
 template <> struct Ops<double> {
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }

@@ -139,10 +139,20 @@ enum { M_UNIFORM = 0, M_LEARNED = 1, M_RECORD = 2 };
 // SINGLE: P is the kernel's own argument block (constant bank), so the Philox
 // key schedule is read from it as instruction operands; a batch box's block
 // lives in global memory and the keys are bumped round by round instead.
+// The samples of a unit share the counter words (p cell, x cell, step and
+// species), so the parts of the first two Philox rounds that depend only on
+// them are computed once per unit (head) and each draw finishes its counter.
 template <bool SINGLE>
-__device__ __forceinline__ uint4 draw(const CollideArgs<float>& P, uint4 ctr)
+__device__ __forceinline__ uint4 draw_head(const CollideArgs<float>& P, uint32_t cy, uint32_t cz, uint32_t cw)
 {
-    return SINGLE ? philox4x32_10_ks(ctr, P.ks) : philox4x32_10(ctr, P.key0, P.key1);
+    return SINGLE ? philox_head(cy, cz, cw, P.ks[0], P.ks[1], P.ks[2], P.ks[3])
+                  : philox_head(cy, cz, cw, P.key0, P.key1, P.key0 + 0x9E3779B9u, P.key1 + 0xBB67AE85u);
+}
+template <bool SINGLE>
+__device__ __forceinline__ uint4 draw(const CollideArgs<float>& P, uint32_t c0, uint4 head, uint32_t cy, uint32_t cz,
+                                      uint32_t cw)
+{
+    return SINGLE ? philox_tail_ks(c0, head, P.ks) : philox4x32_10(make_uint4(c0, cy, cz, cw), P.key0, P.key1);
 }
 
 template <int MODE, bool GROUPS, bool SINGLE>
@@ -211,6 +221,9 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                                              lane == 0 ? ps1 : ps3);
     }
     const uint32_t ctr3 = ((uint32_t)step << 3) | (uint32_t)d;
+    // single boxes: the unit's Philox head; the batch kernel (whose registers
+    // are spoken for) runs every round of each counter
+    const uint4 phead = SINGLE ? draw_head<SINGLE>(P, (uint32_t)j, (uint32_t)x, ctr3) : make_uint4(0u, 0u, 0u, 0u);
     const float pc0 = -L + ((float)jx + 0.5f) * P.dp[0];
     const float pc1 = -L + ((float)jy + 0.5f) * P.dp[1];
     const float pc2 = -L + ((float)jz + 0.5f) * P.dp[2];
@@ -354,8 +367,8 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const unsigned pos = __popc(keep_mask & lt_mask);
                     if (keep && (long long)(base + pos) < P.rec_cap) {
                         const int smp = bmeta & 0xFFFFFF;
-                        const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
-                        const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
+                        const uint4 r0 = draw<SINGLE>(P, 2u * smp, phead, (uint32_t)j, (uint32_t)x, ctr3);
+                        const uint4 r1 = draw<SINGLE>(P, 2u * smp + 1u, phead, (uint32_t)j, (uint32_t)x, ctr3);
                         ProposalRecord R;
                         R.a = a;
                         R.w = S.wfac[sb];
@@ -385,8 +398,8 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     // ---- sample geometry (one sample per lane) ----
                     const int smp = c * 32 + lane;
                     const bool live = smp < P.nsamples;
-                    const uint4 r0 = draw<SINGLE>(P, make_uint4(2u * smp, (uint32_t)j, (uint32_t)x, ctr3));
-                    const uint4 r1 = draw<SINGLE>(P, make_uint4(2u * smp + 1u, (uint32_t)j, (uint32_t)x, ctr3));
+                    const uint4 r0 = draw<SINGLE>(P, 2u * smp, phead, (uint32_t)j, (uint32_t)x, ctr3);
+                    const uint4 r1 = draw<SINGLE>(P, 2u * smp + 1u, phead, (uint32_t)j, (uint32_t)x, ctr3);
                     const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
                     const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
                     const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
@@ -394,7 +407,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     bool margk = false;
                     if (MODE == M_LEARNED) {
                         // defensive mixture alpha U + (1 - alpha) prod g_i, selector from a third block
-                        const uint4 r2 = draw<SINGLE>(P, make_uint4(0x80000000u | (uint32_t)smp, (uint32_t)j, (uint32_t)x, ctr3));
+                        const uint4 r2 = draw<SINGLE>(P, 0x80000000u | (uint32_t)smp, phead, (uint32_t)j, (uint32_t)x, ctr3);
                         // Component i: with v = Fa + u D and cv = cFb + (1 - u) D = 1 - v,
                         // y = mu + s (v - cv) / sqrt(2 v cv), where the density is
                         // (2 v cv)^(3/2) / (s D); a uniform draw y = 2u - 1 has density
