@@ -55,9 +55,9 @@ struct WarpSmem {
     int2 lin3meta[SBUF];          // bin of k3; sample index | k2perp inside << 24 | on an edge << 25
     float wfac[SBUF];             // learned: 1/(32 q(y)); record mode: sum of |c~| of the sample
     float3 tlc[4];                // learned: t2_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
-    // pending roots
-    float z[RING], E3[RING], sqH[RING];
-    unsigned tag[RING];           // live-sample sequence number | first term << 24 | (terms - 1) << 28
+    // pending roots: (z, E3, sqrt H, tag as bits), one 16-byte entry per root;
+    // tag = live-sample sequence number | first term << 24 | (terms - 1) << 28
+    float4 ring[RING];
     // this unit's terms: masses of the legs and sym, packed leg slots / flags / row
     float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
     int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
@@ -66,8 +66,16 @@ struct WarpSmem {
 
 __device__ __forceinline__ float unif23(uint32_t x)
 {
-    // ((x >> 9) + 1/2) 2^-23, exactly: 1.m - 1 gives m 2^-23, + 2^-24 is exact
-    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.0f) + 5.9604644775390625e-8f;
+    // ((x >> 9) + 1/2) 2^-23 = 1.m - (1 - 2^-24), exact in one subtraction:
+    // (2m + 1) 2^-24 has at most 24 significant bits
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994f;
+}
+
+// unif23(x) - 1/2, exactly: 1.m - 3/2 is exact (operands within a factor of
+// two), and adding 2^-24 to it is too ((2m + 1 - 2^23) 2^-24, |.| < 2^23 units)
+__device__ __forceinline__ float jit23(uint32_t x)
+{
+    return (__uint_as_float(0x3F800000u | (x >> 9)) - 1.5f) + 5.9604644775390625e-8f;
 }
 
 __device__ __forceinline__ float sel4(int k, float a, float b, float c, float d)
@@ -103,9 +111,9 @@ constexpr float EDGE_XY = 1e-5f;
 constexpr float EDGE_Z = 1e-5f;
 __device__ __forceinline__ bool near_edge(float v, float L, float inv_dp, float nu)
 {
+    // r = frac(t) within nu of 0 or 1: |r - 1/2| > 1/2 - nu (r - 1/2 is exact)
     const float t = (v + L) * inv_dp;
-    const float r = t - floorf(t);
-    return r < nu || r > 1.0f - nu;
+    return fabsf((t - floorf(t)) - 0.5f) > 0.5f - nu;
 }
 
 // Student-t with two degrees of freedom, truncated to [-1, 1), centre mu and
@@ -241,10 +249,11 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
         int src_rec = -1 - lane;
         if (lane < n) {
             const int ri = (head + lane) & (RING - 1);
-            const unsigned tg = S.tag[ri];
+            const float4 rv = S.ring[ri];
+            const unsigned tg = __float_as_uint(rv.w);
             const int src = tg & (SBUF - 1), t0 = (tg >> 24) & 15, tn = GROUPS ? (int)(tg >> 28) + 1 : 1;
             src_rec = src;
-            const float z = S.z[ri], E3 = S.E3[ri], sqH = S.sqH[ri];
+            const float z = rv.x, E3 = rv.y, sqH = rv.z;
             const float4 tmv0 = S.tm[t0];  // leg masses shared by the group's terms
             const float ma2 = tmv0.x, mc2 = tmv0.z;
             const float2 epz = S.EpPz[src];
@@ -400,9 +409,9 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const bool live = smp < P.nsamples;
                     const uint4 r0 = draw<SINGLE>(P, 2u * smp, phead, (uint32_t)j, (uint32_t)x, ctr3);
                     const uint4 r1 = draw<SINGLE>(P, 2u * smp + 1u, phead, (uint32_t)j, (uint32_t)x, ctr3);
-                    const float p0 = pc0 + P.dp[0] * (unif23(r0.x) - 0.5f);
-                    const float p1 = pc1 + P.dp[1] * (unif23(r0.y) - 0.5f);
-                    const float p2 = pc2 + P.dp[2] * (unif23(r0.z) - 0.5f);
+                    const float p0 = pc0 + P.dp[0] * jit23(r0.x);
+                    const float p1 = pc1 + P.dp[1] * jit23(r0.y);
+                    const float p2 = pc2 + P.dp[2] * jit23(r0.z);
                     float k1x, k1y, k30, k31, k32, wfac = 1.0f;
                     bool margk = false;
                     if (MODE == M_LEARNED) {
@@ -462,7 +471,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     // finish the pending roots that may still refer to those first.  The
                     // oldest pending root belongs to the batch of the head root, which
                     // starts at a multiple of 32 (only the last batch of a unit is short).
-                    if (pend > 0 && ((S.tag[head & (RING - 1)] & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
+                    if (pend > 0 && ((__float_as_uint(S.ring[head & (RING - 1)].w) & 0xFFFFFF) & ~31) + SBUF < nlive + cnt) {
                         redo = true;  // draw this chunk again after the flush
                         break;
                     }
@@ -572,11 +581,11 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                 const int n0 = __popc(b0);
                 if (v0) {
                     const int r = (tail + __popc(b0 & lt_mask)) & (RING - 1);
-                    S.z[r] = z0; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
+                    S.ring[r] = make_float4(z0, E3, sqH, __uint_as_float(tag));
                 }
                 if (v1) {
                     const int r = (tail + n0 + __popc(b1 & lt_mask)) & (RING - 1);
-                    S.z[r] = z1; S.E3[r] = E3; S.sqH[r] = sqH; S.tag[r] = tag;
+                    S.ring[r] = make_float4(z1, E3, sqH, __uint_as_float(tag));
                 }
                 tail += n0 + __popc(b1);
                 ti += gn;
