@@ -43,7 +43,7 @@ constexpr int WARPS = F32_WARPS;  // warps per block
 #define BZ_F32_MIN_BLOCKS_GROUPED 7  // the same for single boxes whose equations have groups of several terms
 #endif
 
-struct WarpSmem {
+struct WarpSmemBase {
     // live samples (k2 inside the box in x and y, or on its edge), [field][slot];
     // fields read together are paired into 8-byte words
     float2 EpPz[SBUF];            // Ep, Pz
@@ -51,8 +51,7 @@ struct WarpSmem {
     float2 PPkk3[SBUF];           // P^2, |k3|^2
     float2 k13k3z[SBUF];          // k1perp.k3perp, k3z
     float2 k1ppz[SBUF];           // k1perp.pperp, pz
-    int2 bxy[SBUF];               // bins of k1perp and k2perp (x, y)
-    int2 lin3meta[SBUF];          // bin of k3; sample index | k2perp inside << 24 | on an edge << 25
+    int2 lin3meta[SBUF];          // bin of k3 or its Philox word (see below); sample index | k2perp inside << 24 | on an edge << 25
     float wfac[SBUF];             // learned: 1/(32 q(y)); record mode: sum of |c~| of the sample
     float3 tlc[4];                // learned: t2_consts of k1 (centre 0, sigma1) and of k3x, k3y, k3z
     // pending roots: (z, E3, sqrt H, tag as bits), one 16-byte entry per root;
@@ -62,6 +61,21 @@ struct WarpSmem {
     float4 tm[MAX_TERMS];         // (ma2, mb2, mc2, sym)
     int tinfo[MAX_TERMS];         // slot0 | slot1 << 3 | slot2 << 6 | quark0..3 << 9..12 | cls << 13
     int tgn[MAX_TERMS];           // terms of the kinematic group the term opens (0: not a group's first)
+};
+
+// The sampled legs' bins.  Equations whose groups have several terms (several
+// roots per sample) take them at the draw: bxy = (bin of k1perp, bin of
+// k2perp), lin3meta.x = bin of k3.  Equations of one-term groups in uniform and
+// record modes (about a third of their samples have a root) take them when a
+// root is evaluated, from the kept Philox words of k1perp and k3 (w4 = k1x,
+// k1y, k3x, k3y words; lin3meta.x = the k3z word) and k2perp (bxyf).
+template <bool BINS_AT_ROOT> struct WarpSmem;
+template <> struct WarpSmem<false> : WarpSmemBase {
+    int2 bxy[SBUF];
+};
+template <> struct WarpSmem<true> : WarpSmemBase {
+    uint4 w4[SBUF];
+    float2 bxyf[SBUF];
 };
 
 __device__ __forceinline__ float unif23(uint32_t x)
@@ -164,9 +178,12 @@ __device__ __forceinline__ uint4 draw(const CollideArgs<float>& P, uint32_t c0, 
 }
 
 template <int MODE, bool GROUPS, bool SINGLE>
-__device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step, WarpSmem& S,
+__device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_t unit, int step,
+                                             WarpSmem<(!GROUPS && MODE != M_LEARNED)>& S,
                                              DeferCtx& dq, unsigned long long box_tag)
 {
+    // the sampled legs' bins when a root is evaluated (one-term groups, sampled words)
+    constexpr bool BINS_AT_ROOT = !GROUPS && MODE != M_LEARNED;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float L = P.L, twoL = P.twoL;
@@ -271,9 +288,22 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
             if (s <= 0.0f || t - mg2 >= 0.0f || uu - mg2 >= 0.0f) {
                 red_add(&P.flags[0], tn);
             } else {
-                const int2 bxy = S.bxy[src];
-                const int lin1 = bxy.x * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
-                const int lin2 = bxy.y * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
+                int b1xy, b2xy, lin3;
+                if constexpr (!BINS_AT_ROOT) {
+                    const int2 bxy = S.bxy[src];
+                    b1xy = bxy.x;
+                    b2xy = bxy.y;
+                    lin3 = S.lin3meta[src].x;
+                } else {
+                    const uint4 w4 = S.w4[src];
+                    const float2 bb = S.bxyf[src];
+                    b1xy = bin_word(w4.x, P.np[0]) * P.np[1] + bin_word(w4.y, P.np[1]);
+                    lin3 = (bin_word(w4.z, P.np[0]) * P.np[1] + bin_word(w4.w, P.np[1])) * P.np[2]
+                           + bin_word((uint32_t)S.lin3meta[src].x, P.np[2]);
+                    b2xy = binf(bb.x, L, inv_dp0, P.np[0]) * P.np[1] + binf(bb.y, L, inv_dp1, P.np[1]);
+                }
+                const int lin1 = b1xy * P.np[2] + binf(z, L, inv_dp2, P.np[2]);
+                const int lin2 = b2xy * P.np[2] + binf(dz, L, inv_dp2, P.np[2]);
                 // |J| E1 E2 = sqrt(H) at a root of Eq. (work out delta E)
                 const float den = P.twopi5 * 16.0f * sqH * E3 * Ep;
                 for (int k = 0; k < tn; ++k) {  // the group's terms: |M|^2, leg species, statistics
@@ -283,7 +313,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                     const float M2 = msq<float>(info >> 13, P, s, t, uu, mg2);
                     const unsigned i1 = (unsigned)(info & 7) * slot_stride + xoff + lin1;
                     const unsigned i2 = (unsigned)((info >> 3) & 7) * slot_stride + xoff + lin2;
-                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + S.lin3meta[src].x;
+                    const unsigned i3 = (unsigned)((info >> 6) & 7) * slot_stride + xoff + lin3;
                     if (!(bz_in(i1, P.ncell) & bz_in(i2, P.ncell) & bz_in(i3, P.ncell))) continue;
                     float f1, f2, f3, fpp;
                     if (P.analytic) {
@@ -482,18 +512,25 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                         S.ab2m[sb] = make_float2(k1x * k1x + k1y * k1y, bx * bx + by * by);
                         S.k13k3z[sb] = make_float2(k1x * k30 + k1y * k31, k32);
                         S.k1ppz[sb] = make_float2(k1x * p0 + k1y * p1, p2);
-                        int lin3, b1xy;
-                        if (MODE == M_LEARNED) {
-                            lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
-                                         + binf(k32, L, inv_dp2, P.np[2]);
-                            b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                        const int meta = smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25);
+                        if constexpr (!BINS_AT_ROOT) {
+                            int lin3, b1xy;
+                            if (MODE == M_LEARNED) {
+                                lin3 = (binf(k30, L, inv_dp0, P.np[0]) * P.np[1] + binf(k31, L, inv_dp1, P.np[1])) * P.np[2]
+                                       + binf(k32, L, inv_dp2, P.np[2]);
+                                b1xy = binf(k1x, L, inv_dp0, P.np[0]) * P.np[1] + binf(k1y, L, inv_dp1, P.np[1]);
+                            } else {
+                                lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
+                                       + bin_word(r1.w, P.np[2]);
+                                b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                            }
+                            S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
+                            S.lin3meta[sb] = make_int2(lin3, meta);
                         } else {
-                            lin3 = (bin_word(r1.y, P.np[0]) * P.np[1] + bin_word(r1.z, P.np[1])) * P.np[2]
-                                         + bin_word(r1.w, P.np[2]);
-                            b1xy = bin_word(r0.w, P.np[0]) * P.np[1] + bin_word(r1.x, P.np[1]);
+                            S.w4[sb] = make_uint4(r0.w, r1.x, r1.y, r1.z);
+                            S.bxyf[sb] = make_float2(bx, by);
+                            S.lin3meta[sb] = make_int2((int)r1.w, meta);
                         }
-                        S.bxy[sb] = make_int2(b1xy, binf(bx, L, inv_dp0, P.np[0]) * P.np[1] + binf(by, L, inv_dp1, P.np[1]));
-                        S.lin3meta[sb] = make_int2(lin3, smp | ((int)k2xy_in << 24) | ((int)marg_xy << 25));
                         S.wfac[sb] = MODE == M_RECORD ? 0.0f : wfac;
                     }
                     nlive += cnt;
@@ -627,7 +664,7 @@ __global__ void __launch_bounds__(32 * WARPS, (GROUPS && !BATCH) ? BZ_F32_MIN_BL
                   const int64_t* __restrict__ prefix, int nboxes, unsigned long long* counter, const int* step_dev,
                   int chunk, int* qcount, unsigned long long* qitems, long long qcap)
 {
-    __shared__ WarpSmem smem[WARPS];
+    __shared__ WarpSmem<(!GROUPS && MODE != M_LEARNED)> smem[WARPS];
     __shared__ int s_qcount[WARPS];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
