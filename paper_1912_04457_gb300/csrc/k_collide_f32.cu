@@ -455,7 +455,7 @@ __device__ __forceinline__ void collide_unit(const CollideArgs<float>& P, int64_
                         float y[5];
                         const bool uni = unif23(r2.x) < pa;
                         float G = 1.0f;
-    #pragma unroll
+#pragma unroll
                         for (int i = 0; i < 5; ++i) {
                             const float mu = i < 2 ? 0.0f : (i == 2 ? pm0 : (i == 3 ? pm1 : pm2));
                             const float sg = i < 2 ? ps1 : ps3;
