@@ -425,6 +425,15 @@ def run_bz(args):
             executed = {"achieved": ex, "frac": ex / peak, "unit": "TFLOP/s",
                         "basis": "FP32 add + mul + 2 x FMA executed per launch (ncu instruction counters, "
                                  "committed summary) over the same event-timed launch duration"}
+        issue = None
+        if summ and summ.get("warp_inst_executed_per_launch"):
+            # the kernel is bound by instruction issue: warp instructions per second against one
+            # instruction per scheduler per clock (4 schedulers per SM)
+            ia = summ["warp_inst_executed_per_launch"] / coll_s / 1e9
+            ip = nsm * 4 * mhz * 1e6 / 1e9
+            issue = {"achieved": ia, "peak": ip, "unit": "G warp instructions/s", "frac": ia / ip,
+                     "basis": "warp instructions executed per launch (ncu, committed summary) over the "
+                              "event-timed launch duration; peak = SMs x 4 schedulers x sampled SM clock"}
 
         # the plain FP64 GPU path on the same workload (one step, same samples)
         fp64 = None
@@ -479,7 +488,7 @@ def run_bz(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_collide_f32 (FP32 pipe)",
-                         "executed": executed,
+                         "executed": executed, "issue": issue,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 flop (FMA) x %.0f MHz sampled "
                                        "median SM clock" % (nsm, mhz),
                          "work_basis": "%d flop/sample + %d flop/term + %d flop/accepted root, "
