@@ -364,9 +364,11 @@ def test_qgp_box_full_size_sampled_anchors():
     assert int(A.abs().sum().item()) > 0
 
 
-def test_gluon_bump_full_size():
+def test_gluon_bump_full_size(monkeypatch):
     """16^3 x 20^3 gluons, N = 256: masses and drift over all 33M cells are
-    bit-exact; collisions on sampled anchors; one full FP32 step conserves."""
+    bit-exact; collisions on sampled anchors (FP64 bit-exact, the FP32 kernel of
+    the timed step within tolerance under both work schedules, the same bits
+    from each); one full FP32 step conserves."""
     from paper_1912_04457_gb300 import bz
     torch = torch_mod()
     w = I.gluon_bump_xp()
@@ -384,7 +386,20 @@ def test_gluon_bump_full_size():
     out = torch.empty_like(dev)
     h.drift(dev, out, w.dt)
     assert np.array_equal(out.cpu().numpy().reshape(st.shape), O.drift(cfg, st, m2, w.dt))
+    ref32 = O.collision(cfg, st, m2, w.nsamples, step=0, dt=w.dt, ubits=23, anchor_stride=65537,
+                        anchor_offset=11)["A"]
+    got = {}
+    for sched in ("counter", "static"):
+        monkeypatch.setenv("BZ_F32_SCHEDULE", sched)
+        h.reset_masses()
+        h.collision_term(dev, A, w.nsamples, 0, w.dt, bz.PREC_F32)
+        got[sched] = A.cpu().numpy().reshape(ref32.shape)
+        assert int(got[sched].sum()) == 0
+        assert rel_l2(got[sched], ref32) <= F32_TOL
+    monkeypatch.delenv("BZ_F32_SCHEDULE")
+    assert np.array_equal(got["counter"], got["static"])
     h.set_anchor_subset(1, 0)
+    h.reset_masses()
     total = int(dev.sum().item())
     h.step(dev, w.dt, 1, w.nsamples, bz.PREC_F32)
     assert int(dev.sum().item()) == total
